@@ -1,0 +1,446 @@
+"""Benchmark: dynamic-SSSP batch repair on GB300 (edge-updates/s, p50/p99).
+
+One step = one sp_apply_batch of one update batch (sort, count, merge into
+both stores, OnDelete mark + subtree invalidation, pull, OnAdd relax, push
+fixedPoint) on the device-resident graph.  Default workload: R-MAT scale 20
+(1,048,576 vertices, 16,777,216 edges, a=.57 b=.19 c=.19 d=.05, w~U[1,100],
+source = max out-degree vertex), batches of 1% of m (83,886 deletions of
+existing edges + 83,886 R-MAT insertions).
+
+Printed JSON line (rank 0): value = edge updates per second over the K timed
+steps (inputs resident in HBM, L2 flushed between steps, CUDA events on the
+graph's stream, max over ranks); e2e = the same through host buffers with the
+H2D copy of the batch and the D2H read of all distances inside the timed
+region; static = from-scratch GPU SSSP (sp_sssp_init) on the updated graph;
+roofline = the dominant kernel's algorithmic bytes / its event-timed duration
+against the measured HBM copy bandwidth; cpu_baseline = the CPU oracle
+(apply + Dijkstra) on a bounded sample of the same batches.
+
+--impl reference times the CPU oracle as the reference arm.
+--gpus N under torchrun runs N independent replicas (one graph per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2507_11094_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "dyn-SSSP edge updates/s & p50/p99 batch latency vs GPU static recompute"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20",
+                    help="rmat20 | rmat<scale> | er1k | grid<side>-<pct> (e.g. grid4096-1)")
+    ap.add_argument("--batch-pct", type=float, default=None)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--static-reps", type=int, default=3)
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def make_workload(name: str, seed: int, pct: float | None):
+    if name == "er1k":
+        return wl.tiny_er(seed=seed), {"n": 1024, "m": 8192}
+    if name.startswith("rmat"):
+        scale = int(name[4:] or 20)
+        frac = (pct if pct is not None else 1.0) / 100.0
+        W = wl.rmat(scale=scale, batch_frac=frac, seed=seed)
+        return W, {"scale": scale, "edge_factor": 16}
+    if name.startswith("grid"):
+        side, p = name[4:].split("-")
+        frac = (pct if pct is not None else float(p)) / 100.0
+        W = wl.grid(int(side), int(side), batch_frac=frac, seed=seed)
+        return W, {"rows": int(side), "cols": int(side)}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(W, batches, budget_s: float, min_batches: int = 2):
+    """Time the CPU oracle (batch apply + from-scratch Dijkstra, one core) on
+    as many of `batches` as fit in about budget_s seconds."""
+    import oracle
+    g = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    times, sizes = [], []
+    t_start = time.perf_counter()
+    for i, b in enumerate(batches):
+        t0 = time.perf_counter()
+        g.apply(b)
+        g.dijkstra(W.source)
+        times.append(time.perf_counter() - t0)
+        sizes.append(b.size)
+        if i + 1 >= min_batches and time.perf_counter() - t_start > budget_s:
+            break
+    g.close()
+    return times, sizes
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    W, cfg = make_workload(args.workload, args.seed, args.batch_pct)
+    batches = [W.batch(k) for k in range(args.warmup + args.steps)]
+    g = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    g.dijkstra(W.source)
+    lat, ups = [], 0
+    for k, b in enumerate(batches):
+        t0 = time.perf_counter()
+        g.apply(b)
+        g.dijkstra(W.source)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            lat.append(dt)
+            ups += b.size
+    value = ups / sum(lat)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edge_updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(lat) / len(lat), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": W.name, **cfg, "n": W.n, "m": W.m,
+                   "batch_updates": W.batch_edges, "source": W.source},
+        "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+        "cpu_baseline": {"value": value, "unit": "edge_updates/s", "cores": 1,
+                         "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"{len(lat)} full batches of {W.batch_edges} updates: "
+                                   "oracle batch apply + binary-heap Dijkstra from scratch"},
+        "e2e": {"value": value, "unit": "edge_updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import torch
+
+    from paper_2507_11094_gb300 import sp
+
+    ws, rank, local = dist_env()
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sp.load(build_if_missing=True)
+
+    seed = args.seed + rank
+    W, cfg = make_workload(args.workload, seed, args.batch_pct)
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        g = sp.Graph(W.n, W.row_off, W.col, W.w, stream=stream)
+    g.sssp_init(W.source)
+
+    tree = W.tree_fraction > 0
+    # device leg batches (generated against the evolving edge set; tree-biased
+    # deletions use the current distances read back between generations)
+    def gen(k, dist):
+        return W.batch(k, dist=dist if tree else None)
+
+    d_cur = g.get_dist() if tree else None
+    dev_batches = []
+    # generate all device-leg batches first (the stream tracks the edge set);
+    # tree-biased workloads need distances, so they are generated one step ahead
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def to_dev(b):
+        return [torch.from_numpy(x).to(dev) for x in
+                (b.del_src, b.del_dst, b.add_src, b.add_dst, b.add_w)]
+
+    lat_ms, lib_ms, sizes, stats_all, launches = [], [], [], [], 0
+    wall_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if not tree:
+        dev_batches = [to_dev(gen(k, None)) for k in range(Wm + K)]
+        sizes_all = [int(t[0].numel() + t[2].numel()) for t in dev_batches]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    with clocks:
+        for k in range(Wm + K):
+            if tree:
+                b = gen(k, g.get_dist())
+                tb = to_dev(b)
+                size = b.size
+            else:
+                tb = dev_batches[k]
+                size = sizes_all[k]
+            flush.fill_(k)                      # evict L2 between steps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev0.record(stream)
+            st = g.apply_batch(*tb, stats=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            t1 = time.perf_counter()
+            if k >= Wm:
+                lat_ms.append(ev0.elapsed_time(ev1))
+                lib_ms.append(st.ms_total)
+                wall_ms.append(1e3 * (t1 - t0))
+                sizes.append(size)
+                stats_all.append(st.as_dict())
+                launches += st.n_launches
+    torch.cuda.synchronize()
+    total_ms = sum(lat_ms)
+    ups = sum(sizes)
+
+    # from-scratch GPU SSSP on the updated graph (the comparator)
+    static_ms = []
+    for _ in range(max(1, args.static_reps)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sst = g.sssp_init(W.source, stats=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        static_ms.append(ev0.elapsed_time(ev1))
+
+    # end to end through host buffers: H2D of the batch + D2H of all distances
+    e2e_batches = [gen(Wm + K + k, g.get_dist() if tree else None) for k in range(1 + K)]
+    pinned = []
+    for b in e2e_batches:
+        arrs = []
+        for x in (b.del_src, b.del_dst, b.add_src, b.add_dst, b.add_w):
+            t = torch.empty(x.size, dtype=torch.int32, pin_memory=True)
+            t.numpy()[:] = x
+            arrs.append(t.numpy())
+        pinned.append(arrs)
+    dist_host = torch.empty(W.n, dtype=torch.int32, pin_memory=True).numpy()
+    e2e_ms, e2e_sizes = [], []
+    for k, arrs in enumerate(pinned):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.apply_batch(*arrs)
+        lib = sp.load()
+        import ctypes
+        rc = lib.sp_get_dist(g._h, dist_host.ctypes.data_as(ctypes.c_void_p), None, 0)
+        assert rc == 0
+        ev1.record(stream)
+        ev1.synchronize()
+        if k >= 1:
+            e2e_ms.append(ev0.elapsed_time(ev1))
+            e2e_sizes.append(e2e_batches[k].size)
+    bi = sum(a.nbytes for a in pinned[1]) if len(pinned) > 1 else 0
+    bo = dist_host.nbytes
+
+    # aggregate over ranks: max time, summed work
+    if pg:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([ups, sum(e2e_sizes)], dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ms_all, e2e_ms_all = float(t[0]), float(t[1])
+        ups_all, e2e_ups_all = float(u[0]), float(u[1])
+    else:
+        total_ms_all, e2e_ms_all = total_ms, sum(e2e_ms)
+        ups_all, e2e_ups_all = ups, sum(e2e_sizes)
+
+    # dominant kernel: the phase with the largest device time over the steps
+    phases = list(sp.PHASES)
+    ph_ms = {p: sum(s["ms_phase"][p] for s in stats_all) for p in phases}
+    ph_bytes = {p: sum(s["alg_bytes"][p] for s in stats_all) for p in phases}
+    dom = max(phases, key=lambda p: ph_ms[p])
+    peak, peak_kind = measured_peaks()
+    achieved = ph_bytes[dom] / (ph_ms[dom] * 1e-3) / 1e9 if ph_ms[dom] > 0 else 0.0
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        with open(tf) as f:
+            tj = json.load(f)
+        ent = tj.get(W.name, {}).get(dom)
+        if ent and ent.get("valid", False):
+            traffic = ent["bytes_per_launch"]
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            import oracle
+            oracle.build()
+            Wc, _ = make_workload(args.workload, seed, args.batch_pct)
+            sample = [Wc.batch(k) for k in range(4)] if not tree else []
+            if sample:
+                times, szs = oracle_sample(Wc, sample, budget_s=12.0)
+                cpu = {"value": sum(szs) / sum(times), "unit": "edge_updates/s", "cores": 1,
+                       "kind": "oracle", "cpu": cpu_model(), "nproc": os.cpu_count(),
+                       "sample": f"first {len(times)} batches of the same workload "
+                                 f"({szs[0]} updates each): oracle batch apply + "
+                                 "binary-heap Dijkstra from scratch, single-threaded"}
+        step_ms = total_ms_all / max(1, len(lat_ms))
+        line = {
+            "metric": METRIC,
+            "value": ups_all / (total_ms_all * 1e-3),
+            "unit": "edge_updates/s",
+            "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": W.name, **cfg, "n": W.n, "m": W.m,
+                       "batch_updates": W.batch_edges, "source": W.source,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "p50_ms": percentile(lat_ms, 50), "p99_ms": percentile(lat_ms, 99),
+            "wall_p50_ms": percentile(wall_ms, 50), "wall_p99_ms": percentile(wall_ms, 99),
+            "static": {"ms_p50": percentile(static_ms, 50), "ms_min": min(static_ms),
+                       "rounds": sst.rounds_push,
+                       "speedup_dynamic_vs_static": percentile(static_ms, 50) /
+                       percentile(lat_ms, 50)},
+            "e2e": {"value": e2e_ups_all / (e2e_ms_all * 1e-3) if e2e_ms_all else None,
+                    "unit": "edge_updates/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "p50_ms": percentile(e2e_ms, 50),
+                    "p99_ms": percentile(e2e_ms, 99)},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "traffic": traffic},
+            "phase_ms": {p: ph_ms[p] / len(lat_ms) for p in phases},
+            "phase_alg_bytes": {p: ph_bytes[p] / len(lat_ms) for p in phases},
+            "per_step": {
+                "affected": statistics.mean(s["affected"] for s in stats_all),
+                "rounds_push": statistics.mean(s["rounds_push"] for s in stats_all),
+                "rounds_inval": statistics.mean(s["rounds_inval"] for s in stats_all),
+                "relaxed_edges": statistics.mean(s["relaxed_edges"] for s in stats_all),
+                "rows_touched": statistics.mean(s["rows_touched"] for s in stats_all),
+                "regrows": sum(s["regrows"] for s in stats_all),
+            },
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    g.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * sp.h -- C ABI of libsp: dynamic single-source shortest paths on one GPU.
+ *
+ * The library keeps a weighted directed graph resident on the device as a
+ * forward and a reverse CSR with slack in every row, together with the
+ * distance and parent of every vertex from one source.  A batch of edge
+ * deletions and insertions is merged into both CSRs and the distances are
+ * repaired incrementally, as the DynSSSP driver of the paper does (Section 3.2
+ * "Language Overview with a Motivating Example: Dynamic SSSP"; Appendix,
+ * DynSSSP/Incremental/Decremental listings): deletions first, then
+ * insertions.  All arithmetic is exact integer.
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes: every function returns an sp_status; no C++ exception
+ *     crosses the ABI.  sp_status_str() names a code.
+ *   - Ownership: the library copies every input array during the call; the
+ *     caller keeps its buffers and may reuse them as soon as the call returns.
+ *     The sp_graph handle and all device memory it holds belong to the
+ *     library until sp_graph_destroy().
+ *   - Host or device pointers: a flag on each call says whether the arrays
+ *     are host memory (pageable or pinned) or device memory of the graph's
+ *     device.  Device arrays must stay valid until the call returns.
+ *   - Streams: every call is ordered on the CUDA stream given at creation and
+ *     returns only after its work on that stream is complete (the status it
+ *     returns is the device's).  A handle is not thread-safe; distinct
+ *     handles may be used concurrently from different threads and streams.
+ *   - Validation happens before any change: a batch that fails validation
+ *     (SP_EINVAL) leaves the graph exactly as it was.
+ *   - A device-side bound being hit (SP_ETIMEOUT) or a distance that does not
+ *     fit (SP_ERANGE) during a repair leaves distances unspecified: the graph
+ *     is then in SP_ESTATE until sp_sssp_init() is called again.  The edge set
+ *     is always consistent with the batches that returned SP_OK, SP_ERANGE or
+ *     SP_ETIMEOUT (the CSR merge completes before any repair starts).
+ */
+#ifndef SP_H
+#define SP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp_graph sp_graph;   /* opaque, owned by the library */
+
+typedef enum {
+    SP_OK = 0,
+    SP_EINVAL = -1,        /* bad argument or batch (ids, weights, sizes)   */
+    SP_ENOMEM = -2,        /* a device or host allocation failed            */
+    SP_ERANGE = -3,        /* a finite distance reached SP_INF              */
+    SP_ESTATE = -4,        /* call not valid in this state (e.g. no source) */
+    SP_ECUDA = -5,         /* a CUDA runtime call failed                    */
+    SP_ETIMEOUT = -6,      /* a device-side round cap or wait bound was hit */
+    SP_ENOMEM_BUDGET = -7  /* refused: the graph would exceed a memory budget */
+} sp_status;
+
+/* Distance of an unreachable vertex: INT_MAX/2, the value the appendix's
+ * OnDelete and Decremental listings store (so SP_INF + w cannot overflow). */
+#define SP_INF 1073741823
+/* Largest accepted edge weight; weights must be 1 <= w <= SP_WMAX. */
+#define SP_WMAX (1 << 20)
+/* Number of per-phase slots in sp_batch_stats. */
+#define SP_NPHASE 8
+
+/* Phases of one batch, in launch order (indexes of ms_phase / alg_bytes). */
+enum {
+    SP_PH_SORT = 0,      /* validate + sort the batch by (row, col)           */
+    SP_PH_COUNT = 1,     /* per touched row: applied/absent/present, new size */
+    SP_PH_MERGE = 2,     /* OnDelete mark + merge into forward/reverse CSR    */
+    SP_PH_INVAL = 3,     /* invalidate shortest-path subtrees (Decremental 1) */
+    SP_PH_PULL = 4,      /* pull repair of invalidated vertices (Decremental 2)*/
+    SP_PH_ADD = 5,       /* relax inserted edges (OnAdd)                      */
+    SP_PH_PUSH = 6,      /* push fixedPoint (Incremental)                     */
+    SP_PH_FINISH = 7     /* status + counters back to the host                */
+};
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc()
+ * returns device memory of at least `bytes` bytes, 256-byte aligned, or NULL;
+ * free() releases it.  `stream` is the graph's cudaStream_t.  With a NULL
+ * allocator the library uses cudaMallocAsync/cudaFreeAsync on that stream. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} sp_allocator;
+
+/* Counters and timings of one sp_apply_batch (or sp_sssp_init) call. */
+typedef struct {
+    int64_t n_del_applied;   /* deletions of present edges                  */
+    int64_t n_del_absent;    /* deletions of absent edges (no-ops)          */
+    int64_t n_add_applied;   /* insertions of new edges                     */
+    int64_t n_add_present;   /* insertions of present edges (no-ops)        */
+    int64_t affected;        /* vertices invalidated by deletions           */
+    int64_t seeds;           /* vertices in the first push frontier         */
+    int64_t relaxed_edges;   /* edges scanned by the push loop              */
+    int64_t improved;        /* successful distance decreases in the loop   */
+    int64_t rows_touched;    /* forward + reverse rows rewritten            */
+    int64_t rows_relocated;  /* rows moved to the spare pool                */
+    int32_t rounds_inval;    /* rounds of the subtree invalidation          */
+    int32_t rounds_push;     /* rounds of the push fixedPoint               */
+    int32_t n_launches;      /* kernels launched by this call               */
+    int32_t regrows;         /* times the call grew a buffer and re-ran     */
+    int64_t alg_bytes[SP_NPHASE]; /* algorithmic bytes moved per phase      */
+    float ms_phase[SP_NPHASE];    /* device time per phase (CUDA events)    */
+    float ms_total;               /* device time of the whole call          */
+} sp_batch_stats;
+
+/* Read-only facts about a graph. */
+typedef struct {
+    int32_t n;
+    int32_t source;          /* -1 before sp_sssp_init                      */
+    int64_t m;               /* current number of edges                     */
+    int64_t cap_fwd;         /* edge slots of the forward store (all rows + pool) */
+    int64_t cap_rev;
+    int64_t pool_used_fwd;   /* spare-pool slots taken by relocated rows    */
+    int64_t pool_used_rev;
+    int64_t device_bytes;    /* device memory held by the handle            */
+    int32_t state;           /* 0 = no distances, 1 = valid, 2 = SP_ESTATE  */
+    int32_t num_sms;
+} sp_graph_info;
+
+/*
+ * Create a graph from a CSR: row_off[n+1] (int64, row_off[0] = 0,
+ * non-decreasing, row_off[n] = m), col[m] (destinations, 0 <= col < n) and
+ * w[m] (1 <= w <= SP_WMAX).  Rows need not be sorted; duplicate edges are
+ * rejected with SP_EINVAL.  `slack` (>= 0, e.g. 0.25) is the fraction of
+ * spare slots reserved per row.  `alloc` may be NULL.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out receives the
+ * handle.  The graph lives on the device that is current at the call.
+ * Graph storage: the CSR of Section 3.5 ("Modified Graph Representation"),
+ * with per-row slack in place of the paper's diff-CSR.
+ */
+sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off,
+                          const int32_t *col, const int32_t *w,
+                          int inputs_on_device, float slack,
+                          const sp_allocator *alloc, void *cuda_stream,
+                          sp_graph **out);
+
+/* Release every resource of g (NULL is accepted). */
+sp_status sp_graph_destroy(sp_graph *g);
+
+/*
+ * Compute distances and parents from `source` from scratch (the appendix's
+ * staticSSSP: dist = INF and parent = -1 everywhere, then a fixedPoint of
+ * Min relaxations seeded by the source).  Also the from-scratch comparator.
+ * stats may be NULL.  SP_EINVAL if source is out of range.
+ */
+sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats);
+
+/*
+ * Apply one batch: deletions (del_src[i] -> del_dst[i]) then insertions
+ * (add_src[i] -> add_dst[i] with weight add_w[i]), and repair distances and
+ * parents (DynSSSP driver, Section 3.2 and Appendix).  Either count may be 0
+ * (the matching pointers may then be NULL).  Semantics of cases the paper
+ * leaves open:
+ *   - deleting an absent edge, or deleting one edge twice, is a counted no-op;
+ *   - inserting an edge present after the deletions is a counted no-op and
+ *     keeps the old weight; among repeated insertions of one edge the smallest
+ *     weight wins;
+ *   - an edge deleted and inserted in one batch ends up with the new weight.
+ * Requires a prior successful sp_sssp_init (else SP_ESTATE).  SP_EINVAL (ids
+ * out of range, w outside [1, SP_WMAX], negative counts) leaves the graph
+ * unchanged.  stats may be NULL; with stats the call also records per-phase
+ * CUDA events.
+ */
+sp_status sp_apply_batch(sp_graph *g,
+                         int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                         int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                         const int32_t *add_w,
+                         int inputs_on_device, sp_batch_stats *stats);
+
+/*
+ * Copy distances (dist[n]; SP_INF = unreachable) and, if parent != NULL,
+ * parents (parent[n]; -1 for the source and unreachable vertices) out.
+ * SP_ESTATE if no valid distances exist.
+ */
+sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent,
+                      int out_on_device);
+
+/* Number of edges now in the graph. */
+sp_status sp_graph_num_edges(const sp_graph *g, int64_t *m);
+
+/*
+ * Export the current edge set as a row-sorted CSR: row_off[n+1], col[m],
+ * w[m] with m from sp_graph_num_edges.  `reverse` = 1 exports the reverse
+ * (transpose) store instead: row v lists the sources u of edges u -> v with
+ * their weights.  Used for checkpoints and for store tests.
+ */
+sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off,
+                        int32_t *col, int32_t *w, int out_on_device);
+
+/* Fill *info. */
+sp_status sp_graph_info_get(const sp_graph *g, sp_graph_info *info);
+
+/*
+ * Device-side bounds of the repair loops: max_rounds caps the rounds of each
+ * fixedPoint loop (0 = the Bellman-Ford bound n + 1); wait_ns bounds every
+ * grid-barrier wait in nanoseconds (0 = 2 s).  Hitting either returns
+ * SP_ETIMEOUT.  Meant for tests of the timeout path and for latency limits.
+ */
+sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns);
+
+/* Static name of a status code. */
+const char *sp_status_str(sp_status s);
+
+/* Library version as "major.minor.patch". */
+const char *sp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP_H */

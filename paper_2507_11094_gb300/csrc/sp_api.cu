@@ -1,0 +1,562 @@
+// sp_api.cu -- the C ABI (include/sp.h): handle lifetime, argument checks,
+// buffer management and the order of launches for one call.
+//
+// One sp_apply_batch is one stream-ordered sequence of kernels with a single
+// device-to-host copy of the control block at the end (the paper's CUDA
+// backend instead copies a `finished` flag to the host every fixedPoint
+// iteration, Section 5.3).
+#include <algorithm>
+#include <new>
+
+#include "sp_graph.cuh"
+
+using sp::Ctl;
+using sp::u32;
+using sp::u64;
+
+namespace sp {
+
+void *Alloc::get(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void *p = nullptr;
+  if (has_user) {
+    p = user.alloc(user.ctx, bytes, (void *)stream);
+  } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) bytes_held += (long long)bytes;
+  return p;
+}
+
+void Alloc::put(void *p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (has_user) user.free(user.ctx, p, bytes, (void *)stream);
+  else cudaFreeAsync(p, stream);
+  bytes_held -= (long long)bytes;
+}
+
+sp_status csr_validate(sp_graph *g, const long long *row_off_d, const int *col_d,
+                       const int *w_d, long long m, int *launches);
+
+}  // namespace sp
+
+namespace {
+
+// Buffers sized by the batch: grown (never shrunk) when a larger batch comes.
+template <typename T>
+bool regrow(sp_graph *g, T *&p, long long &cap_now, long long need, size_t elem) {
+  (void)elem;
+  if (need <= cap_now && p) return true;
+  g->al.put(p, (size_t)cap_now * sizeof(T));
+  p = (T *)g->al.get((size_t)need * sizeof(T));
+  cap_now = p ? need : 0;
+  return p != nullptr;
+}
+
+sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
+  sp::BatchBufs &b = g->bb;
+  const long long want = std::max<long long>(ni + 1, 1024);
+  if (want > b.cap_items) {
+    long long c = std::max(want, b.cap_items * 2);
+    auto &al = g->al;
+    long long old = b.cap_items;
+    al.put(b.keys, old * 8); al.put(b.keys_alt, old * 8);
+    al.put(b.vals, old * 4); al.put(b.vals_alt, old * 4);
+    al.put(b.flags, old); al.put(b.itemv, old * 8); al.put(b.item_pref, old * 8);
+    al.put(b.head, old * 4); al.put(b.head_scan, old * 4);
+    al.put(b.seg, old * sizeof(sp::Seg));
+    al.put(b.small_list, old * 4); al.put(b.large_list, old * 4);
+    al.put(b.tmp, b.tmp_bytes);
+    b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
+    b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
+    b.flags = (unsigned char *)al.get(c);
+    b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
+    b.head = (u32 *)al.get(c * 4); b.head_scan = (u32 *)al.get(c * 4);
+    b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
+    b.small_list = (u32 *)al.get(c * 4); b.large_list = (u32 *)al.get(c * 4);
+    b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
+    b.tmp = al.get(b.tmp_bytes);
+    b.cap_items = c;
+    if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
+        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.small_list || !b.large_list ||
+        !b.tmp) {
+      return SP_ENOMEM;
+    }
+  }
+  if (nb_host > b.cap_in) {
+    long long c = std::max(nb_host, b.cap_in * 2);
+    long long old = b.cap_in;
+    auto &al = g->al;
+    al.put(b.in_del_src, old * 4); al.put(b.in_del_dst, old * 4);
+    al.put(b.in_add_src, old * 4); al.put(b.in_add_dst, old * 4); al.put(b.in_add_w, old * 4);
+    b.in_del_src = (int *)al.get(c * 4); b.in_del_dst = (int *)al.get(c * 4);
+    b.in_add_src = (int *)al.get(c * 4); b.in_add_dst = (int *)al.get(c * 4);
+    b.in_add_w = (int *)al.get(c * 4);
+    b.cap_in = c;
+    if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
+      return SP_ENOMEM;
+  }
+  if (!b.scratch) {
+    long long c = std::max<long long>(1 << 20, g->m / 8);
+    b.scratch = (int2 *)g->al.get((size_t)c * sizeof(int2));
+    if (!b.scratch) return SP_ENOMEM;
+    b.scratch_cap = c;
+  }
+  return SP_OK;
+}
+
+void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int regrows,
+                long long ni, bool timed) {
+  if (!st) return;
+  st->n_del_applied = (int64_t)c.del_applied;
+  st->n_del_absent = (int64_t)c.del_absent;
+  st->n_add_applied = (int64_t)c.add_applied;
+  st->n_add_present = (int64_t)c.add_present;
+  st->affected = (int64_t)c.affected;
+  st->seeds = (int64_t)c.seeds;
+  st->relaxed_edges = (int64_t)c.relaxed;
+  st->improved = (int64_t)c.improved;
+  st->rows_touched = (int64_t)c.rows_touched;
+  st->rows_relocated = (int64_t)c.rows_relocated;
+  st->rounds_inval = (int32_t)c.rounds_inval;
+  st->rounds_push = (int32_t)c.rounds_push;
+  st->n_launches = launches;
+  st->regrows = regrows;
+  // Algorithmic bytes: what each phase must move, counted from what it did.
+  const int passes = (2 * g->bits + 2 + 7) / 8;
+  const long long nb = ni / 2;
+  st->alg_bytes[SP_PH_SORT] = ni ? (int64_t)(nb * 20 + ni * 12 + (long long)passes * ni * 24) : 0;
+  st->alg_bytes[SP_PH_COUNT] = (int64_t)(ni * 21 + (long long)c.rows_touched * 16);
+  st->alg_bytes[SP_PH_MERGE] = (int64_t)(c.merge_slots * 8 + c.rows_touched * 32 + ni * 21);
+  st->alg_bytes[SP_PH_INVAL] =
+      (int64_t)(c.affected * (16 + 8 + 8 + 4) + c.inval_edges * 16);
+  st->alg_bytes[SP_PH_PULL] = (int64_t)(c.affected * 16 + c.pull_edges * 16 + c.seeds * 20);
+  st->alg_bytes[SP_PH_ADD] = (int64_t)(c.add_applied * (12 + 16));
+  st->alg_bytes[SP_PH_PUSH] =
+      (int64_t)(c.push_vertices * (4 + 16 + 8) + c.relaxed * 16 + c.improved * 8 +
+                c.enqueued * (4 + 4 + 4));
+  st->alg_bytes[SP_PH_FINISH] = (int64_t)sizeof(Ctl);
+  for (int i = 0; i < SP_NPHASE; ++i) st->ms_phase[i] = 0.f;
+  st->ms_total = 0.f;
+  if (timed) {
+    for (int i = 0; i < SP_NPHASE; ++i)
+      cudaEventElapsedTime(&st->ms_phase[i], g->ev[i], g->ev[i + 1]);
+    cudaEventElapsedTime(&st->ms_total, g->ev[0], g->ev[SP_NPHASE]);
+  }
+}
+
+void rec(sp_graph *g, bool timed, int i) {
+  if (timed) cudaEventRecord(g->ev[i], g->stream);
+}
+
+sp_status read_ctl(sp_graph *g) {
+  cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream);
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  return SP_OK;
+}
+
+void set_limits(sp_graph *g) {
+  g->lim.max_rounds = g->max_rounds_user > 0 ? (u32)g->max_rounds_user
+                                             : (u32)std::min<long long>((long long)g->n + 1, 0x7fffffffLL);
+  g->lim.wait_ns = g->wait_ns_user > 0 ? (u64)g->wait_ns_user : 2000000000ull;
+}
+
+sp_status status_of_repair(sp_graph *g, const Ctl &c) {
+  if (c.bad) {
+    g->state = 2;
+    return SP_ECUDA;
+  }
+  if (c.timeout) {
+    g->state = 2;
+    return SP_ETIMEOUT;
+  }
+  if (c.range_err) {
+    g->state = 2;
+    return SP_ERANGE;
+  }
+  return SP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sp_status_str(sp_status s) {
+  switch (s) {
+    case SP_OK: return "SP_OK";
+    case SP_EINVAL: return "SP_EINVAL: invalid argument";
+    case SP_ENOMEM: return "SP_ENOMEM: allocation failed";
+    case SP_ERANGE: return "SP_ERANGE: a distance does not fit below SP_INF";
+    case SP_ESTATE: return "SP_ESTATE: no valid distances (call sp_sssp_init)";
+    case SP_ECUDA: return "SP_ECUDA: CUDA runtime error";
+    case SP_ETIMEOUT: return "SP_ETIMEOUT: device-side round cap or wait bound hit";
+    case SP_ENOMEM_BUDGET: return "SP_ENOMEM_BUDGET: over the memory budget";
+  }
+  return "unknown sp_status";
+}
+
+const char *sp_version(void) { return "0.1.0"; }
+
+sp_status sp_graph_destroy(sp_graph *g) {
+  if (!g) return SP_OK;
+  cudaStreamSynchronize(g->stream);
+  auto &al = g->al;
+  auto &b = g->bb;
+  const long long n = g->n;
+  long long c = b.cap_items;
+  al.put(b.keys, c * 8); al.put(b.keys_alt, c * 8);
+  al.put(b.vals, c * 4); al.put(b.vals_alt, c * 4);
+  al.put(b.flags, c); al.put(b.itemv, c * 8); al.put(b.item_pref, c * 8);
+  al.put(b.head, c * 4); al.put(b.head_scan, c * 4);
+  al.put(b.seg, c * sizeof(sp::Seg));
+  al.put(b.small_list, c * 4); al.put(b.large_list, c * 4);
+  al.put(b.tmp, b.tmp_bytes);
+  c = b.cap_in;
+  al.put(b.in_del_src, c * 4); al.put(b.in_del_dst, c * 4);
+  al.put(b.in_add_src, c * 4); al.put(b.in_add_dst, c * 4); al.put(b.in_add_w, c * 4);
+  al.put(b.scratch, (size_t)b.scratch_cap * sizeof(int2));
+  al.put(g->fwd.row, n * sizeof(sp::RowMeta));
+  al.put(g->fwd.adj, (size_t)g->fwd.slots * sizeof(int2));
+  al.put(g->rev.row, n * sizeof(sp::RowMeta));
+  al.put(g->rev.adj, (size_t)g->rev.slots * sizeof(int2));
+  al.put(g->s, n * 8);
+  al.put(g->qflag, n * 4);
+  al.put(g->qlight[0], n * 4); al.put(g->qlight[1], n * 4);
+  al.put(g->qheavy[0], n * 8); al.put(g->qheavy[1], n * 8);
+  al.put(g->alist, n * 4);
+  al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
+  al.put(g->ctl, sizeof(Ctl));
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
+  for (auto &e : g->ev)
+    if (e) cudaEventDestroy(e);
+  cudaStreamSynchronize(g->stream);
+  delete g;
+  return SP_OK;
+}
+
+sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                          const int32_t *w, int inputs_on_device, float slack,
+                          const sp_allocator *alloc, void *cuda_stream, sp_graph **out) {
+  if (!out) return SP_EINVAL;
+  *out = nullptr;
+  if (n <= 0 || m < 0 || !row_off || (m > 0 && (!col || !w)) || !(slack >= 0.f) || slack > 16.f)
+    return SP_EINVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SP_EINVAL;
+  sp_graph *g = new (std::nothrow) sp_graph();
+  if (!g) return SP_ENOMEM;
+  g->n = n;
+  g->bits = sp::id_bits(n);
+  g->slack = slack;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->al.stream = g->stream;
+  if (alloc) {
+    g->al.user = *alloc;
+    g->al.has_user = true;
+  }
+  if (cudaGetDevice(&g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return SP_ECUDA;
+  }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+  g->loop_blocks_push = sp::loop_blocks(0, g->num_sms);
+  g->loop_blocks_inval = sp::loop_blocks(1, g->num_sms);
+  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0) {
+    delete g;
+    return SP_ECUDA;
+  }
+  for (auto &e : g->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      sp_graph_destroy(g);
+      return SP_ECUDA;
+    }
+  if (cudaMallocHost(&g->ctl_host, sizeof(Ctl)) != cudaSuccess) {
+    cudaGetLastError();
+    g->ctl_host = nullptr;
+    sp_graph_destroy(g);
+    return SP_ENOMEM;
+  }
+  g->ctl = (Ctl *)g->al.get(sizeof(Ctl));
+  const size_t nn = (size_t)n;
+  g->s = (u64 *)g->al.get(nn * 8);
+  g->qflag = (u32 *)g->al.get(nn * 4);
+  g->qlight[0] = (u32 *)g->al.get(nn * 4);
+  g->qlight[1] = (u32 *)g->al.get(nn * 4);
+  g->qheavy[0] = (int2 *)g->al.get(nn * 8);
+  g->qheavy[1] = (int2 *)g->al.get(nn * 8);
+  g->alist = (u32 *)g->al.get(nn * 4);
+  g->out_dist = (int *)g->al.get(nn * 4);
+  g->out_parent = (int *)g->al.get(nn * 4);
+  if (!g->ctl || !g->s || !g->qflag || !g->qlight[0] || !g->qlight[1] || !g->qheavy[0] ||
+      !g->qheavy[1] || !g->alist || !g->out_dist || !g->out_parent) {
+    sp_graph_destroy(g);
+    return SP_ENOMEM;
+  }
+  cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream);
+  cudaMemsetAsync(g->qflag, 0, nn * 4, g->stream);
+  int launches = 0;
+  sp::launch_ctl_reset(g, 1, &launches);
+
+  // inputs on the device
+  const long long *ro_d = (const long long *)row_off;
+  const int *col_d = col, *w_d = w;
+  void *tmp_in = nullptr;
+  size_t tmp_in_bytes = 0;
+  if (!inputs_on_device) {
+    tmp_in_bytes = (nn + 1) * 8 + (size_t)std::max<int64_t>(m, 1) * 8 + 512;
+    tmp_in = g->al.get(tmp_in_bytes);
+    if (!tmp_in) {
+      sp_graph_destroy(g);
+      return SP_ENOMEM;
+    }
+    long long *ro = (long long *)tmp_in;
+    int *cc = (int *)(((uintptr_t)(ro + nn + 1) + 255) & ~(uintptr_t)255);
+    int *ww = cc + std::max<int64_t>(m, 1);
+    cudaMemcpyAsync(ro, row_off, (nn + 1) * 8, cudaMemcpyHostToDevice, g->stream);
+    if (m > 0) {
+      cudaMemcpyAsync(cc, col, (size_t)m * 4, cudaMemcpyHostToDevice, g->stream);
+      cudaMemcpyAsync(ww, w, (size_t)m * 4, cudaMemcpyHostToDevice, g->stream);
+    }
+    ro_d = ro;
+    col_d = cc;
+    w_d = ww;
+  }
+  sp_status rc = sp::csr_validate(g, ro_d, col_d, w_d, m, &launches);
+  if (rc == SP_OK) rc = sp::store_build(g, &g->fwd, ro_d, col_d, w_d, m, 0, &launches);
+  if (rc == SP_OK) rc = sp::store_build(g, &g->rev, ro_d, col_d, w_d, m, 1, &launches);
+  if (tmp_in) g->al.put(tmp_in, tmp_in_bytes);
+  if (rc == SP_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) rc = SP_ECUDA;
+  if (rc != SP_OK) {
+    cudaGetLastError();
+    sp_graph_destroy(g);
+    return rc;
+  }
+  g->m = m;
+  set_limits(g);
+  *out = g;
+  return SP_OK;
+}
+
+sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns) {
+  if (!g || max_rounds < 0 || wait_ns < 0) return SP_EINVAL;
+  g->max_rounds_user = max_rounds;
+  g->wait_ns_user = wait_ns;
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats) {
+  if (!g) return SP_EINVAL;
+  if (source < 0 || source >= g->n) return SP_EINVAL;
+  const bool timed = stats != nullptr;
+  int launches = 0;
+  for (int i = 0; i < SP_NPHASE; ++i) rec(g, timed, i);   // empty phases
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_init(g, source, &launches);
+  cudaError_t e = sp::launch_push(g, &launches);
+  rec(g, timed, SP_NPHASE - 1);
+  sp::launch_finish(g, &launches);
+  rec(g, timed, SP_NPHASE);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(g->stream);
+    g->state = 2;
+    return SP_ECUDA;
+  }
+  sp_status rc = read_ctl(g);
+  if (rc != SP_OK) {
+    g->state = 2;
+    return rc;
+  }
+  const Ctl &c = *g->ctl_host;
+  fill_stats(g, c, stats, launches, 0, 0, timed);
+  if (stats) {
+    // an init has only the push phase
+    for (int i = 0; i < SP_NPHASE; ++i)
+      if (i != SP_PH_PUSH) stats->alg_bytes[i] = 0;
+    stats->alg_bytes[SP_PH_PUSH] += (int64_t)g->n * 8;  // the reset of all states
+  }
+  rc = status_of_repair(g, c);
+  if (rc == SP_OK) {
+    g->state = 1;
+    g->source = source;
+  } else {
+    g->source = source;
+  }
+  return rc;
+}
+
+sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                         const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                         const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
+                         sp_batch_stats *stats) {
+  if (!g) return SP_EINVAL;
+  if (n_del < 0 || n_add < 0) return SP_EINVAL;
+  if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
+    return SP_EINVAL;
+  if (n_del + n_add > (1LL << 30)) return SP_EINVAL;
+  if (g->state != 1) return SP_ESTATE;
+  const long long nb = n_del + n_add, ni = 2 * nb;
+  const bool timed = stats != nullptr;
+  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
+  if (rc != SP_OK) return rc;
+  auto &b = g->bb;
+  const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
+  rec(g, timed, 0);
+  if (!inputs_on_device) {
+    cudaStream_t s = g->stream;
+    if (n_del) {
+      cudaMemcpyAsync(b.in_del_src, del_src, n_del * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_del_dst, del_dst, n_del * 4, cudaMemcpyHostToDevice, s);
+    }
+    if (n_add) {
+      cudaMemcpyAsync(b.in_add_src, add_src, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_dst, add_dst, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_w, add_w, n_add * 4, cudaMemcpyHostToDevice, s);
+    }
+    ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
+  }
+  int launches = 0, regrows = 0;
+  for (int attempt = 0;; ++attempt) {
+    launches = 0;
+    if (attempt) rec(g, timed, 0);
+    sp::launch_ctl_reset(g, 0, &launches);
+    sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
+    sp::launch_segments(g, ni, &launches);
+    rec(g, timed, 1);
+    sp::launch_count(g, ni, &launches);
+    rec(g, timed, 2);
+    sp::launch_merge(g, ni, &launches);
+    rec(g, timed, 3);
+    cudaError_t e = cudaSuccess;
+    if (n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, &launches);
+    rec(g, timed, 4);
+    if (n_del > 0) sp::launch_pull(g, &launches);
+    rec(g, timed, 5);
+    sp::launch_add(g, ni, &launches);
+    rec(g, timed, 6);
+    if (e == cudaSuccess) e = sp::launch_push(g, &launches);
+    rec(g, timed, 7);
+    sp::launch_finish(g, &launches);
+    rec(g, timed, 8);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(g->stream);
+      g->state = 2;
+      return SP_ECUDA;
+    }
+    rc = read_ctl(g);
+    if (rc != SP_OK) {
+      g->state = 2;
+      return rc;
+    }
+    const Ctl &c = *g->ctl_host;
+    if (c.status != 0) return (sp_status)c.status;   // nothing changed
+    if (c.need_grow == 0) break;
+    if (attempt >= 6) {
+      g->state = 2;
+      return SP_ENOMEM;
+    }
+    ++regrows;
+    if (c.need_grow & sp::kGrowPoolFwd) {
+      rc = sp::store_grow_pool(g, &g->fwd, (long long)c.pool_need[0] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    if (c.need_grow & sp::kGrowPoolRev) {
+      rc = sp::store_grow_pool(g, &g->rev, (long long)c.pool_need[1] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    if (c.need_grow & sp::kGrowScratch) {
+      long long want = std::max<long long>((long long)c.scratch_used + 1024, 2 * b.scratch_cap);
+      g->al.put(b.scratch, (size_t)b.scratch_cap * sizeof(int2));
+      b.scratch = (int2 *)g->al.get((size_t)want * sizeof(int2));
+      b.scratch_cap = b.scratch ? want : 0;
+      if (!b.scratch) return SP_ENOMEM;
+    }
+  }
+  const Ctl &c = *g->ctl_host;
+  g->m += (long long)c.add_applied - (long long)c.del_applied;
+  fill_stats(g, c, stats, launches, regrows, ni, timed);
+  return status_of_repair(g, c);
+}
+
+sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_device) {
+  if (!g || !dist) return SP_EINVAL;
+  if (g->state != 1) return SP_ESTATE;
+  int launches = 0;
+  if (out_on_device) {
+    sp::launch_unpack(g, dist, parent, &launches);
+  } else {
+    sp::launch_unpack(g, g->out_dist, parent ? g->out_parent : nullptr, &launches);
+    cudaMemcpyAsync(dist, g->out_dist, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream);
+    if (parent)
+      cudaMemcpyAsync(parent, g->out_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream);
+  }
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  return SP_OK;
+}
+
+sp_status sp_graph_num_edges(const sp_graph *g, int64_t *m) {
+  if (!g || !m) return SP_EINVAL;
+  *m = g->m;
+  return SP_OK;
+}
+
+sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off, int32_t *col, int32_t *w,
+                        int out_on_device) {
+  if (!g || !row_off || (g->m > 0 && (!col || !w))) return SP_EINVAL;
+  int launches = 0;
+  const sp::Store *st = reverse ? &g->rev : &g->fwd;
+  if (out_on_device) return sp::store_export(g, st, (long long *)row_off, col, w, &launches);
+  const size_t nn = (size_t)g->n, mm = (size_t)std::max<long long>(g->m, 1);
+  size_t bytes = (nn + 1) * 8 + 2 * mm * 4 + 512;
+  char *buf = (char *)g->al.get(bytes);
+  if (!buf) return SP_ENOMEM;
+  long long *ro = (long long *)buf;
+  int *cc = (int *)(((uintptr_t)(ro + nn + 1) + 255) & ~(uintptr_t)255);
+  int *ww = cc + mm;
+  sp_status rc = sp::store_export(g, st, ro, cc, ww, &launches);
+  if (rc == SP_OK) {
+    cudaMemcpyAsync(row_off, ro, (nn + 1) * 8, cudaMemcpyDeviceToHost, g->stream);
+    if (g->m > 0) {
+      cudaMemcpyAsync(col, cc, (size_t)g->m * 4, cudaMemcpyDeviceToHost, g->stream);
+      cudaMemcpyAsync(w, ww, (size_t)g->m * 4, cudaMemcpyDeviceToHost, g->stream);
+    }
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) rc = SP_ECUDA;
+  }
+  g->al.put(buf, bytes);
+  return rc;
+}
+
+sp_status sp_graph_info_get(const sp_graph *g, sp_graph_info *info) {
+  if (!g || !info) return SP_EINVAL;
+  info->n = g->n;
+  info->source = g->source;
+  info->m = g->m;
+  info->cap_fwd = g->fwd.slots;
+  info->cap_rev = g->rev.slots;
+  Ctl c{};
+  if (cudaMemcpy(&c, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  info->pool_used_fwd = (int64_t)c.pool_used[0];
+  info->pool_used_rev = (int64_t)c.pool_used[1];
+  info->device_bytes = g->al.bytes_held;
+  info->state = g->state;
+  info->num_sms = g->num_sms;
+  return SP_OK;
+}
+
+}  // extern "C"

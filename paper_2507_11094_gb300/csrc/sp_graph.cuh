@@ -1,0 +1,120 @@
+// sp_graph.cuh -- host-side graph handle and the launch wrappers each
+// translation unit provides to sp_api.cu.
+#pragma once
+
+#include "sp_internal.cuh"
+
+namespace sp {
+
+// Frontier queue sizing: a vertex whose row holds more than kHeavyDeg edges
+// is expanded in chunks of kChunk edges spread over many warps; lighter
+// vertices are expanded 32 at a time by one warp.
+constexpr int kHeavyDeg = 256;
+constexpr int kChunk = 256;
+constexpr int kLoopThreads = 256;
+
+// One touched (store, row) pair of a batch, after sorting.
+struct Seg {
+  u32 first, end;        // item range in the sorted batch
+  int row;
+  int dir;               // 0 = forward store, 1 = reverse store
+  long long dest;        // slot where the merged row is written
+  long long scratch;     // scratch slot for a large in-place merge, else -1
+  int new_deg;
+  int new_cap;
+};
+
+// Per-call buffers that grow on demand.
+struct BatchBufs {
+  long long cap_items = 0;
+  u64 *keys = nullptr, *keys_alt = nullptr;
+  u32 *vals = nullptr, *vals_alt = nullptr;
+  unsigned char *flags = nullptr;   // per item: bit0 = applied
+  u64 *itemv = nullptr;             // per item: applied del (1) | applied add (1<<32)
+  u64 *item_pref = nullptr;         // exclusive scan of itemv
+  u32 *head = nullptr, *head_scan = nullptr;
+  Seg *seg = nullptr;
+  u32 *small_list = nullptr, *large_list = nullptr;
+  void *tmp = nullptr;
+  size_t tmp_bytes = 0;
+  long long cap_in = 0;             // staging for host inputs
+  int *in_del_src = nullptr, *in_del_dst = nullptr;
+  int *in_add_src = nullptr, *in_add_dst = nullptr, *in_add_w = nullptr;
+  int2 *scratch = nullptr;          // merge scratch
+  long long scratch_cap = 0;
+};
+
+// Arguments of the persistent frontier loops.
+struct LoopArgs {
+  Ctl *ctl;
+  Limits lim;
+  Store fwd, rev;
+  u64 *s;
+  u32 *qflag;
+  u32 *qlight[2];
+  int2 *qheavy[2];
+  u32 *alist;
+  int n;
+  // fused OnDelete mark (invalidation loop only)
+  const int *del_src, *del_dst;
+  long long n_del;
+};
+
+}  // namespace sp
+
+struct sp_graph {
+  int n = 0;
+  int bits = 1;                // id bits
+  int device = 0;
+  int num_sms = 0;
+  float slack = 0.25f;
+  cudaStream_t stream = nullptr;
+  sp::Alloc al;
+  sp::Store fwd, rev;
+  long long m = 0;
+  sp::u64 *s = nullptr;
+  sp::u32 *qflag = nullptr;
+  sp::u32 *qlight[2] = {nullptr, nullptr};
+  int2 *qheavy[2] = {nullptr, nullptr};
+  sp::u32 *alist = nullptr;
+  sp::Ctl *ctl = nullptr;       // device
+  sp::Ctl *ctl_host = nullptr;  // pinned
+  int *out_dist = nullptr, *out_parent = nullptr;
+  sp::BatchBufs bb;
+  int source = -1;
+  int state = 0;                // 0 none, 1 valid, 2 needs re-init
+  sp::Limits lim{};
+  int32_t max_rounds_user = 0;
+  long long wait_ns_user = 0;
+  int loop_blocks_push = 0, loop_blocks_inval = 0;
+  cudaEvent_t ev[SP_NPHASE + 1] = {};
+};
+
+namespace sp {
+
+// sp_store.cu
+sp_status store_build(sp_graph *g, sp::Store *st, const long long *row_off_d,
+                      const int *col_d, const int *w_d, long long m, int reverse,
+                      int *launches);
+sp_status store_export(sp_graph *g, const sp::Store *st, long long *row_off_d,
+                       int *col_d, int *w_d, int *launches);
+sp_status store_grow_pool(sp_graph *g, sp::Store *st, long long min_pool_slots);
+void launch_ctl_reset(sp_graph *g, int full, int *launches);
+void launch_prep(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                 const int *ad, const int *aw, long long na, int *launches);
+void launch_segments(sp_graph *g, long long n_items, int *launches);
+void launch_count(sp_graph *g, long long n_items, int *launches);
+void launch_merge(sp_graph *g, long long n_items, int *launches);
+void launch_finish(sp_graph *g, int *launches);
+
+// sp_frontier.cu
+int loop_blocks(int which, int num_sms);
+void launch_init(sp_graph *g, int source, int *launches);
+cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd,
+                         int *launches);
+void launch_pull(sp_graph *g, int *launches);
+void launch_add(sp_graph *g, long long n_items, int *launches);
+cudaError_t launch_push(sp_graph *g, int *launches);
+void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+
+}  // namespace sp

@@ -1,0 +1,181 @@
+// sp_internal.cuh -- device data layout and helpers shared by libsp's
+// translation units.  Nothing here is part of the ABI (include/sp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sp.h"
+
+namespace sp {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------------------
+// Packed per-vertex state: s[v] = dist << 32 | (u32)parent.
+// A 64-bit atomicMin on the packed word realises the paper's
+// <dist, parent> = <Min(dist, cand), v> multi-assignment (Incremental listing,
+// Section 3.3) as one atomic, so a parent always belongs to the distance
+// stored next to it.  Ties on distance pick the smaller parent id.
+// ---------------------------------------------------------------------------
+constexpr u32 kInf = SP_INF;                     // INT_MAX/2
+constexpr u32 kNoParent = 0xFFFFFFFFu;           // parent -1
+constexpr u64 kInfPack = ((u64)kInf << 32) | kNoParent;
+
+__host__ __device__ __forceinline__ u64 pack(u32 d, u32 p) {
+  return ((u64)d << 32) | (u64)p;
+}
+__host__ __device__ __forceinline__ u32 dist_of(u64 s) { return (u32)(s >> 32); }
+__host__ __device__ __forceinline__ u32 parent_of(u64 s) { return (u32)s; }
+
+// ---------------------------------------------------------------------------
+// Slack CSR.  Row r occupies adj[start, start+cap); its first deg slots hold
+// (col, w) pairs sorted by col.  Row starts are multiples of 4 slots (32 B,
+// one DRAM sector).  Rows that outgrow their capacity move to the spare pool
+// at the end of adj.
+// ---------------------------------------------------------------------------
+struct __align__(16) RowMeta {
+  long long start;
+  int deg;
+  int cap;
+};
+
+struct Store {
+  RowMeta *row = nullptr;   // [n]
+  int2 *adj = nullptr;      // [slots]  (x = col, y = w)
+  long long main_slots = 0; // end of the per-row region
+  long long slots = 0;      // total = main + pool
+};
+
+// ---------------------------------------------------------------------------
+// Control block in device memory.  One per graph; the host reads it back at
+// the end of every call (one small D2H copy).
+// ---------------------------------------------------------------------------
+enum : int {
+  kGrowPoolFwd = 1,
+  kGrowPoolRev = 2,
+  kGrowScratch = 4,
+};
+
+struct Ctl {
+  int status;            // sp_status of the running call (0 = ok)
+  int need_grow;         // kGrow* bits: a buffer was too small, nothing changed
+  int range_err;         // a candidate distance reached SP_INF
+  int timeout;           // 1 = round cap, 2 = barrier wait bound
+  int bad;               // an internal bounds check failed (write skipped)
+  // grid barrier (persistent kernels)
+  u32 bar_arrive;
+  u32 bar_gen;
+  // frontier state of the persistent loops
+  u32 cur;               // which queue buffer is current (0/1)
+  u32 round;
+  u32 done;
+  u32 epoch;             // dedupe tag of the frontier being built
+  u32 light_cnt[2];      // light queue sizes
+  u32 pad0;
+  u64 heavy_cnt[2];      // heavy queue: count << 40 | chunks
+  u32 work_next;         // dynamic work counter of the current round
+  u32 work_total;        // work items in the current round
+  u32 n_light_groups;    // light groups in the current round
+  u32 pad1;
+  // invalidation list A
+  u32 a_count;           // entries appended so far
+  u32 a_lo, a_hi;        // current round's slice of A
+  u32 pad2;
+  // batch bookkeeping
+  u32 n_seg;             // touched (dir,row) segments
+  u32 n_small, n_large;  // segments merged by one warp / by one block
+  u32 n_heavy;           // heavy queue entries of the current round
+  u64 pull_heavy;        // deferred pull rows: count << 40 | chunks
+  u64 pool_used[2];      // spare slots taken (fwd, rev), persistent
+  u64 pool_need[2];      // demand seen by the last count pass
+  u64 scratch_used;      // merge scratch slots reserved this batch
+  // counters of the call
+  u64 del_applied, del_absent, add_applied, add_present;
+  u64 affected, seeds, relaxed, improved, rows_touched, rows_relocated;
+  u64 inval_edges, pull_edges, push_vertices, enqueued;
+  u64 merge_slots;       // old + new slots of all merged rows
+  u32 rounds_inval, rounds_push;
+};
+
+// Launch-time limits.
+struct Limits {
+  u32 max_rounds;        // per fixedPoint loop
+  u64 wait_ns;           // per barrier wait
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 ld_cg_u64(const u64 *p) {
+  return __ldcg((const unsigned long long *)p);
+}
+__device__ __forceinline__ u32 ld_cg_u32(const u32 *p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_cg_i32(const int *p) { return __ldcg(p); }
+
+__device__ __forceinline__ u32 ld_acquire_u32(const u32 *p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(u32 *p, u32 v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ u64 globaltimer_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ u32 lanemask_lt() {
+  u32 m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__host__ __device__ __forceinline__ long long round_up4(long long x) {
+  return (x + 3) & ~3LL;
+}
+
+// Capacity given to a row of `deg` edges: deg plus max(slack*deg, 4) spare
+// slots, rounded up to a multiple of 4.
+__host__ __device__ __forceinline__ int row_capacity(long long deg, float slack) {
+  long long extra = (long long)(slack * (float)deg + 0.999f);
+  if (extra < 4) extra = 4;
+  return (int)round_up4(deg + extra);
+}
+
+// Number of bits needed for vertex ids in [0, n).
+__host__ __device__ __forceinline__ int id_bits(long long n) {
+  int b = 1;
+  while ((1LL << b) < n) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers implemented in the .cu files.
+// ---------------------------------------------------------------------------
+struct Alloc {
+  sp_allocator user{};
+  bool has_user = false;
+  cudaStream_t stream = nullptr;
+  long long bytes_held = 0;
+  void *get(size_t bytes);
+  void put(void *p, size_t bytes);
+};
+
+// Device-wide exclusive scans (sp_scan.cu).  `tmp` needs scan_tmp_bytes(n).
+size_t scan_tmp_bytes(long long n);
+void scan_exclusive_u32(const u32 *in, u32 *out, long long n, void *tmp,
+                        cudaStream_t st, int *launches);
+void scan_exclusive_u64(const u64 *in, u64 *out, long long n, void *tmp,
+                        cudaStream_t st, int *launches);
+
+// LSD radix sort of (u64 key, u32 value) pairs on the low `key_bits` bits
+// (sp_sort.cu).  Sorts keys/vals in place using alt buffers of the same size
+// and `tmp` of sort_tmp_bytes(n).  Stable.
+size_t sort_tmp_bytes(long long n);
+void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,
+                int key_bits, void *tmp, cudaStream_t st, int *launches);
+
+}  // namespace sp

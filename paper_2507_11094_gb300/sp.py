@@ -1,0 +1,294 @@
+"""ctypes binding of libsp (include/sp.h): argument marshalling only.
+
+Every step of the computation runs in libsp's CUDA kernels.  PyTorch supplies
+device memory (its caching allocator, passed as an sp_allocator) and the CUDA
+stream.  Arrays may be numpy (host) or CUDA torch tensors (device); the
+matching ``*_on_device`` flag is set from the array type.  There is no CPU
+fallback: if libsp.so is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SP_INF = 1073741823
+SP_WMAX = 1 << 20
+SP_NPHASE = 8
+PHASES = ("sort", "count", "merge", "inval", "pull", "add", "push", "finish")
+
+STATUS = {0: "SP_OK", -1: "SP_EINVAL", -2: "SP_ENOMEM", -3: "SP_ERANGE",
+          -4: "SP_ESTATE", -5: "SP_ECUDA", -6: "SP_ETIMEOUT",
+          -7: "SP_ENOMEM_BUDGET"}
+SP_OK, SP_EINVAL, SP_ENOMEM, SP_ERANGE = 0, -1, -2, -3
+SP_ESTATE, SP_ECUDA, SP_ETIMEOUT, SP_ENOMEM_BUDGET = -4, -5, -6, -7
+
+
+class SpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [
+        ("n_del_applied", ctypes.c_int64), ("n_del_absent", ctypes.c_int64),
+        ("n_add_applied", ctypes.c_int64), ("n_add_present", ctypes.c_int64),
+        ("affected", ctypes.c_int64), ("seeds", ctypes.c_int64),
+        ("relaxed_edges", ctypes.c_int64), ("improved", ctypes.c_int64),
+        ("rows_touched", ctypes.c_int64), ("rows_relocated", ctypes.c_int64),
+        ("rounds_inval", ctypes.c_int32), ("rounds_push", ctypes.c_int32),
+        ("n_launches", ctypes.c_int32), ("regrows", ctypes.c_int32),
+        ("alg_bytes", ctypes.c_int64 * SP_NPHASE),
+        ("ms_phase", ctypes.c_float * SP_NPHASE),
+        ("ms_total", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_
+             if k not in ("alg_bytes", "ms_phase")}
+        d["alg_bytes"] = dict(zip(PHASES, list(self.alg_bytes)))
+        d["ms_phase"] = dict(zip(PHASES, list(self.ms_phase)))
+        return d
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("source", ctypes.c_int32), ("m", ctypes.c_int64),
+        ("cap_fwd", ctypes.c_int64), ("cap_rev", ctypes.c_int64),
+        ("pool_used_fwd", ctypes.c_int64), ("pool_used_rev", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64), ("state", ctypes.c_int32),
+        ("num_sms", ctypes.c_int32),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                           ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+# Entry points declared in include/sp.h: name -> (restype, argtypes)
+_P, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "sp_graph_create": (ctypes.c_int, [_I32, _I64, _P, _P, _P, ctypes.c_int, ctypes.c_float,
+                                       _P, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "sp_graph_destroy": (ctypes.c_int, [_P]),
+    "sp_sssp_init": (ctypes.c_int, [_P, _I32, _P]),
+    "sp_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int, _P]),
+    "sp_get_dist": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "sp_graph_num_edges": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "sp_export_csr": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]),
+    "sp_graph_info_get": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
+    "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
+    "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "sp_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsp.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"{path} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != SP_OK:
+        raise SpError(rc, what)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("CUDA is not available: libsp has no CPU path")
+    return torch
+
+
+def _is_cuda_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+class _Arrays:
+    """Marshal a group of arrays as all-host (numpy) or all-device (torch)."""
+
+    def __init__(self, arrays, dtypes):
+        self.keep = []
+        self.ptrs = []
+        dev = [a is not None and _is_cuda_tensor(a) for a in arrays]
+        present = [a is not None for a in arrays]
+        if any(dev) and not all(d for d, p in zip(dev, present) if p):
+            raise TypeError("mix of host and device arrays")
+        self.on_device = any(dev)
+        for a, dt in zip(arrays, dtypes):
+            if a is None:
+                self.ptrs.append(None)
+                continue
+            if self.on_device:
+                t = _torch()
+                tdt = {np.int32: t.int32, np.int64: t.int64}[dt]
+                a = a.to(tdt).contiguous()
+                self.keep.append(a)
+                self.ptrs.append(ctypes.c_void_p(a.data_ptr()))
+            else:
+                a = np.ascontiguousarray(a, dtype=dt)
+                self.keep.append(a)
+                self.ptrs.append(a.ctypes.data_as(ctypes.c_void_p))
+
+
+class Graph:
+    """A device-resident dynamic graph with SSSP distances (libsp handle)."""
+
+    def __init__(self, n, row_off, col, w, slack: float = 0.25, stream=None,
+                 torch_allocator: bool = True):
+        torch = _torch()
+        lib = load()
+        self.n = int(n)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._alloc = None
+        alloc_p = None
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+
+            def _a(ctx, size, st):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), dev, st or 0)
+                except Exception:
+                    return None
+
+            def _f(ctx, ptr, size, st):
+                try:
+                    torch.cuda.caching_allocator_delete(ptr)
+                except Exception:
+                    pass
+
+            self._alloc = Allocator(None, ALLOC_FN(_a), FREE_FN(_f))
+            alloc_p = ctypes.byref(self._alloc)
+        arr = _Arrays([row_off, col, w], [np.int64, np.int32, np.int32])
+        m = int(arr.keep[1].numel() if arr.on_device else arr.keep[1].size)
+        h = ctypes.c_void_p()
+        rc = lib.sp_graph_create(self.n, m, arr.ptrs[0], arr.ptrs[1], arr.ptrs[2],
+                                 int(arr.on_device), float(slack), alloc_p,
+                                 ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
+        _check(rc, "sp_graph_create")
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sp_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ------------------------------------------------------------
+    def sssp_init(self, source: int, stats: bool = False):
+        st = BatchStats() if stats else None
+        rc = load().sp_sssp_init(self._h, int(source), ctypes.byref(st) if st else None)
+        _check(rc, "sp_sssp_init")
+        return st
+
+    def apply_batch(self, del_src, del_dst, add_src, add_dst, add_w, stats: bool = False,
+                    raise_on_error: bool = True):
+        """Apply deletions then insertions; numpy arrays are host inputs,
+        CUDA tensors device inputs.  Returns BatchStats (or None)."""
+        arr = _Arrays([del_src, del_dst, add_src, add_dst, add_w], [np.int32] * 5)
+        size = (lambda a: int(a.numel())) if arr.on_device else (lambda a: int(a.size))
+        nd, na = size(arr.keep[0]), size(arr.keep[2])
+        if size(arr.keep[1]) != nd or size(arr.keep[3]) != na or size(arr.keep[4]) != na:
+            raise SpError(SP_EINVAL, "batch array sizes")
+        st = BatchStats() if stats else None
+        rc = load().sp_apply_batch(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
+                                   arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
+                                   ctypes.byref(st) if st else None)
+        if raise_on_error:
+            _check(rc, "sp_apply_batch")
+            return st
+        return rc, st
+
+    def apply(self, batch, stats: bool = False):
+        """Apply a ``workloads.Batch``."""
+        return self.apply_batch(batch.del_src, batch.del_dst, batch.add_src,
+                                batch.add_dst, batch.add_w, stats=stats)
+
+    def get_dist(self, parent: bool = False, out=None):
+        """dist (and parent) as numpy arrays, or into CUDA tensors ``out``
+        = (dist, parent_or_None)."""
+        lib = load()
+        if out is not None:
+            d, p = out
+            rc = lib.sp_get_dist(self._h, ctypes.c_void_p(d.data_ptr()),
+                                 ctypes.c_void_p(p.data_ptr()) if p is not None else None, 1)
+            _check(rc, "sp_get_dist")
+            return out
+        d = np.empty(self.n, dtype=np.int32)
+        p = np.empty(self.n, dtype=np.int32) if parent else None
+        rc = lib.sp_get_dist(self._h, d.ctypes.data_as(ctypes.c_void_p),
+                             p.ctypes.data_as(ctypes.c_void_p) if p is not None else None, 0)
+        _check(rc, "sp_get_dist")
+        return (d, p) if parent else d
+
+    @property
+    def m(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().sp_graph_num_edges(self._h, ctypes.byref(v)), "sp_graph_num_edges")
+        return int(v.value)
+
+    def export_csr(self, reverse: bool = False):
+        m = self.m
+        ro = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(max(m, 1), dtype=np.int32)
+        w = np.empty(max(m, 1), dtype=np.int32)
+        rc = load().sp_export_csr(self._h, int(reverse), ro.ctypes.data_as(ctypes.c_void_p),
+                                  col.ctypes.data_as(ctypes.c_void_p),
+                                  w.ctypes.data_as(ctypes.c_void_p), 0)
+        _check(rc, "sp_export_csr")
+        return ro, col[:m], w[:m]
+
+    def info(self) -> GraphInfo:
+        gi = GraphInfo()
+        _check(load().sp_graph_info_get(self._h, ctypes.byref(gi)), "sp_graph_info_get")
+        return gi
+
+    def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
+        _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")
+
+
+def status_str(code: int) -> str:
+    return load().sp_status_str(int(code)).decode()

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point of
+include/sp.h (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_11094_gb300 import build, sp
+    build.build()
+    return sp.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sp_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sp_graph_create", "sp_sssp_init", "sp_apply_batch", "sp_get_dist",
+                     "sp_graph_destroy", "sp_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function(lib):
+    from paper_2507_11094_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(sp_[a-z_0-9]+)$", out, flags=re.M))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_binding_covers_every_declared_function():
+    from paper_2507_11094_gb300 import sp
+    assert sorted(sp.SIGNATURES) == declared_functions()
+
+
+def test_status_strings_and_version(lib):
+    from paper_2507_11094_gb300 import sp
+    for code, name in sp.STATUS.items():
+        assert sp.status_str(code).startswith(name)
+    assert re.match(rb"^\d+\.\d+\.\d+$", lib.sp_version())
+
+
+def test_argument_checks_need_no_device(lib):
+    # rejected before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.sp_graph_create(0, 0, None, None, None, 0, 0.25, None, None,
+                               ctypes.byref(h)) == -1
+    assert lib.sp_graph_destroy(None) == 0
+    assert lib.sp_sssp_init(None, 0, None) == -1
+    assert lib.sp_apply_batch(None, 0, None, None, 0, None, None, None, 0, None) == -1
+
+
+def test_stats_struct_layout_matches_header():
+    from paper_2507_11094_gb300 import sp
+    # 10 int64 + 4 int32 + 8 int64 + 8 float + 1 float, 8-byte aligned
+    assert ctypes.sizeof(sp.BatchStats) == 10 * 8 + 4 * 4 + 8 * 8 + 8 * 4 + 4 + 4
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2507_11094_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt, f

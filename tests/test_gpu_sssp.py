@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Distances must equal the oracle's bit for bit after sp_sssp_init and after
+every batch; parents must satisfy the shortest-path-tree invariants (ties make
+parents non-unique); the stores must equal the oracle's edge set (forward)
+and its transpose (reverse); the batch counters must equal the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.invariants import check_sssp
+from paper_2507_11094_gb300 import sp
+from paper_2507_11094_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+INF = sp.SP_INF
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2507_11094_gb300 import build
+    build.build()
+    oracle.build()
+    sp.load()
+
+
+def transpose(n, ro, col, w):
+    u = np.repeat(np.arange(n, dtype=np.int64), np.diff(ro))
+    key = col.astype(np.int64) * n + u
+    order = np.argsort(key, kind="stable")
+    rro = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(col, minlength=n), out=rro[1:])
+    return rro, u[order].astype(np.int32), w[order]
+
+
+def check_all(g, ref, src, store=True):
+    d, p = g.get_dist(parent=True)
+    want = ref.dijkstra(src)
+    np.testing.assert_array_equal(d, want)
+    ro, col, w = ref.csr()
+    check_sssp(g.n, ro, col, w, src, d, p)
+    assert g.m == col.size
+    if store:
+        for a, b in zip(g.export_csr(), (ro, col, w)):
+            np.testing.assert_array_equal(a, b)
+        for a, b in zip(g.export_csr(reverse=True), transpose(g.n, ro, col, w)):
+            np.testing.assert_array_equal(a, b)
+    return d
+
+
+def run_workload(W, n_batches, store=True, slack=0.25):
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    with sp.Graph(W.n, W.row_off, W.col, W.w, slack=slack) as g:
+        g.sssp_init(W.source)
+        d = check_all(g, ref, W.source, store)
+        for k in range(n_batches):
+            b = W.batch(k, dist=d if W.tree_fraction else None)
+            st = g.apply(b, stats=True)
+            cnt = ref.apply(b)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == cnt
+            d = check_all(g, ref, W.source, store)
+
+
+def test_tiny_er_ten_batches():
+    run_workload(wl.tiny_er(seed=1), 10)
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_tiny_er_other_seeds(seed):
+    run_workload(wl.tiny_er(seed=seed), 10)
+
+
+def test_rmat_scale14_heavy_rows():
+    W = wl.rmat(scale=14, batch_frac=0.01, seed=1)
+    assert np.diff(W.row_off).max() > 256      # exercises heavy chunks
+    run_workload(W, 5)
+
+
+def test_rmat_scale12_big_batches():
+    run_workload(wl.rmat(scale=12, batch_frac=0.05, seed=5), 4)
+
+
+def test_grid_tree_biased_deletions():
+    run_workload(wl.grid(64, 64, batch_frac=0.02, seed=1), 5)
+
+
+def test_grid_uniform_pair_insertions():
+    run_workload(wl.grid(48, 80, batch_frac=0.01, seed=2, insert_kind="uniform"), 4)
+
+
+def test_slack_zero_forces_relocation_and_pool_growth():
+    n = 300
+    ro, col, w = wl.er_digraph(n, 1200, 1, 50, seed=8)
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w, slack=0.0) as g:
+        g.sssp_init(0)
+        rng = np.random.default_rng(0)
+        total_reloc = 0
+        for k in range(6):
+            # pile insertions onto a few rows
+            u = rng.integers(0, 5, size=2000).astype(np.int32)
+            v = rng.integers(0, n, size=2000).astype(np.int32)
+            ww = rng.integers(1, 50, size=2000).astype(np.int32)
+            z = np.zeros(0, np.int32)
+            st = g.apply_batch(z, z, u, v, ww, stats=True)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == ref.apply_batch(z, z, u, v, ww)
+            total_reloc += st.rows_relocated
+            check_all(g, ref, 0)
+        assert total_reloc > 0
+        assert g.info().pool_used_fwd > 0
+
+
+# ---------------------------------------------------------------- edge cases
+
+def small_graph(seed=4, n=500, m=4000):
+    ro, col, w = wl.er_digraph(n, m, 1, 100, seed)
+    return n, ro, col, w
+
+
+def test_empty_batch():
+    n, ro, col, w = small_graph()
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(3)
+        z = np.zeros(0, np.int32)
+        st = g.apply_batch(z, z, z, z, z, stats=True)
+        assert st.n_del_applied == st.n_add_applied == 0
+        check_all(g, ref, 3)
+
+
+def test_delete_then_reinsert_restores_distances():
+    n, ro, col, w = small_graph()
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(0)
+        d0 = g.get_dist()
+        u = np.repeat(np.arange(n), np.diff(ro)).astype(np.int32)
+        pick = np.random.default_rng(3).choice(col.size, 800, replace=False)
+        z = np.zeros(0, np.int32)
+        g.apply_batch(u[pick], col[pick], z, z, z)
+        ref.apply_batch(u[pick], col[pick], z, z, z)
+        check_all(g, ref, 0)
+        g.apply_batch(z, z, u[pick], col[pick], w[pick])
+        ref.apply_batch(z, z, u[pick], col[pick], w[pick])
+        np.testing.assert_array_equal(check_all(g, ref, 0), d0)
+
+
+def test_delete_all_out_edges_of_source():
+    n, ro, col, w = small_graph()
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w) as g:
+        src = 7
+        g.sssp_init(src)
+        v = col[ro[src]:ro[src + 1]]
+        u = np.full(v.size, src, np.int32)
+        z = np.zeros(0, np.int32)
+        g.apply_batch(u, v, z, z, z)
+        ref.apply_batch(u, v, z, z, z)
+        d = check_all(g, ref, src)
+        assert d[src] == 0 and np.all(np.delete(d, src) == INF)
+
+
+def test_noop_readings_and_duplicates():
+    n, ro, col, w = small_graph(seed=6, n=200, m=1500)
+    ref = oracle.OracleGraph(n, ro, col, w)
+    u_all = np.repeat(np.arange(n), np.diff(ro)).astype(np.int32)
+    rng = np.random.default_rng(1)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(0)
+        for k in range(5):
+            pick = rng.choice(col.size, 60, replace=False)
+            du, dv = u_all[pick], col[pick]
+            # absent deletions, repeated deletions
+            au = rng.integers(0, n, 40).astype(np.int32)
+            av = rng.integers(0, n, 40).astype(np.int32)
+            del_s = np.concatenate([du, du[:10], au])
+            del_d = np.concatenate([dv, dv[:10], av])
+            # present insertions, duplicates with different weights,
+            # re-insertion of deleted edges with new weights
+            iu = np.concatenate([u_all[pick[10:20]], au[:20], au[:20], du[:15]])
+            iv = np.concatenate([col[pick[10:20]], av[:20], av[:20], dv[:15]])
+            iw = rng.integers(1, 100, iu.size).astype(np.int32)
+            st = g.apply_batch(del_s, del_d, iu, iv, iw, stats=True)
+            cnt = ref.apply_batch(del_s, del_d, iu, iv, iw)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == cnt
+            check_all(g, ref, 0)
+            ro2, col2, w2 = ref.csr()
+            u_all = np.repeat(np.arange(n), np.diff(ro2)).astype(np.int32)
+            col = col2
+
+
+def test_invalid_batch_leaves_graph_unchanged():
+    n, ro, col, w = small_graph()
+    ref = oracle.OracleGraph(n, ro, col, w)
+    a = lambda *x: np.array(x, np.int32)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(0)
+        for args in [(a(0), a(n), a(), a(), a()),
+                     (a(), a(), a(1), a(2), a(0)),
+                     (a(), a(), a(1), a(2), a(sp.SP_WMAX + 1)),
+                     (a(-1), a(2), a(1), a(2), a(5))]:
+            rc, _ = g.apply_batch(*args, raise_on_error=False)
+            assert rc == sp.SP_EINVAL
+            check_all(g, ref, 0)
+
+
+def test_state_errors_and_invalid_source():
+    n, ro, col, w = small_graph()
+    with sp.Graph(n, ro, col, w) as g:
+        z = np.zeros(0, np.int32)
+        rc, _ = g.apply_batch(z, z, z, z, z, raise_on_error=False)
+        assert rc == sp.SP_ESTATE
+        with pytest.raises(sp.SpError) as e:
+            g.get_dist()
+        assert e.value.code == sp.SP_ESTATE
+        for bad in (-1, n):
+            with pytest.raises(sp.SpError) as e:
+                g.sssp_init(bad)
+            assert e.value.code == sp.SP_EINVAL
+
+
+def test_create_rejects_bad_csr_and_sorts_unsorted_rows():
+    ro = np.array([0, 2, 3, 3], np.int64)
+    with pytest.raises(sp.SpError):
+        sp.Graph(3, ro, np.array([1, 1, 0], np.int32), np.array([1, 2, 3], np.int32))
+    with pytest.raises(sp.SpError):
+        sp.Graph(3, ro, np.array([1, 2, 5], np.int32), np.array([1, 2, 3], np.int32))
+    with pytest.raises(sp.SpError):
+        sp.Graph(3, ro, np.array([1, 2, 0], np.int32), np.array([1, 0, 3], np.int32))
+    # unsorted rows are accepted and stored sorted
+    n, ro, col, w = small_graph(seed=9, n=300, m=3000)
+    perm_col, perm_w = col.copy(), w.copy()
+    rng = np.random.default_rng(2)
+    for u in range(n):
+        s, e = ro[u], ro[u + 1]
+        p = rng.permutation(e - s) + s
+        perm_col[s:e], perm_w[s:e] = col[p], w[p]
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, perm_col, perm_w) as g:
+        g.sssp_init(0)
+        check_all(g, ref, 0)
+
+
+def test_range_error_and_recovery():
+    n = 1101
+    ro = np.concatenate([np.arange(n, dtype=np.int64), [n - 1]])
+    col = np.arange(1, n, dtype=np.int32)
+    w = np.full(n - 1, sp.SP_WMAX, dtype=np.int32)
+    with sp.Graph(n, ro, col, w) as g:
+        with pytest.raises(sp.SpError) as e:
+            g.sssp_init(0)
+        assert e.value.code == sp.SP_ERANGE
+        assert g.info().state == 2
+        g.sssp_init(600)      # 500 edges of 2^20 fit
+        d = g.get_dist()
+        assert d[-1] == 500 * sp.SP_WMAX and np.all(d[:600] == INF)
+
+
+def test_round_cap_returns_timeout_and_reinit_recovers():
+    n = 400
+    ro = np.concatenate([np.arange(n, dtype=np.int64), [n - 1]])
+    col = np.arange(1, n, dtype=np.int32)
+    w = np.ones(n - 1, dtype=np.int32)
+    with sp.Graph(n, ro, col, w) as g:
+        g.set_limits(max_rounds=5)
+        with pytest.raises(sp.SpError) as e:
+            g.sssp_init(0)
+        assert e.value.code == sp.SP_ETIMEOUT
+        z = np.zeros(0, np.int32)
+        rc, _ = g.apply_batch(z, z, z, z, z, raise_on_error=False)
+        assert rc == sp.SP_ESTATE
+        g.set_limits(0, 0)
+        g.sssp_init(0)
+        np.testing.assert_array_equal(g.get_dist(), np.arange(n))
+
+
+def test_device_tensor_inputs_and_outputs():
+    import torch
+    W = wl.tiny_er(seed=7)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    dev = torch.device("cuda")
+    with sp.Graph(W.n, torch.from_numpy(W.row_off).to(dev), torch.from_numpy(W.col).to(dev),
+                  torch.from_numpy(W.w).to(dev)) as g:
+        g.sssp_init(W.source)
+        for k in range(3):
+            b = W.batch(k)
+            t = [torch.from_numpy(x).to(dev) for x in
+                 (b.del_src, b.del_dst, b.add_src, b.add_dst, b.add_w)]
+            g.apply_batch(*t)
+            ref.apply(b)
+            d = torch.empty(W.n, dtype=torch.int32, device=dev)
+            p = torch.empty(W.n, dtype=torch.int32, device=dev)
+            g.get_dist(out=(d, p))
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(d.cpu().numpy(), ref.dijkstra(W.source))
+            ro, col, w = ref.csr()
+            check_sssp(W.n, ro, col, w, W.source, d.cpu().numpy(), p.cpu().numpy())
+
+
+def test_worked_example_numbers_on_gpu():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "worked_example_sec3.json")
+    fix = json.load(open(path))
+    names = fix["vertices"]
+    idx = {s: i for i, s in enumerate(names)}
+    n = len(names)
+    e = sorted((idx[a], idx[b], c) for a, b, c in fix["edges"])
+    ro = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount([x[0] for x in e], minlength=n), out=ro[1:])
+    col = np.array([x[1] for x in e], np.int32)
+    w = np.array([x[2] for x in e], np.int32)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(idx[fix["source"]])
+        d = g.get_dist()
+        for k, val in fix["before"]["paper_dist"].items():
+            assert d[idx[k]] == val
+        b = fix["both"]
+        arr = lambda L, j: np.array([idx[x[j]] if j < 2 else x[j] for x in L], np.int32)
+        g.apply_batch(arr(b["del"], 0), arr(b["del"], 1), arr(b["add"], 0), arr(b["add"], 1),
+                      arr(b["add"], 2))
+        d = g.get_dist()
+        for k, val in b["paper_dist"].items():
+            assert d[idx[k]] == val
+
+
+def test_static_recompute_equals_dynamic():
+    W = wl.rmat(scale=13, batch_frac=0.02, seed=3)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        g.sssp_init(W.source)
+        for k in range(3):
+            g.apply(W.batch(k))
+            d_dyn = g.get_dist()
+            g.sssp_init(W.source)
+            np.testing.assert_array_equal(g.get_dist(), d_dyn)
