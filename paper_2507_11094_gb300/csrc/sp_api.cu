@@ -44,17 +44,11 @@ sp_status csr_validate(sp_graph *g, const long long *row_off_d, const int *col_d
 
 namespace {
 
-// Buffers sized by the batch: grown (never shrunk) when a larger batch comes.
-template <typename T>
-bool regrow(sp_graph *g, T *&p, long long &cap_now, long long need, size_t elem) {
-  (void)elem;
-  if (need <= cap_now && p) return true;
-  g->al.put(p, (size_t)cap_now * sizeof(T));
-  p = (T *)g->al.get((size_t)need * sizeof(T));
-  cap_now = p ? need : 0;
-  return p != nullptr;
-}
+// Frontier edge ranges are 32-bit (a frontier holds each vertex at most once,
+// so its edges never exceed m); graphs stay below 2^31 edges.
+constexpr long long kMaxEdges = (1LL << 31) - 1;
 
+// Buffers sized by the batch: grown (never shrunk) when a larger batch comes.
 sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
   sp::BatchBufs &b = g->bb;
   const long long want = std::max<long long>(ni + 1, 1024);
@@ -67,7 +61,9 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     al.put(b.flags, old); al.put(b.itemv, old * 8); al.put(b.item_pref, old * 8);
     al.put(b.head, old * 4); al.put(b.head_scan, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
-    al.put(b.small_list, old * 4); al.put(b.large_list, old * 4);
+    al.put(b.small_list, old * 4); al.put(b.medium_list, old * 4);
+    al.put(b.large_list, old * 4); al.put(b.large_cb, old * 4);
+    al.put(b.copy_list, old * 4); al.put(b.copy_cb, old * 4);
     al.put(b.tmp, b.tmp_bytes);
     b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
     b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
@@ -75,12 +71,15 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
     b.head = (u32 *)al.get(c * 4); b.head_scan = (u32 *)al.get(c * 4);
     b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
-    b.small_list = (u32 *)al.get(c * 4); b.large_list = (u32 *)al.get(c * 4);
+    b.small_list = (u32 *)al.get(c * 4); b.medium_list = (u32 *)al.get(c * 4);
+    b.large_list = (u32 *)al.get(c * 4); b.large_cb = (u32 *)al.get(c * 4);
+    b.copy_list = (u32 *)al.get(c * 4); b.copy_cb = (u32 *)al.get(c * 4);
     b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
     if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
-        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.small_list || !b.large_list ||
+        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.small_list ||
+        !b.medium_list || !b.large_list || !b.large_cb || !b.copy_list || !b.copy_cb ||
         !b.tmp) {
       return SP_ENOMEM;
     }
@@ -214,7 +213,9 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(b.flags, c); al.put(b.itemv, c * 8); al.put(b.item_pref, c * 8);
   al.put(b.head, c * 4); al.put(b.head_scan, c * 4);
   al.put(b.seg, c * sizeof(sp::Seg));
-  al.put(b.small_list, c * 4); al.put(b.large_list, c * 4);
+  al.put(b.small_list, c * 4); al.put(b.medium_list, c * 4);
+  al.put(b.large_list, c * 4); al.put(b.large_cb, c * 4);
+  al.put(b.copy_list, c * 4); al.put(b.copy_cb, c * 4);
   al.put(b.tmp, b.tmp_bytes);
   c = b.cap_in;
   al.put(b.in_del_src, c * 4); al.put(b.in_del_dst, c * 4);
@@ -226,9 +227,10 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->rev.adj, (size_t)g->rev.slots * sizeof(int2));
   al.put(g->s, n * 8);
   al.put(g->qflag, n * 4);
-  al.put(g->qlight[0], n * 4); al.put(g->qlight[1], n * 4);
-  al.put(g->qheavy[0], n * 8); al.put(g->qheavy[1], n * 8);
-  al.put(g->alist, n * 4);
+  al.put(g->qent[0], n * 8); al.put(g->qent[1], n * 8);
+  al.put(g->aent, n * 8);
+  al.put(g->qown[0], (size_t)g->own_cap * 4); al.put(g->qown[1], (size_t)g->own_cap * 4);
+  al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
   al.put(g->ctl, sizeof(Ctl));
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
@@ -246,6 +248,7 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   *out = nullptr;
   if (n <= 0 || m < 0 || !row_off || (m > 0 && (!col || !w)) || !(slack >= 0.f) || slack > 16.f)
     return SP_EINVAL;
+  if (m > kMaxEdges) return SP_EINVAL;
   if (alloc && (!alloc->alloc || !alloc->free)) return SP_EINVAL;
   sp_graph *g = new (std::nothrow) sp_graph();
   if (!g) return SP_ENOMEM;
@@ -288,15 +291,13 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   const size_t nn = (size_t)n;
   g->s = (u64 *)g->al.get(nn * 8);
   g->qflag = (u32 *)g->al.get(nn * 4);
-  g->qlight[0] = (u32 *)g->al.get(nn * 4);
-  g->qlight[1] = (u32 *)g->al.get(nn * 4);
-  g->qheavy[0] = (int2 *)g->al.get(nn * 8);
-  g->qheavy[1] = (int2 *)g->al.get(nn * 8);
-  g->alist = (u32 *)g->al.get(nn * 4);
+  g->qent[0] = (int2 *)g->al.get(nn * 8);
+  g->qent[1] = (int2 *)g->al.get(nn * 8);
+  g->aent = (int2 *)g->al.get(nn * 8);
   g->out_dist = (int *)g->al.get(nn * 4);
   g->out_parent = (int *)g->al.get(nn * 4);
-  if (!g->ctl || !g->s || !g->qflag || !g->qlight[0] || !g->qlight[1] || !g->qheavy[0] ||
-      !g->qheavy[1] || !g->alist || !g->out_dist || !g->out_parent) {
+  if (!g->ctl || !g->s || !g->qflag || !g->qent[0] || !g->qent[1] || !g->aent ||
+      !g->out_dist || !g->out_parent) {
     sp_graph_destroy(g);
     return SP_ENOMEM;
   }
@@ -332,6 +333,7 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   sp_status rc = sp::csr_validate(g, ro_d, col_d, w_d, m, &launches);
   if (rc == SP_OK) rc = sp::store_build(g, &g->fwd, ro_d, col_d, w_d, m, 0, &launches);
   if (rc == SP_OK) rc = sp::store_build(g, &g->rev, ro_d, col_d, w_d, m, 1, &launches);
+  if (rc == SP_OK) rc = sp::ensure_owner_tables(g);
   if (tmp_in) g->al.put(tmp_in, tmp_in_bytes);
   if (rc == SP_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) rc = SP_ECUDA;
   if (rc != SP_OK) {
@@ -403,6 +405,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
     return SP_EINVAL;
   if (n_del + n_add > (1LL << 30)) return SP_EINVAL;
+  if (g->m + n_add > kMaxEdges) return SP_EINVAL;
   if (g->state != 1) return SP_ESTATE;
   const long long nb = n_del + n_add, ni = 2 * nb;
   const bool timed = stats != nullptr;
@@ -472,6 +475,10 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
     }
     if (c.need_grow & sp::kGrowPoolRev) {
       rc = sp::store_grow_pool(g, &g->rev, (long long)c.pool_need[1] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    if (c.need_grow & (sp::kGrowPoolFwd | sp::kGrowPoolRev)) {
+      rc = sp::ensure_owner_tables(g);
       if (rc != SP_OK) return rc;
     }
     if (c.need_grow & sp::kGrowScratch) {

@@ -16,6 +16,13 @@
 //     out-edges of the frontier until no distance changes.
 // Rounds are separated by a grid barrier whose waits are bounded; the round
 // count is capped (Bellman-Ford bound n + 1 by default).
+//
+// Work balance: a vertex entering a frontier reserves a contiguous range of
+// that frontier's edge space (one packed 64-bit atomic per warp), and the
+// round is processed as chunks of kChunk edges, one warp per chunk and
+// kEdgesPerLane consecutive edges per lane, so a 40,000-edge hub and a
+// 2-edge vertex cost the same per edge.  Each lane issues the loads of all
+// its edges before it uses any of them.
 #include <algorithm>
 
 #include "sp_graph.cuh"
@@ -24,22 +31,16 @@ namespace sp {
 
 namespace {
 
-constexpr int kWarps = kLoopThreads / 32;
-constexpr u64 kMask40 = (1ull << 40) - 1;
 constexpr int kOpPush = 0, kOpInval = 1;
-
-struct WarpSmem {
-  u32 excl[32];
-  u32 v[32];
-  u32 d[32];
-  long long start[32];
-};
+constexpr int K = kEdgesPerLane;
+constexpr u32 kNoEdge = 0xFFFFFFFFu;
+constexpr u32 kFull = 0xffffffffu;
 
 __device__ __forceinline__ u32 warp_incl_scan(u32 x) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    u32 y = __shfl_up_sync(0xffffffffu, x, o);
+    u32 y = __shfl_up_sync(kFull, x, o);
     if (lane >= o) x += y;
   }
   return x;
@@ -48,8 +49,17 @@ __device__ __forceinline__ u32 warp_incl_scan(u32 x) {
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+__device__ __forceinline__ u64 shfl64(u64 x, int src) {
+  u32 lo = __shfl_sync(kFull, (u32)x, src), hi = __shfl_sync(kFull, (u32)(x >> 32), src);
+  return ((u64)hi << 32) | lo;
+}
+__device__ __forceinline__ u64 shfl64_down(u64 x, int d) {
+  u32 lo = __shfl_down_sync(kFull, (u32)x, d), hi = __shfl_down_sync(kFull, (u32)(x >> 32), d);
+  return ((u64)hi << 32) | lo;
 }
 
 // Grid barrier: the last block to arrive runs `hook` (thread 0 only), then
@@ -70,21 +80,27 @@ __device__ __forceinline__ void grid_barrier(Ctl *c, const Limits &lim, Hook hoo
       st_release_u32(&c->bar_gen, gen + 1);
     } else {
       const u64 t0 = globaltimer_ns();
+      u32 nap = 20;
       while (ld_acquire_u32(&c->bar_gen) == gen) {
         if (ld_cg_i32(&c->timeout) != 0) break;
         if (globaltimer_ns() - t0 > lim.wait_ns) {
           atomicCAS(&c->timeout, 0, 2);
           break;
         }
-        __nanosleep(32);
+        __nanosleep(nap);
+        if (nap < 320) nap += nap >> 1;
       }
     }
   }
   __syncthreads();
 }
 
+__device__ __forceinline__ volatile u64 *qcnt_of(volatile Ctl *c, u32 b) {
+  return b ? &c->qcnt1 : &c->qcnt0;
+}
+
 // Serial step between rounds (runs in one thread).  `first` is the step
-// before round 0, when the producers have filled queue `cur`.
+// before round 0, when the producers have filled frontier buffer `cur`.
 __device__ void serial_advance(Ctl *cc, const Limits &lim, bool first, int op) {
   volatile Ctl *c = cc;
   u32 cur = c->cur;
@@ -96,18 +112,15 @@ __device__ void serial_advance(Ctl *cc, const Limits &lim, bool first, int op) {
     c->cur = cur;
     c->round = c->round + 1;
   }
-  c->light_cnt[cur ^ 1u] = 0;
-  c->heavy_cnt[cur ^ 1u] = 0;
-  const u32 nl = c->light_cnt[cur];
-  const u64 hv = c->heavy_cnt[cur];
-  const u32 hc = (u32)(hv & kMask40);
-  c->n_heavy = (u32)(hv >> 40);
-  c->n_light_groups = (nl + 31) / 32;
-  c->work_total = c->n_light_groups + hc;
-  c->work_next = 0;
+  *qcnt_of(c, cur ^ 1u) = 0ull;          // the buffer this round fills
+  const u64 q = *qcnt_of(c, cur);
+  const u32 ne = (u32)(q >> 32), edges = (u32)q;
+  c->n_ent = ne;
+  c->n_edges = edges;
+  c->n_chunks = (edges + kChunk - 1) / kChunk;
   c->epoch = c->epoch + 1;
   bool done = false;
-  if (nl == 0 && hc == 0) {
+  if (edges == 0) {
     done = true;
   } else if (c->round >= lim.max_rounds) {
     c->timeout = 1;
@@ -117,72 +130,56 @@ __device__ void serial_advance(Ctl *cc, const Limits &lim, bool first, int op) {
     c->done = 1;
     if (op == kOpPush) c->rounds_push = c->round;
     else c->rounds_inval = c->round;
-    // leave the queues empty for the next producer
-    c->cur = 0;
-    c->light_cnt[0] = c->light_cnt[1] = 0;
-    c->heavy_cnt[0] = c->heavy_cnt[1] = 0;
+    c->cur = 0;                          // leave the frontier empty
+    c->qcnt0 = 0ull;
+    c->qcnt1 = 0ull;
     c->epoch = c->epoch + 1;
   }
 }
 
-// Position of the owner of edge k among the 32 lanes of a group: the last
-// lane whose exclusive degree prefix is <= k (lanes with no edges are skipped
-// because the next lane has the same prefix).
-__device__ __forceinline__ int find_owner(const u32 *excl, u32 k) {
-  int o = 0;
+// Append up to K vertices per lane to queue q (warp-collective).  Each kept
+// vertex (want and degree > 0 in `row`) reserves deg slots of the queue's
+// edge space; the chunk-owner table gets its slot for every chunk whose first
+// edge falls in that range.
+__device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, const u32 *x,
+                                        const bool *want, int kk, u64 &n_enq) {
+  const int lane = threadIdx.x & 31;
+  int d[K];
+  u32 cnt = 0, sum = 0;
 #pragma unroll
-  for (int step = 16; step > 0; step >>= 1)
-    if (o + step < 32 && excl[o + step] <= k) o += step;
-  return o;
+  for (int k = 0; k < K; ++k) {
+    d[k] = (k < kk && want[k]) ? __ldg(&row[x[k]].deg) : 0;
+    if (d[k] > 0) {
+      ++cnt;
+      sum += (u32)d[k];
+    }
+  }
+  if (!__ballot_sync(kFull, cnt > 0)) return;
+  const u32 ci = warp_incl_scan(cnt), si = warp_incl_scan(sum);
+  const u32 ctot = __shfl_sync(kFull, ci, 31), stot = __shfl_sync(kFull, si, 31);
+  u64 base = 0;
+  if (lane == 0) base = atomicAdd(q.cnt, ((u64)ctot << 32) | (u64)stot);
+  base = shfl64(base, 0);
+  u32 slot = (u32)(base >> 32) + ci - cnt;
+  u32 eb = (u32)base + si - sum;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (d[k] > 0) {
+      q.ent[slot] = make_int2((int)x[k], (int)eb);
+      const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + (u32)d[k] - 1) / kChunk;
+      for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
+      ++slot;
+      eb += (u32)d[k];
+    }
+  }
+  n_enq += cnt;
 }
 
-// Append x to the next frontier (warp-collective: every lane calls).  Light
-// vertices go to the light queue, 32 per warp later; heavy ones get one queue
-// entry plus ceil(deg / kChunk) chunk ids for the next round.
-struct Enqueuer {
-  Ctl *c;
-  u32 *ql;
-  int2 *qh;
-  u32 *lcnt;
-  u64 *hcnt;
-  const RowMeta *row;   // forward rows (degree decides light/heavy)
-  u32 *alist;           // also append to A (invalidation only)
-  u64 n_enq = 0;
-
-  __device__ __forceinline__ void push(bool want, u32 x) {
-    const int lane = threadIdx.x & 31;
-    int dx = 0;
-    if (want) dx = __ldg(&row[x].deg);
-    const bool heavy = want && dx > kHeavyDeg;
-    const bool light = want && !heavy;
-    const u32 lm = __ballot_sync(0xffffffffu, light);
-    if (lm) {
-      const int leader = __ffs(lm) - 1;
-      u32 base = 0;
-      if (lane == leader) base = atomicAdd(lcnt, (u32)__popc(lm));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (light) ql[base + __popc(lm & lanemask_lt())] = x;
-    }
-    if (heavy) {
-      const u64 ch = (u64)((dx + kChunk - 1) / kChunk);
-      const u64 old = atomicAdd((unsigned long long *)hcnt, (1ull << 40) | ch);
-      qh[old >> 40] = make_int2((int)x, (int)(old & kMask40));
-    }
-    if (alist) {
-      const u32 am = __ballot_sync(0xffffffffu, want);
-      if (am) {
-        const int leader = __ffs(am) - 1;
-        u32 base = 0;
-        if (lane == leader) base = atomicAdd(&c->a_count, (u32)__popc(am));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (want) alist[base + __popc(am & lanemask_lt())] = x;
-      }
-    }
-    if (want) ++n_enq;
-  }
-};
-
 // --- edge operations ------------------------------------------------------
+//
+// Each op provides vdata(v) (a per-source datum read once per queue entry),
+// load(e) (the state word an edge needs) and run(...) (the updates of one
+// lane's edges followed by the warp-collective enqueue of what they queue).
 
 // Incremental fixedPoint body: <dist, parent>[x] = <Min(dist[x], dist[v] + w), v>
 // as one packed atomicMin; an improved x joins the next frontier once.
@@ -190,198 +187,247 @@ struct PushOp {
   u64 *s;
   u32 *qflag;
   u32 tag;
-  Enqueuer enq;
-  Ctl *c;
-  int n;
-  u64 n_vert = 0, n_edges = 0, n_imp = 0;
+  Queue next;
+  const RowMeta *row;
+  u64 n_edges = 0, n_imp = 0, n_enq = 0;
   int range_err = 0;
 
-  __device__ __forceinline__ bool vertex(u32 v, u32 &d) {
-    d = dist_of(ld_cg_u64(s + v));
-    ++n_vert;
-    return d < kInf;
-  }
-  __device__ __forceinline__ void edge(bool act, u32 v, u32 dv, int x, int w) {
-    bool want = false;
-    if (act) {
-      ++n_edges;
-      const u32 nd = dv + (u32)w;
-      if (nd >= kInf) {
-        range_err = 1;
-      } else {
-        const u64 cand = pack(nd, v);
-        if (cand < ld_cg_u64(s + x)) {
-          const u64 old = atomicMin((unsigned long long *)(s + x), cand);
-          if (cand < old) {
-            ++n_imp;
-            want = atomicExch(qflag + x, tag) != tag;
+  __device__ __forceinline__ u32 vdata(u32 v) { return dist_of(ld_cg_u64(s + v)); }
+  __device__ __forceinline__ u64 load(int2 e) { return ld_cg_u64(s + e.x); }
+  __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *od,
+                                      const int2 *ed, const u64 *sx) {
+    u32 tx[K];
+    bool want[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      want[k] = false;
+      tx[k] = (u32)ed[k].x;
+      if (act[k]) {
+        ++n_edges;
+        if (od[k] < kInf) {
+          const u32 nd = od[k] + (u32)ed[k].y;
+          if (nd >= kInf) {
+            range_err = 1;
+          } else {
+            const u64 cand = pack(nd, ov[k]);
+            if (cand < sx[k]) {
+              const u64 old = atomicMin((unsigned long long *)(s + ed[k].x), cand);
+              if (cand < old) {
+                ++n_imp;
+                want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
+              }
+            }
           }
         }
       }
     }
-    enq.push(want, (u32)x);
+    enqueue(next, row, tx, want, K, n_enq);
   }
 };
 
 // Decremental first loop body: a child x of v (parent[x] == v) loses its
-// distance and parent and joins the next frontier and the affected list A.
+// distance and parent, joins the next frontier (its out-edges) and the
+// affected list A (its in-edges, for the pull).
 struct InvalOp {
   u64 *s;
-  Enqueuer enq;
-  Ctl *c;
-  int n;
-  u64 n_vert = 0, n_edges = 0;
+  Queue next, alist;
+  const RowMeta *row, *rrow;
+  u64 n_edges = 0, n_enq = 0, n_aff = 0;
+  int range_err = 0;
 
-  __device__ __forceinline__ bool vertex(u32, u32 &d) {
-    d = 0;
-    ++n_vert;
-    return true;
-  }
-  __device__ __forceinline__ void edge(bool act, u32 v, u32, int x, int) {
-    bool hit = false;
-    if (act) {
-      ++n_edges;
-      const u64 sx = ld_cg_u64(s + x);
-      if (parent_of(sx) == v) {
-        __stcg((unsigned long long *)(s + x), kInfPack);
-        hit = true;
+  __device__ __forceinline__ u32 vdata(u32) { return 0; }
+  __device__ __forceinline__ u64 load(int2 e) { return ld_cg_u64(s + e.x); }
+  __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
+                                      const int2 *ed, const u64 *sx) {
+    u32 tx[K];
+    bool want[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      tx[k] = (u32)ed[k].x;
+      want[k] = act[k] && parent_of(sx[k]) == ov[k];
+      if (act[k]) ++n_edges;
+      if (want[k]) {
+        __stcg((unsigned long long *)(s + ed[k].x), kInfPack);
+        ++n_aff;
       }
     }
-    enq.push(hit, (u32)x);
+    enqueue(next, row, tx, want, K, n_enq);
+    u64 dummy = 0;
+    enqueue(alist, rrow, tx, want, K, dummy);
   }
 };
 
 // Decremental second loop body, one pass over the reverse store: an
-// invalidated v takes min over in-edges x -> v of (dist[x] + w, x).  v joins
-// the first push frontier once if it got a finite distance.
+// invalidated v takes min over in-edges x -> v of (dist[x] + w, x).  The
+// minimum is formed per lane and then per warp before one atomicMin per
+// (warp, vertex); v joins the first push frontier once if it improved.
 struct PullOp {
   u64 *s;
   u32 *qflag;
   u32 tag;
-  Enqueuer enq;
-  Ctl *c;
-  int n;
-  int2 *defer_q;       // heavy in-degree rows, chunked by a second kernel
-  u64 *defer_cnt;
-  u64 n_vert = 0, n_edges = 0;
+  Queue next;
+  const RowMeta *row;
+  u64 n_edges = 0, n_enq = 0;
   int range_err = 0;
 
-  __device__ __forceinline__ bool vertex(u32, u32 &d) {
-    d = 0;
-    ++n_vert;
-    return true;
+  __device__ __forceinline__ u32 vdata(u32) { return 0; }
+  __device__ __forceinline__ u64 load(int2 e) { return ld_cg_u64(s + e.x); }
+  __device__ __forceinline__ bool offer(u32 v, u64 best) {
+    if (best == ~0ull || best >= ld_cg_u64(s + v)) return false;
+    const u64 old = atomicMin((unsigned long long *)(s + v), best);
+    return best < old && atomicExch(qflag + v, tag) != tag;
   }
-  __device__ __forceinline__ void defer(u32 v, int deg) {
-    const u64 ch = (u64)((deg + kChunk - 1) / kChunk);
-    const u64 old = atomicAdd((unsigned long long *)defer_cnt, (1ull << 40) | ch);
-    defer_q[old >> 40] = make_int2((int)v, (int)(old & kMask40));
-  }
-  __device__ __forceinline__ void edge(bool act, u32 v, u32, int x, int w) {
-    bool want = false;
-    if (act) {
-      ++n_edges;
-      const u32 dx = dist_of(ld_cg_u64(s + x));
-      if (dx < kInf) {
-        const u32 nd = dx + (u32)w;
-        if (nd >= kInf) {
-          range_err = 1;
-        } else {
-          const u64 cand = pack(nd, (u32)x);
-          if (cand < ld_cg_u64(s + v)) {
-            const u64 old = atomicMin((unsigned long long *)(s + v), cand);
-            if (cand < old) want = atomicExch(qflag + v, tag) != tag;
-          }
+  __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
+                                      const int2 *ed, const u64 *sx) {
+    const int lane = threadIdx.x & 31;
+    u32 tx[K];
+    bool want[K];
+    int nw = 0;
+    u32 bv = kNoEdge;
+    u64 best = ~0ull;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      want[k] = false;
+      tx[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (act[k]) {
+        ++n_edges;
+        u64 cand = ~0ull;
+        const u32 dx = dist_of(sx[k]);
+        if (dx < kInf) {
+          const u32 nd = dx + (u32)ed[k].y;
+          if (nd >= kInf) range_err = 1;
+          else cand = pack(nd, (u32)ed[k].x);
         }
+        if (ov[k] != bv) {           // owner changed inside this lane's run
+          if (bv != kNoEdge && offer(bv, best)) {
+            tx[nw] = bv;
+            want[nw] = true;
+            ++nw;
+          }
+          bv = ov[k];
+          best = ~0ull;
+        }
+        if (cand < best) best = cand;
       }
     }
-    enq.push(want, v);
+    // segmented minimum over the lanes that end on the same vertex
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = shfl64_down(best, o);
+      const u32 yv = __shfl_down_sync(kFull, bv, o);
+      if (lane + o < 32 && yv == bv && y < best) best = y;
+    }
+    const u32 pv = __shfl_up_sync(kFull, bv, 1);
+    const bool head = bv != kNoEdge && (lane == 0 || pv != bv);
+    if (head && nw < K && offer(bv, best)) {
+      tx[nw] = bv;
+      want[nw] = true;
+      ++nw;
+    }
+    enqueue(next, row, tx, want, K, n_enq);
   }
 };
 
-// --- frontier expansion ---------------------------------------------------
+// --- chunk expansion --------------------------------------------------------
 
-// One warp expands up to 32 queued vertices: a warp scan of their degrees
-// maps the concatenated edge lists onto lanes 32 edges at a time, so rows of
-// any length up to kHeavyDeg share the warp without divergence.
-template <class Op, bool kDefer>
-__device__ __forceinline__ void expand_group(Op &op, const u32 *q, u32 count, u32 group,
-                                             const Store &st, WarpSmem &ws) {
+// Expand edge chunk `chunk` of a frontier (ent/own, n_ent entries, n_edges
+// edges) over store `st`: lane L takes edges [e0 + K*L, e0 + K*L + K).
+template <class Op>
+__device__ __forceinline__ void process_chunk(Op &op, const int2 *ent, const u32 *own, u32 n_ent,
+                                              u32 n_edges, u32 chunk, const Store &st, int n,
+                                              Ctl *c) {
   const int lane = threadIdx.x & 31;
-  const u32 idx = group * 32 + lane;
-  u32 v = 0, dv = 0;
-  int deg = 0;
-  long long start = 0;
-  if (idx < count) {
-    v = ld_cg_u32(q + idx);
-    if (v >= (u32)op.n) {  // never expected: record and skip
-      atomicExch(&op.c->bad, 1);
-      v = 0;
+  const u32 e0 = chunk * kChunk;
+  const u32 e_end = e0 + kChunk < n_edges ? e0 + kChunk : n_edges;
+  const u32 jw = __ldcg(own + chunk);
+  // window: the 32 entries from the one holding e0
+  const u32 wj = jw + lane;
+  u32 wv = 0, web = kNoEdge, wdeg = 0, wd = 0;
+  long long wstart = 0;
+  if (wj < n_ent) {
+    const int2 en = __ldcg(ent + wj);
+    wv = (u32)en.x;
+    web = (u32)en.y;
+    if (wv < (u32)n) {
+      const RowMeta rm = st.row[wv];
+      wdeg = (u32)rm.deg;
+      wstart = rm.start;
+      wd = op.vdata(wv);
+    } else {                             // never expected: record and skip
+      atomicExch(&c->bad, 1);
+      wv = 0;
+      web = kNoEdge;
     }
+  }
+  const u32 l31 = __shfl_sync(kFull, web == kNoEdge ? kNoEdge : web + wdeg, 31);
+  const u32 wend = l31 == kNoEdge ? n_edges : l31;
+  const u32 ebeg = e0 + (u32)(K * lane);
+  // owner of ebeg inside the window: last lane whose first edge <= ebeg
+  int o = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const u32 ebc = __shfl_sync(kFull, web, (o + step) & 31);
+    if (o + step < 32 && ebc <= ebeg) o += step;
+  }
+  u32 slot = jw + (u32)o;
+  u32 v = __shfl_sync(kFull, wv, o), eb = __shfl_sync(kFull, web, o);
+  u32 deg = __shfl_sync(kFull, wdeg, o), dv = __shfl_sync(kFull, wd, o);
+  long long start = (long long)shfl64((u64)wstart, o);
+  if (ebeg < e_end && ebeg >= wend) {
+    // beyond the window (many tiny rows in one chunk): search the queue
+    u32 lo = jw, hi = n_ent - 1;
+    while (lo < hi) {
+      const u32 mid = (lo + hi + 1) >> 1;
+      if ((u32)__ldcg(&ent[mid].y) <= ebeg) lo = mid; else hi = mid - 1;
+    }
+    slot = lo;
+    const int2 en = __ldcg(ent + slot);
+    v = (u32)en.x;
+    eb = (u32)en.y;
     const RowMeta rm = st.row[v];
-    if (op.vertex(v, dv)) {
-      deg = rm.deg;
-      start = rm.start;
-    }
-    if constexpr (kDefer) {
-      if (deg > kHeavyDeg) {
-        op.defer(v, deg);
-        deg = 0;
+    deg = (u32)rm.deg;
+    start = rm.start;
+    dv = op.vdata(v);
+    o = 32;
+  }
+  bool act[K];
+  u32 ov[K], od[K];
+  int2 ed[K];
+  u64 sx[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const u32 e = ebeg + (u32)k;
+    act[k] = e < e_end;
+    const int nl = (o + 1) & 31;
+    const u32 nv = __shfl_sync(kFull, wv, nl), neb = __shfl_sync(kFull, web, nl);
+    const u32 ndeg = __shfl_sync(kFull, wdeg, nl), nd = __shfl_sync(kFull, wd, nl);
+    const long long nstart = (long long)shfl64((u64)wstart, nl);
+    if (act[k] && e >= eb + deg) {  // next entry (entries are contiguous in edge space)
+      ++slot;
+      if (o + 1 < 32) {
+        ++o;
+        v = nv; eb = neb; deg = ndeg; dv = nd; start = nstart;
+      } else {
+        const int2 en = __ldcg(ent + slot);
+        v = (u32)en.x;
+        eb = (u32)en.y;
+        const RowMeta rm = st.row[v];
+        deg = (u32)rm.deg;
+        start = rm.start;
+        dv = op.vdata(v);
+        o = 32;
       }
     }
+    ov[k] = v;
+    od[k] = dv;
+    ed[k] = act[k] ? __ldg(st.adj + start + (e - eb)) : make_int2(0, 0);
   }
-  const u32 incl = warp_incl_scan((u32)deg);
-  const u32 total = __shfl_sync(0xffffffffu, incl, 31);
-  ws.excl[lane] = incl - (u32)deg;
-  ws.v[lane] = v;
-  ws.d[lane] = dv;
-  ws.start[lane] = start;
-  __syncwarp();
-  for (u32 e = 0; e < total; e += 32) {
-    const u32 k = e + lane;
-    const bool act = k < total;
-    int o = 0;
-    int2 ed = make_int2(0, 0);
-    if (act) {
-      o = find_owner(ws.excl, k);
-      ed = __ldg(st.adj + ws.start[o] + (k - ws.excl[o]));
-    }
-    op.edge(act, ws.v[o], ws.d[o], ed.x, ed.y);
-  }
-  __syncwarp();
-}
-
-// One warp expands chunk `chunk` (kChunk edges) of a heavy queue entry.
-template <class Op>
-__device__ __forceinline__ void expand_chunk(Op &op, const int2 *hq, u32 nheavy, u32 chunk,
-                                             const Store &st) {
-  const int lane = threadIdx.x & 31;
-  int lo = 0, hi = (int)nheavy - 1;  // last entry whose first chunk <= chunk
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((u32)__ldcg(&hq[mid].y) <= chunk) lo = mid; else hi = mid - 1;
-  }
-  const int2 h = __ldcg(hq + lo);
-  u32 v = (u32)h.x;
-  if (nheavy == 0 || v >= (u32)op.n) {  // never expected: record and skip
-    atomicExch(&op.c->bad, 1);
-    return;
-  }
-  const long long e0 = (long long)(chunk - (u32)h.y) * kChunk;
-  const RowMeta rm = st.row[v];
-  u32 dv = 0;
-  long long cnt = 0;
-  if (op.vertex(v, dv)) {
-    cnt = (long long)rm.deg - e0;
-    if (cnt > kChunk) cnt = kChunk;
-  }
-#pragma unroll 2
-  for (int t = 0; t < kChunk; t += 32) {
-    const int kk = t + lane;
-    const bool act = kk < cnt;
-    int2 ed = make_int2(0, 0);
-    if (act) ed = __ldg(st.adj + rm.start + e0 + kk);
-    op.edge(act, v, dv, ed.x, ed.y);
-  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) sx[k] = act[k] ? op.load(ed[k]) : 0ull;
+  op.run(act, ov, od, ed, sx);
 }
 
 __device__ __forceinline__ bool repair_enabled(Ctl *c) {
@@ -389,90 +435,87 @@ __device__ __forceinline__ bool repair_enabled(Ctl *c) {
          ld_cg_i32(&c->timeout) == 0 && ld_cg_i32(&c->bad) == 0;
 }
 
+__device__ __forceinline__ Queue make_queue(int2 *ent, u32 *own, u64 *cnt) {
+  Queue q;
+  q.ent = ent;
+  q.owner = own;
+  q.cnt = (unsigned long long *)cnt;
+  return q;
+}
+
 // --- persistent loop ------------------------------------------------------
 
 template <int OP>
-__global__ void __launch_bounds__(kLoopThreads) k_loop(LoopArgs a) {
-  __shared__ WarpSmem ws[kWarps];
+__global__ void __launch_bounds__(kLoopThreads, 2) k_loop(LoopArgs a) {
   Ctl *c = a.ctl;
   if (!repair_enabled(c)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u64 n_vert = 0, n_edges = 0, n_imp = 0, n_enq = 0;
+  const int lane = threadIdx.x & 31;
+  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  u64 n_edges = 0, n_imp = 0, n_enq = 0, n_aff = 0;
   int range_err = 0;
 
   if (OP == kOpInval && a.n_del > 0) {
     // OnDelete: a deleted edge u -> v that is v's parent edge invalidates v.
-    Enqueuer enq{c, a.qlight[0], a.qheavy[0], &c->light_cnt[0], &c->heavy_cnt[0], a.fwd.row,
-                 a.alist};
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long base = gw * 32; base < a.n_del; base += nw * 32) {
+    const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0);
+    const Queue qa = make_queue(a.aent, a.aown, &c->acnt);
+    for (long long base = (long long)gw * 32; base < a.n_del; base += (long long)nw * 32) {
       const long long i = base + lane;
-      bool hit = false;
-      u32 v = 0;
+      bool hit[K] = {};
+      u32 v[K] = {};
       if (i < a.n_del) {
         const u32 u = (u32)a.del_src[i];
-        v = (u32)a.del_dst[i];
-        const u64 sv = ld_cg_u64(a.s + v);
+        v[0] = (u32)a.del_dst[i];
+        const u64 sv = ld_cg_u64(a.s + v[0]);
         if (parent_of(sv) == u)
-          hit = atomicCAS((unsigned long long *)(a.s + v), sv, kInfPack) == sv;
+          hit[0] = atomicCAS((unsigned long long *)(a.s + v[0]), sv, kInfPack) == sv;
       }
-      enq.push(hit, v);
+      n_aff += hit[0];
+      enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
+      u64 dummy = 0;
+      enqueue(qa, a.rev.row, v, hit, 1, dummy);
     }
-    n_enq += enq.n_enq;
   }
 
   grid_barrier(c, a.lim, [&] { serial_advance(c, a.lim, true, OP); });
   for (;;) {
     if (ld_cg_u32(&c->done) || ld_cg_i32(&c->timeout)) break;
     const u32 cur = ld_cg_u32(&c->cur), nxt = cur ^ 1u;
-    const u32 nl = ld_cg_u32(&c->light_cnt[cur]);
-    const u32 nlg = ld_cg_u32(&c->n_light_groups);
-    const u32 tot = ld_cg_u32(&c->work_total);
-    const u32 nh = ld_cg_u32(&c->n_heavy);
+    const u32 ne = ld_cg_u32(&c->n_ent), nedge = ld_cg_u32(&c->n_edges);
+    const u32 nch = ld_cg_u32(&c->n_chunks);
     const u32 tag = ld_cg_u32(&c->epoch);
-    Enqueuer enq{c, a.qlight[nxt], a.qheavy[nxt], &c->light_cnt[nxt], &c->heavy_cnt[nxt],
-                 a.fwd.row, OP == kOpInval ? a.alist : nullptr};
+    const Queue qn = make_queue(a.qent[nxt], a.qown[nxt], nxt ? &c->qcnt1 : &c->qcnt0);
     if (OP == kOpPush) {
-      PushOp op{a.s, a.qflag, tag, enq, c, a.n};
-      for (;;) {
-        u32 item = 0;
-        if (lane == 0) item = atomicAdd(&c->work_next, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= tot) break;
-        if (item < nlg) expand_group<PushOp, false>(op, a.qlight[cur], nl, item, a.fwd, ws[warp]);
-        else expand_chunk(op, a.qheavy[cur], nh, item - nlg, a.fwd);
-      }
-      n_vert += op.n_vert; n_edges += op.n_edges; n_imp += op.n_imp;
-      n_enq += op.enq.n_enq; range_err |= op.range_err;
+      PushOp op{a.s, a.qflag, tag, qn, a.fwd.row};
+      for (u32 ch = gw; ch < nch; ch += nw)
+        process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, ch, a.fwd, a.n, c);
+      n_edges += op.n_edges;
+      n_imp += op.n_imp;
+      n_enq += op.n_enq;
+      range_err |= op.range_err;
     } else {
-      InvalOp op{a.s, enq, c, a.n};
-      for (;;) {
-        u32 item = 0;
-        if (lane == 0) item = atomicAdd(&c->work_next, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= tot) break;
-        if (item < nlg) expand_group<InvalOp, false>(op, a.qlight[cur], nl, item, a.fwd, ws[warp]);
-        else expand_chunk(op, a.qheavy[cur], nh, item - nlg, a.fwd);
-      }
-      n_vert += op.n_vert; n_edges += op.n_edges; n_enq += op.enq.n_enq;
+      InvalOp op{a.s, qn, make_queue(a.aent, a.aown, &c->acnt), a.fwd.row, a.rev.row};
+      for (u32 ch = gw; ch < nch; ch += nw)
+        process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, ch, a.fwd, a.n, c);
+      n_edges += op.n_edges;
+      n_enq += op.n_enq;
+      n_aff += op.n_aff;
     }
     grid_barrier(c, a.lim, [&] { serial_advance(c, a.lim, false, OP); });
   }
-  n_vert = warp_sum(n_vert);
   n_edges = warp_sum(n_edges);
   n_imp = warp_sum(n_imp);
   n_enq = warp_sum(n_enq);
-  range_err = __any_sync(0xffffffffu, range_err);
+  n_aff = warp_sum(n_aff);
+  range_err = __any_sync(kFull, range_err);
   if (lane == 0) {
     if (OP == kOpPush) {
-      if (n_vert) atomicAdd(&c->push_vertices, n_vert);
       if (n_edges) atomicAdd(&c->relaxed, n_edges);
       if (n_imp) atomicAdd(&c->improved, n_imp);
       if (n_enq) atomicAdd(&c->enqueued, n_enq);
     } else {
       if (n_edges) atomicAdd(&c->inval_edges, n_edges);
-      if (n_enq) atomicAdd(&c->affected, n_enq);
+      if (n_aff) atomicAdd(&c->affected, n_aff);
     }
     if (range_err) atomicExch(&c->range_err, 1);
   }
@@ -481,45 +524,20 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop(LoopArgs a) {
 // --- pull (one pass over A) -----------------------------------------------
 
 __global__ void __launch_bounds__(kLoopThreads) k_pull(LoopArgs a) {
-  __shared__ WarpSmem ws[kWarps];
-  Ctl *c = a.ctl;
-  if (!repair_enabled(c)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 na = ld_cg_u32(&c->a_count);
-  const u32 groups = (na + 31) / 32;
-  const u32 tag = ld_cg_u32(&c->epoch);
-  Enqueuer enq{c, a.qlight[0], a.qheavy[0], &c->light_cnt[0], &c->heavy_cnt[0], a.fwd.row,
-               nullptr};
-  PullOp op{a.s, a.qflag, tag, enq, c, a.n, a.qheavy[1], &c->pull_heavy};
-  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 g = gw; g < groups; g += nw)
-    expand_group<PullOp, true>(op, a.alist, na, g, a.rev, ws[warp]);
-  u64 e = warp_sum(op.n_edges), q = warp_sum(op.enq.n_enq);
-  int re = __any_sync(0xffffffffu, op.range_err);
-  if (lane == 0) {
-    if (e) atomicAdd(&c->pull_edges, e);
-    if (q) atomicAdd(&c->seeds, q);
-    if (re) atomicExch(&c->range_err, 1);
-  }
-}
-
-__global__ void __launch_bounds__(kLoopThreads) k_pull_heavy(LoopArgs a) {
   Ctl *c = a.ctl;
   if (!repair_enabled(c)) return;
   const int lane = threadIdx.x & 31;
-  const u64 hv = ld_cg_u64(&c->pull_heavy);
-  const u32 nh = (u32)(hv >> 40), chunks = (u32)(hv & kMask40);
-  if (chunks == 0) return;
+  const u64 ac = ld_cg_u64(&c->acnt);
+  const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
+  const u32 nch = (nedge + kChunk - 1) / kChunk;
   const u32 tag = ld_cg_u32(&c->epoch);
-  Enqueuer enq{c, a.qlight[0], a.qheavy[0], &c->light_cnt[0], &c->heavy_cnt[0], a.fwd.row,
-               nullptr};
-  PullOp op{a.s, a.qflag, tag, enq, c, a.n, nullptr, nullptr};
+  PullOp op{a.s, a.qflag, tag, make_queue(a.qent[0], a.qown[0], &c->qcnt0), a.fwd.row};
   const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 ch = gw; ch < chunks; ch += nw) expand_chunk(op, a.qheavy[1], nh, ch, a.rev);
-  u64 e = warp_sum(op.n_edges), q = warp_sum(op.enq.n_enq);
-  int re = __any_sync(0xffffffffu, op.range_err);
+  for (u32 ch = gw; ch < nch; ch += nw)
+    process_chunk(op, a.aent, a.aown, ne, nedge, ch, a.rev, a.n, c);
+  u64 e = warp_sum(op.n_edges), q = warp_sum(op.n_enq);
+  int re = __any_sync(kFull, op.range_err);
   if (lane == 0) {
     if (e) atomicAdd(&c->pull_edges, e);
     if (q) atomicAdd(&c->seeds, q);
@@ -543,22 +561,22 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
   if (!repair_enabled(c)) return;
   const int lane = threadIdx.x & 31;
   const u32 tag = ld_cg_u32(&c->epoch);
-  Enqueuer enq{c, a.la.qlight[0], a.la.qheavy[0], &c->light_cnt[0], &c->heavy_cnt[0],
-               a.la.fwd.row, nullptr};
+  const Queue q0 = make_queue(a.la.qent[0], a.la.qown[0], &c->qcnt0);
   const u64 cmask = (1ull << a.bits) - 1;
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   int range_err = 0;
+  u64 n_enq = 0;
   for (long long base = gw * 32; base < a.n_items; base += nw * 32) {
     const long long i = base + lane;
-    bool want = false;
-    u32 v = 0;
+    bool want[K] = {};
+    u32 v[K] = {};
     if (i < a.n_items) {
       const u64 key = a.keys[i];
       // forward-store insertion that the merge applied
       if ((key >> (2 * a.bits + 1)) == 0 && (key & 1) && (a.flags[i] & 1)) {
         const u32 u = (u32)((key >> (a.bits + 1)) & cmask);
-        v = (u32)((key >> 1) & cmask);
+        v[0] = (u32)((key >> 1) & cmask);
         const u32 du = dist_of(ld_cg_u64(a.la.s + u));
         if (du < kInf) {
           const u32 nd = du + a.vals[i];
@@ -566,18 +584,18 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
             range_err = 1;
           } else {
             const u64 cand = pack(nd, u);
-            if (cand < ld_cg_u64(a.la.s + v)) {
-              const u64 old = atomicMin((unsigned long long *)(a.la.s + v), cand);
-              if (cand < old) want = atomicExch(a.la.qflag + v, tag) != tag;
+            if (cand < ld_cg_u64(a.la.s + v[0])) {
+              const u64 old = atomicMin((unsigned long long *)(a.la.s + v[0]), cand);
+              if (cand < old) want[0] = atomicExch(a.la.qflag + v[0], tag) != tag;
             }
           }
         }
       }
     }
-    enq.push(want, v);
+    enqueue(q0, a.la.fwd.row, v, want, 1, n_enq);
   }
-  u64 q = warp_sum(enq.n_enq);
-  int re = __any_sync(0xffffffffu, range_err);
+  u64 q = warp_sum(n_enq);
+  int re = __any_sync(kFull, range_err);
   if (lane == 0) {
     if (q) atomicAdd(&c->seeds, q);
     if (re) atomicExch(&c->range_err, 1);
@@ -586,21 +604,18 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
 
 // --- from-scratch init, unpack ----------------------------------------------
 
-__global__ void k_init(u64 *s, int n, int src, Ctl *c, u32 *qflag, u32 *ql, int2 *qh,
+__global__ void k_init(u64 *s, int n, int src, Ctl *c, u32 *qflag, int2 *qent, u32 *qown,
                        const RowMeta *row) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x)
     s[v] = v == src ? pack(0, kNoParent) : kInfPack;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const u32 tag = c->epoch;
-    qflag[src] = tag;
+    qflag[src] = c->epoch;
     const int d = row[src].deg;
-    if (d > kHeavyDeg) {
-      qh[0] = make_int2(src, 0);
-      c->heavy_cnt[0] = (1ull << 40) | (u64)((d + kChunk - 1) / kChunk);
-    } else {
-      ql[0] = (u32)src;
-      c->light_cnt[0] = 1;
+    if (d > 0) {
+      qent[0] = make_int2(src, 0);
+      for (u32 ch = 0; ch <= (u32)(d - 1) / kChunk; ++ch) qown[ch] = 0;
+      c->qcnt0 = (1ull << 32) | (u64)d;
     }
     c->seeds = 1;
   }
@@ -623,11 +638,12 @@ LoopArgs make_args(sp_graph *g) {
   a.rev = g->rev;
   a.s = g->s;
   a.qflag = g->qflag;
-  a.qlight[0] = g->qlight[0];
-  a.qlight[1] = g->qlight[1];
-  a.qheavy[0] = g->qheavy[0];
-  a.qheavy[1] = g->qheavy[1];
-  a.alist = g->alist;
+  a.qent[0] = g->qent[0];
+  a.qent[1] = g->qent[1];
+  a.qown[0] = g->qown[0];
+  a.qown[1] = g->qown[1];
+  a.aent = g->aent;
+  a.aown = g->aown;
   a.n = g->n;
   a.del_src = nullptr;
   a.del_dst = nullptr;
@@ -648,7 +664,7 @@ int loop_blocks(int which, int num_sms) {
 
 void launch_init(sp_graph *g, int source, int *launches) {
   k_init<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(
-      g->s, g->n, source, g->ctl, g->qflag, g->qlight[0], g->qheavy[0], g->fwd.row);
+      g->s, g->n, source, g->ctl, g->qflag, g->qent[0], g->qown[0], g->fwd.row);
   ++*launches;
 }
 
@@ -670,10 +686,8 @@ cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd
 
 void launch_pull(sp_graph *g, int *launches) {
   LoopArgs a = make_args(g);
-  const unsigned grid = (unsigned)std::max(1, g->num_sms * 8);
-  k_pull<<<grid, kLoopThreads, 0, g->stream>>>(a);
-  k_pull_heavy<<<grid, kLoopThreads, 0, g->stream>>>(a);
-  *launches += 2;
+  k_pull<<<(unsigned)std::max(1, g->num_sms * 4), kLoopThreads, 0, g->stream>>>(a);
+  ++*launches;
 }
 
 void launch_add(sp_graph *g, long long n_items, int *launches) {
@@ -686,7 +700,7 @@ void launch_add(sp_graph *g, long long n_items, int *launches) {
   a.n_items = n_items;
   a.bits = g->bits;
   long long blocks = (n_items + kLoopThreads - 1) / kLoopThreads;
-  blocks = std::min<long long>(std::max<long long>(blocks, 1), g->num_sms * 16);
+  blocks = std::min<long long>(std::max<long long>(blocks, 1), g->num_sms * 8);
   k_add<<<(unsigned)blocks, kLoopThreads, 0, g->stream>>>(a);
   ++*launches;
 }

@@ -6,12 +6,20 @@
 
 namespace sp {
 
-// Frontier queue sizing: a vertex whose row holds more than kHeavyDeg edges
-// is expanded in chunks of kChunk edges spread over many warps; lighter
-// vertices are expanded 32 at a time by one warp.
-constexpr int kHeavyDeg = 256;
+// Frontier expansion: every queued vertex reserves a range of the round's
+// edge space when it is enqueued; the round is then processed in chunks of
+// kChunk edges, one warp per chunk, 8 consecutive edges per lane.
 constexpr int kChunk = 256;
-constexpr int kLoopThreads = 256;
+constexpr int kEdgesPerLane = kChunk / 32;
+constexpr int kLoopThreads = 512;
+
+// A frontier queue: entries (v, first edge) in slot order, and for every
+// chunk the slot of the entry holding the chunk's first edge.
+struct Queue {
+  int2 *ent = nullptr;
+  u32 *owner = nullptr;
+  unsigned long long *cnt = nullptr;   // count << 32 | edges (in Ctl)
+};
 
 // One touched (store, row) pair of a batch, after sorting.
 struct Seg {
@@ -20,8 +28,11 @@ struct Seg {
   int dir;               // 0 = forward store, 1 = reverse store
   long long dest;        // slot where the merged row is written
   long long scratch;     // scratch slot for a large in-place merge, else -1
+  long long old_start;   // the row's slots before the merge
+  int old_deg;
   int new_deg;
   int new_cap;
+  int tier;              // 0 warp, 1 block, 2 chunked
 };
 
 // Per-call buffers that grow on demand.
@@ -34,7 +45,9 @@ struct BatchBufs {
   u64 *item_pref = nullptr;         // exclusive scan of itemv
   u32 *head = nullptr, *head_scan = nullptr;
   Seg *seg = nullptr;
-  u32 *small_list = nullptr, *large_list = nullptr;
+  u32 *small_list = nullptr, *medium_list = nullptr;
+  u32 *large_list = nullptr, *large_cb = nullptr;   // large tier + first chunk
+  u32 *copy_list = nullptr, *copy_cb = nullptr;     // scratch copy-back
   void *tmp = nullptr;
   size_t tmp_bytes = 0;
   long long cap_in = 0;             // staging for host inputs
@@ -44,16 +57,17 @@ struct BatchBufs {
   long long scratch_cap = 0;
 };
 
-// Arguments of the persistent frontier loops.
+// Arguments of the frontier kernels.
 struct LoopArgs {
   Ctl *ctl;
   Limits lim;
   Store fwd, rev;
   u64 *s;
   u32 *qflag;
-  u32 *qlight[2];
-  int2 *qheavy[2];
-  u32 *alist;
+  int2 *qent[2];         // frontier double buffer
+  u32 *qown[2];
+  int2 *aent;            // affected list A (entries carry reverse edges)
+  u32 *aown;
   int n;
   // fused OnDelete mark (invalidation loop only)
   const int *del_src, *del_dst;
@@ -74,9 +88,11 @@ struct sp_graph {
   long long m = 0;
   sp::u64 *s = nullptr;
   sp::u32 *qflag = nullptr;
-  sp::u32 *qlight[2] = {nullptr, nullptr};
-  int2 *qheavy[2] = {nullptr, nullptr};
-  sp::u32 *alist = nullptr;
+  int2 *qent[2] = {nullptr, nullptr};
+  sp::u32 *qown[2] = {nullptr, nullptr};
+  int2 *aent = nullptr;
+  sp::u32 *aown = nullptr;
+  long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device
   sp::Ctl *ctl_host = nullptr;  // pinned
   int *out_dist = nullptr, *out_parent = nullptr;
@@ -99,6 +115,7 @@ sp_status store_build(sp_graph *g, sp::Store *st, const long long *row_off_d,
 sp_status store_export(sp_graph *g, const sp::Store *st, long long *row_off_d,
                        int *col_d, int *w_d, int *launches);
 sp_status store_grow_pool(sp_graph *g, sp::Store *st, long long min_pool_slots);
+sp_status ensure_owner_tables(sp_graph *g);
 void launch_ctl_reset(sp_graph *g, int full, int *launches);
 void launch_prep(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
                  const int *ad, const int *aw, long long na, int *launches);

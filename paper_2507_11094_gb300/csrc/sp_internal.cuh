@@ -58,6 +58,8 @@ enum : int {
   kGrowScratch = 4,
 };
 
+// Fields that many SMs hit at once (barrier words, queue counters) sit on
+// cache lines of their own so that polling one does not slow the others.
 struct Ctl {
   int status;            // sp_status of the running call (0 = ok)
   int need_grow;         // kGrow* bits: a buffer was too small, nothing changed
@@ -65,34 +67,31 @@ struct Ctl {
   int timeout;           // 1 = round cap, 2 = barrier wait bound
   int bad;               // an internal bounds check failed (write skipped)
   // grid barrier (persistent kernels)
-  u32 bar_arrive;
-  u32 bar_gen;
-  // frontier state of the persistent loops
-  u32 cur;               // which queue buffer is current (0/1)
+  alignas(128) u32 bar_arrive;
+  alignas(128) u32 bar_gen;
+  // round state, written by the serial step between rounds
+  alignas(128) u32 cur;  // which frontier buffer is current (0/1)
   u32 round;
   u32 done;
   u32 epoch;             // dedupe tag of the frontier being built
-  u32 light_cnt[2];      // light queue sizes
-  u32 pad0;
-  u64 heavy_cnt[2];      // heavy queue: count << 40 | chunks
-  u32 work_next;         // dynamic work counter of the current round
-  u32 work_total;        // work items in the current round
-  u32 n_light_groups;    // light groups in the current round
-  u32 pad1;
-  // invalidation list A
-  u32 a_count;           // entries appended so far
-  u32 a_lo, a_hi;        // current round's slice of A
-  u32 pad2;
+  u32 n_ent;             // entries of the current frontier
+  u32 n_edges;           // edges of the current frontier
+  u32 n_chunks;          // edge chunks of the current frontier
+  // frontier counters (atomics): count << 32 | edges
+  alignas(128) u64 qcnt0;
+  alignas(128) u64 qcnt1;
+  alignas(128) u64 acnt;           // affected list A (reverse-store edges)
   // batch bookkeeping
-  u32 n_seg;             // touched (dir,row) segments
-  u32 n_small, n_large;  // segments merged by one warp / by one block
-  u32 n_heavy;           // heavy queue entries of the current round
-  u64 pull_heavy;        // deferred pull rows: count << 40 | chunks
+  alignas(128) u32 n_seg;          // touched (dir,row) segments
+  u32 n_small, n_medium;           // segments of the warp / block merge tiers
+  u64 large_pack;                  // large tier: count << 40 | chunks
+  u64 copy_pack;                   // scratch copy-back: count << 40 | chunks
   u64 pool_used[2];      // spare slots taken (fwd, rev), persistent
   u64 pool_need[2];      // demand seen by the last count pass
   u64 scratch_used;      // merge scratch slots reserved this batch
   // counters of the call
-  u64 del_applied, del_absent, add_applied, add_present;
+  alignas(128) u64 del_applied;
+  u64 del_absent, add_applied, add_present;
   u64 affected, seeds, relaxed, improved, rows_touched, rows_relocated;
   u64 inval_edges, pull_edges, push_vertices, enqueued;
   u64 merge_slots;       // old + new slots of all merged rows

@@ -165,12 +165,10 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->cur = 0;
   c->round = 0;
   c->done = 0;
-  c->light_cnt[0] = c->light_cnt[1] = 0;
-  c->heavy_cnt[0] = c->heavy_cnt[1] = 0;
-  c->work_next = c->work_total = c->n_light_groups = 0;
-  c->a_count = c->a_lo = c->a_hi = 0;
-  c->n_seg = c->n_small = c->n_large = c->n_heavy = 0;
-  c->pull_heavy = 0;
+  c->n_ent = c->n_edges = c->n_chunks = 0;
+  c->qcnt0 = c->qcnt1 = c->acnt = 0;
+  c->n_seg = c->n_small = c->n_medium = 0;
+  c->large_pack = c->copy_pack = 0;
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
   c->scratch_used = 0;
@@ -253,6 +251,12 @@ __global__ void k_seg_emit(const u64 *__restrict__ keys, const u32 *__restrict__
 // batch: count pass (which updates apply, new row sizes, where rows go)
 // --------------------------------------------------------------------------
 
+constexpr int kMedRow = 4096;      // rows merged in place by one block
+constexpr int kMedThreads = 512;
+constexpr int kMedPer = kMedRow / kMedThreads;
+constexpr int kLargeChunk = 4096;  // elements per block in the chunked tier
+constexpr u64 kMask40 = (1ull << 40) - 1;
+
 // First slot j in [0, deg) of a sorted row with row[j].x >= c.
 __device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) {
   int lo = 0, hi = deg;
@@ -279,7 +283,8 @@ struct CountArgs {
   Seg *seg;
   unsigned char *flags;
   u64 *itemv;
-  u32 *small_list, *large_list;
+  const u64 *item_pref;
+  u32 *small_list, *medium_list, *large_list, *large_cb, *copy_list, *copy_cb;
   Store st[2];
   int bits;
   float slack;
@@ -288,111 +293,147 @@ struct CountArgs {
   int n;
 };
 
-__global__ void __launch_bounds__(kThreads) k_count(CountArgs a) {
+// One thread per batch item: does this deletion / insertion apply?
+//  - a deletion applies if the edge is in the row and it is the first
+//    deletion of that edge in the batch;
+//  - among the insertions of one edge the smallest weight is the candidate
+//    (first on ties); it applies if the edge is absent after the deletions.
+__global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
   Ctl *c = a.ctl;
   if (ld_cg_i32(&c->status) != 0) return;
   const int lane = threadIdx.x & 31;
-  const u32 nseg = ld_cg_u32(&c->n_seg);
-  const u32 warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u32 nwarps = (gridDim.x * blockDim.x) >> 5;
   const u64 cmask = (1ull << a.bits) - 1;
-  u64 tot_del_ok = 0, tot_del_abs = 0, tot_add_ok = 0, tot_add_pres = 0;
-  u64 touched = 0, relocated = 0, slots = 0;
-  for (u32 si = warp0; si < nseg; si += nwarps) {
-    Seg sg = a.seg[si];
-    if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
-        sg.dir < 0 || sg.dir > 1) {  // never expected: record and stop
-      if (lane == 0) atomicExch(&c->bad, 1);
-      return;
-    }
-    const Store &st = a.st[sg.dir];
-    const RowMeta rm = st.row[sg.row];
-    const int2 *old = st.adj + rm.start;
-    int del_ok = 0, add_ok = 0;
-    for (u32 i = sg.first + lane; i < sg.end; i += 32) {
+  u64 del_ok = 0, del_abs = 0, add_ok = 0, add_pres = 0;
+  const long long ni = a.n_items;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ni;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    if (i < ni) {
       const u64 key = a.keys[i];
+      const int dir = (int)(key >> (2 * a.bits + 1));
+      const int row = (int)((key >> (a.bits + 1)) & cmask);
       const int col = (int)((key >> 1) & cmask);
+      const Store &st = a.st[dir];
+      const RowMeta rm = st.row[row];
+      const int2 *old = st.adj + rm.start;
       const int j = row_lower_bound(old, rm.deg, col);
       const bool present = j < rm.deg && __ldg(&old[j].x) == col;
-      if ((key & 1) == 0) {  // deletion
-        const bool dup = i > sg.first && a.keys[i - 1] == key;
-        const bool applied = present && !dup;
+      if ((key & 1) == 0) {
+        const bool applied = present && !(i > 0 && a.keys[i - 1] == key);
         a.flags[i] = applied ? 1 : 0;
         a.itemv[i] = applied ? 1ull : 0ull;
-        del_ok += applied;
-        if (sg.dir == 0) { applied ? ++tot_del_ok : ++tot_del_abs; }
-      } else if (i == sg.first || a.keys[i - 1] != key) {  // first insertion of this edge
-        u32 j2 = i + 1, best = i;
+        if (dir == 0) { applied ? ++del_ok : ++del_abs; }
+      } else if (i == 0 || a.keys[i - 1] != key) {  // first insertion of this edge
+        long long j2 = i + 1, best = i;
         u32 bw = a.vals[i];
-        while (j2 < sg.end && a.keys[j2] == key) {
-          u32 w2 = a.vals[j2];
+        while (j2 < ni && a.keys[j2] == key) {
+          const u32 w2 = a.vals[j2];
           if (w2 < bw) { bw = w2; best = j2; }
           ++j2;
         }
-        const bool del_exists = i > sg.first && a.keys[i - 1] == (key ^ 1ull);
+        const bool del_exists = i > 0 && a.keys[i - 1] == (key ^ 1ull);
         const bool applied = !present || del_exists;
-        for (u32 t = i; t < j2; ++t) {
+        for (long long t = i; t < j2; ++t) {
           const bool on = applied && t == best;
           a.flags[t] = on ? 1 : 0;
           a.itemv[t] = on ? (1ull << 32) : 0ull;
         }
-        add_ok += applied;
-        if (sg.dir == 0) {
-          tot_add_ok += applied;
-          tot_add_pres += (j2 - i) - (applied ? 1 : 0);
+        if (dir == 0) {
+          add_ok += applied;
+          add_pres += (u64)(j2 - i) - (applied ? 1 : 0);
         }
       }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      del_ok += __shfl_xor_sync(0xffffffffu, del_ok, o);
-      add_ok += __shfl_xor_sync(0xffffffffu, add_ok, o);
-    }
-    if (lane == 0) {
-      const int new_deg = rm.deg - del_ok + add_ok;
-      const bool reloc = new_deg > rm.cap;
-      const bool small = rm.deg <= kSmallRow && (int)(sg.end - sg.first) <= kSmallItems;
-      sg.new_deg = new_deg;
-      sg.scratch = -1;
-      if (reloc) {
-        long long nc = row_capacity(new_deg, a.slack);
-        long long dbl = round_up4(2LL * rm.cap);
-        if (dbl > nc) nc = dbl;
-        u64 off = atomicAdd(&c->pool_need[sg.dir], (u64)nc);
-        if ((long long)(off + nc) > st.slots - st.main_slots)
-          atomicOr(&c->need_grow, sg.dir ? kGrowPoolRev : kGrowPoolFwd);
-        sg.dest = st.main_slots + (long long)off;
-        sg.new_cap = (int)nc;
-        ++relocated;
-      } else {
-        sg.dest = rm.start;
-        sg.new_cap = rm.cap;
-        if (!small) {
-          u64 off = atomicAdd(&c->scratch_used, (u64)new_deg);
-          if ((long long)(off + new_deg) > a.scratch_cap) atomicOr(&c->need_grow, kGrowScratch);
-          sg.scratch = (long long)off;
-        }
-      }
-      a.seg[si] = sg;
-      if (small) a.small_list[atomicAdd(&c->n_small, 1u)] = si;
-      else a.large_list[atomicAdd(&c->n_large, 1u)] = si;
-      ++touched;
-      slots += (u64)rm.deg + (u64)new_deg;
     }
   }
-  // flush counters
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    tot_del_ok += __shfl_xor_sync(0xffffffffu, tot_del_ok, o);
-    tot_del_abs += __shfl_xor_sync(0xffffffffu, tot_del_abs, o);
-    tot_add_ok += __shfl_xor_sync(0xffffffffu, tot_add_ok, o);
-    tot_add_pres += __shfl_xor_sync(0xffffffffu, tot_add_pres, o);
+    del_ok += __shfl_xor_sync(0xffffffffu, del_ok, o);
+    del_abs += __shfl_xor_sync(0xffffffffu, del_abs, o);
+    add_ok += __shfl_xor_sync(0xffffffffu, add_ok, o);
+    add_pres += __shfl_xor_sync(0xffffffffu, add_pres, o);
   }
   if (lane == 0) {
-    if (tot_del_ok) atomicAdd(&c->del_applied, tot_del_ok);
-    if (tot_del_abs) atomicAdd(&c->del_absent, tot_del_abs);
-    if (tot_add_ok) atomicAdd(&c->add_applied, tot_add_ok);
-    if (tot_add_pres) atomicAdd(&c->add_present, tot_add_pres);
+    if (del_ok) atomicAdd(&c->del_applied, del_ok);
+    if (del_abs) atomicAdd(&c->del_absent, del_abs);
+    if (add_ok) atomicAdd(&c->add_applied, add_ok);
+    if (add_pres) atomicAdd(&c->add_present, add_pres);
+  }
+}
+
+// One thread per touched row: new size (from the item prefix counts), merge
+// tier, destination (in place, or a fresh spare-pool segment when the row
+// outgrows its capacity), scratch and chunk reservations.
+__global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
+  Ctl *c = a.ctl;
+  if (ld_cg_i32(&c->status) != 0) return;
+  const int lane = threadIdx.x & 31;
+  const u32 nseg = ld_cg_u32(&c->n_seg);
+  u64 touched = 0, relocated = 0, slots = 0;
+  for (u32 base = blockIdx.x * blockDim.x; base < nseg; base += gridDim.x * blockDim.x) {
+    const u32 si = base + threadIdx.x;
+    if (si >= nseg) continue;
+    Seg sg = a.seg[si];
+    if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
+        sg.dir < 0 || sg.dir > 1) {  // never expected: record and skip
+      atomicExch(&c->bad, 1);
+      continue;
+    }
+    const Store &st = a.st[sg.dir];
+    const RowMeta rm = st.row[sg.row];
+    const u64 p = a.item_pref[sg.end] - a.item_pref[sg.first];
+    const int new_deg = rm.deg - (int)(u32)p + (int)(u32)(p >> 32);
+    const int nitems = (int)(sg.end - sg.first);
+    sg.old_start = rm.start;
+    sg.old_deg = rm.deg;
+    sg.new_deg = new_deg;
+    sg.scratch = -1;
+    sg.tier = (rm.deg <= kSmallRow && nitems <= kSmallItems) ? 0
+            : (rm.deg <= kMedRow && nitems <= kMedRow) ? 1 : 2;
+    const bool reloc = new_deg > rm.cap;
+    if (reloc) {
+      long long nc = row_capacity(new_deg, a.slack);
+      const long long dbl = round_up4(2LL * rm.cap);
+      if (dbl > nc) nc = dbl;
+      const u64 off = atomicAdd(&c->pool_need[sg.dir], (u64)nc);
+      if ((long long)(off + nc) > st.slots - st.main_slots)
+        atomicOr(&c->need_grow, sg.dir ? kGrowPoolRev : kGrowPoolFwd);
+      sg.dest = st.main_slots + (long long)off;
+      sg.new_cap = (int)nc;
+      ++relocated;
+    } else {
+      sg.dest = rm.start;
+      sg.new_cap = rm.cap;
+    }
+    if (sg.tier == 0) {
+      a.small_list[atomicAdd(&c->n_small, 1u)] = si;
+    } else if (sg.tier == 1) {
+      a.medium_list[atomicAdd(&c->n_medium, 1u)] = si;
+    } else {
+      if (!reloc && new_deg > 0) {  // written to scratch, then copied back
+        const u64 off = atomicAdd(&c->scratch_used, (u64)new_deg);
+        if ((long long)(off + new_deg) > a.scratch_cap) atomicOr(&c->need_grow, kGrowScratch);
+        sg.scratch = (long long)off;
+        const u64 nch = (u64)((new_deg + kLargeChunk - 1) / kLargeChunk);
+        const u64 o2 = atomicAdd((unsigned long long *)&c->copy_pack, (1ull << 40) | nch);
+        a.copy_list[o2 >> 40] = si;
+        a.copy_cb[o2 >> 40] = (u32)(o2 & kMask40);
+      }
+      const u64 nch = (u64)((rm.deg + nitems + kLargeChunk - 1) / kLargeChunk);
+      const u64 o = atomicAdd((unsigned long long *)&c->large_pack, (1ull << 40) | nch);
+      a.large_list[o >> 40] = si;
+      a.large_cb[o >> 40] = (u32)(o & kMask40);
+    }
+    a.seg[si] = sg;
+    ++touched;
+    slots += (u64)rm.deg + (u64)new_deg;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    touched += __shfl_xor_sync(0xffffffffu, touched, o);
+    relocated += __shfl_xor_sync(0xffffffffu, relocated, o);
+    slots += __shfl_xor_sync(0xffffffffu, slots, o);
+  }
+  if (lane == 0) {
     if (touched) atomicAdd(&c->rows_touched, touched);
     if (relocated) atomicAdd(&c->rows_relocated, relocated);
     if (slots) atomicAdd(&c->merge_slots, slots);
@@ -410,7 +451,7 @@ struct MergeArgs {
   const unsigned char *flags;
   const u64 *item_pref;   // exclusive scan of itemv, n_items + 1 entries
   const Seg *seg;
-  const u32 *list;
+  const u32 *list, *list_cb;
   Store st[2];
   int2 *scratch;
   int bits;
@@ -426,10 +467,10 @@ __device__ __forceinline__ bool merge_enabled(Ctl *c) {
 // and the applied insertions in col order.
 __device__ __forceinline__ int old_entry_pos(const MergeArgs &a, const Seg &sg, u64 prefix,
                                              u64 base_pref, int j, int c) {
-  u32 i = items_lower_bound(a.keys, sg.first, sg.end, prefix | ((u64)(unsigned)c << 1));
-  if (i < sg.end && a.keys[i] == (prefix | ((u64)(unsigned)c << 1)) && (a.flags[i] & 1))
-    return -1;  // applied deletion of this edge
-  u64 p = a.item_pref[i] - base_pref;
+  const u64 k = prefix | ((u64)(unsigned)c << 1);
+  const u32 i = items_lower_bound(a.keys, sg.first, sg.end, k);
+  if (i < sg.end && a.keys[i] == k && (a.flags[i] & 1)) return -1;  // applied deletion
+  const u64 p = a.item_pref[i] - base_pref;
   return j - (int)(u32)p + (int)(u32)(p >> 32);
 }
 
@@ -437,14 +478,23 @@ __device__ __forceinline__ int old_entry_pos(const MergeArgs &a, const Seg &sg, 
 __device__ __forceinline__ int add_entry_pos(const MergeArgs &a, const Seg &sg, u64 prefix,
                                              u64 base_pref, const int2 *old, int deg, u32 i,
                                              int c) {
-  int pos_old = row_lower_bound(old, deg, c);
-  u32 i0 = items_lower_bound(a.keys, sg.first, i, prefix | ((u64)(unsigned)c << 1));
-  u64 p0 = a.item_pref[i0] - base_pref;
-  u64 pi = a.item_pref[i] - base_pref;
+  const int pos_old = row_lower_bound(old, deg, c);
+  const u32 i0 = items_lower_bound(a.keys, sg.first, i, prefix | ((u64)(unsigned)c << 1));
+  const u64 p0 = a.item_pref[i0] - base_pref;
+  const u64 pi = a.item_pref[i] - base_pref;
   return pos_old - (int)(u32)p0 + (int)(u32)(pi >> 32);
 }
 
-// One warp per small row: all reads go to registers, then all writes.
+__device__ __forceinline__ void write_meta(const Store &st, const Seg &sg) {
+  RowMeta nm;
+  nm.start = sg.dest;
+  nm.deg = sg.new_deg;
+  nm.cap = sg.new_cap;
+  st.row[sg.row] = nm;
+}
+
+// Tier 0: one warp per row with deg <= 256 and <= 256 items.  All reads go to
+// registers before any write, so the row is rewritten in place.
 __global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
   Ctl *c = a.ctl;
   if (!merge_enabled(c)) return;
@@ -456,8 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
   for (u32 li = warp0; li < nlist; li += nwarps) {
     const Seg sg = a.seg[a.list[li]];
     const Store &st = a.st[sg.dir];
-    const RowMeta rm = st.row[sg.row];
-    const int2 *old = st.adj + rm.start;
+    const int2 *old = st.adj + sg.old_start;
     const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
     const u64 base_pref = a.item_pref[sg.first];
     int2 ent[kPerLane];
@@ -466,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
     for (int t = 0; t < kPerLane; ++t) {
       const int j = lane + 32 * t;
       pos[t] = -1;
-      if (j < rm.deg) {
+      if (j < sg.old_deg) {
         ent[t] = old[j];
         pos[t] = old_entry_pos(a, sg, prefix, base_pref, j, ent[t].x);
       }
@@ -480,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
       if (i < sg.end && (a.keys[i] & 1) && (a.flags[i] & 1)) {
         const int col = (int)((a.keys[i] >> 1) & cmask);
         aent[t] = make_int2(col, (int)a.vals[i]);
-        apos[t] = add_entry_pos(a, sg, prefix, base_pref, old, rm.deg, i, col);
+        apos[t] = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
       }
     }
     __syncwarp();
@@ -496,59 +545,136 @@ __global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
       }
     }
     if (bad) atomicExch(&c->bad, 1);
-    if (lane == 0) {
-      RowMeta nm;
-      nm.start = sg.dest;
-      nm.deg = sg.new_deg;
-      nm.cap = sg.new_cap;
-      st.row[sg.row] = nm;
-    }
+    if (lane == 0) write_meta(st, sg);
     __syncwarp();
   }
 }
 
-// One block per large row: written out of place (to its new pool slot, or to
-// scratch and then copied back), so no read can see a partial write.
-__global__ void __launch_bounds__(kThreads) k_merge_large(MergeArgs a) {
+// Tier 1: one block per row with deg <= 4096 and <= 4096 items, rewritten in
+// place: every thread holds its entries in registers across a block barrier.
+__global__ void __launch_bounds__(kMedThreads) k_merge_medium(MergeArgs a) {
   Ctl *c = a.ctl;
   if (!merge_enabled(c)) return;
-  const u32 nlist = ld_cg_u32(&c->n_large);
+  const u32 nlist = ld_cg_u32(&c->n_medium);
   const u64 cmask = (1ull << a.bits) - 1;
   for (u32 li = blockIdx.x; li < nlist; li += gridDim.x) {
     const Seg sg = a.seg[a.list[li]];
     const Store &st = a.st[sg.dir];
-    const RowMeta rm = st.row[sg.row];
-    const int2 *old = st.adj + rm.start;
+    const int2 *old = st.adj + sg.old_start;
     const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
     const u64 base_pref = a.item_pref[sg.first];
-    int2 *target = sg.scratch >= 0 ? a.scratch + sg.scratch : st.adj + sg.dest;
-    for (int j = threadIdx.x; j < rm.deg; j += blockDim.x) {
-      const int2 e = old[j];
-      const int p = old_entry_pos(a, sg, prefix, base_pref, j, e.x);
-      if (p >= sg.new_deg) atomicExch(&c->bad, 1);
-      else if (p >= 0) target[p] = e;
+    int2 ent[kMedPer];
+    int pos[kMedPer];
+#pragma unroll
+    for (int t = 0; t < kMedPer; ++t) {
+      const int j = threadIdx.x + kMedThreads * t;
+      pos[t] = -1;
+      if (j < sg.old_deg) {
+        ent[t] = old[j];
+        pos[t] = old_entry_pos(a, sg, prefix, base_pref, j, ent[t].x);
+      }
     }
-    for (u32 i = sg.first + threadIdx.x; i < sg.end; i += blockDim.x) {
-      if ((a.keys[i] & 1) && (a.flags[i] & 1)) {
+    int2 aent[kMedPer];
+    int apos[kMedPer];
+#pragma unroll
+    for (int t = 0; t < kMedPer; ++t) {
+      const u32 i = sg.first + threadIdx.x + kMedThreads * t;
+      apos[t] = -1;
+      if (i < sg.end && (a.keys[i] & 1) && (a.flags[i] & 1)) {
         const int col = (int)((a.keys[i] >> 1) & cmask);
-        const int p = add_entry_pos(a, sg, prefix, base_pref, old, rm.deg, i, col);
-        if (p < 0 || p >= sg.new_deg) atomicExch(&c->bad, 1);
-        else target[p] = make_int2(col, (int)a.vals[i]);
+        aent[t] = make_int2(col, (int)a.vals[i]);
+        apos[t] = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
       }
     }
     __syncthreads();
-    if (sg.scratch >= 0) {
-      int2 *dst = st.adj + sg.dest;
-      for (int j = threadIdx.x; j < sg.new_deg; j += blockDim.x) dst[j] = target[j];
+    int2 *dst = st.adj + sg.dest;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < kMedPer; ++t) {
+      if (pos[t] >= 0) {
+        if (pos[t] < sg.new_deg) dst[pos[t]] = ent[t]; else bad = true;
+      }
+      if (apos[t] >= 0) {
+        if (apos[t] < sg.new_deg) dst[apos[t]] = aent[t]; else bad = true;
+      }
     }
-    if (threadIdx.x == 0) {
-      RowMeta nm;
-      nm.start = sg.dest;
-      nm.deg = sg.new_deg;
-      nm.cap = sg.new_cap;
-      st.row[sg.row] = nm;
-    }
+    if (bad) atomicExch(&c->bad, 1);
+    if (threadIdx.x == 0) write_meta(st, sg);
     __syncthreads();
+  }
+}
+
+// Slot in a packed (count << 40 | chunks) list owning chunk `ch`.
+__device__ __forceinline__ u32 chunk_owner(const u32 *cb, u32 count, u32 ch) {
+  u32 lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const u32 mid = (lo + hi + 1) >> 1;
+    if (__ldcg(cb + mid) <= ch) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tier 2: rows too large for one block, split into chunks of 4096 elements
+// (old entries, then batch items) over all blocks.  Output goes out of place:
+// to the row's new pool segment, or to scratch and then back (k_merge_copy),
+// so no chunk reads a slot another chunk has rewritten.
+__global__ void __launch_bounds__(kThreads) k_merge_large(MergeArgs a) {
+  Ctl *c = a.ctl;
+  if (!merge_enabled(c)) return;
+  const u64 pk = ld_cg_u64(&c->large_pack);
+  const u32 nlist = (u32)(pk >> 40), nch = (u32)(pk & kMask40);
+  const u64 cmask = (1ull << a.bits) - 1;
+  for (u32 ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const u32 slot = chunk_owner(a.list_cb, nlist, ch);
+    const Seg sg = a.seg[__ldcg(a.list + slot)];
+    const Store &st = a.st[sg.dir];
+    const int2 *old = st.adj + sg.old_start;
+    const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
+    const u64 base_pref = a.item_pref[sg.first];
+    int2 *target = sg.scratch >= 0 ? a.scratch + sg.scratch : st.adj + sg.dest;
+    const long long e0 = (long long)(ch - __ldcg(a.list_cb + slot)) * kLargeChunk;
+    const long long ne = (long long)sg.old_deg + (sg.end - sg.first);
+    const long long e1 = e0 + kLargeChunk < ne ? e0 + kLargeChunk : ne;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      if (e < sg.old_deg) {
+        const int j = (int)e;
+        const int2 en = old[j];
+        const int p = old_entry_pos(a, sg, prefix, base_pref, j, en.x);
+        if (p >= sg.new_deg) atomicExch(&c->bad, 1);
+        else if (p >= 0) target[p] = en;
+      } else {
+        const u32 i = sg.first + (u32)(e - sg.old_deg);
+        if ((a.keys[i] & 1) && (a.flags[i] & 1)) {
+          const int col = (int)((a.keys[i] >> 1) & cmask);
+          const int p = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
+          if (p < 0 || p >= sg.new_deg) atomicExch(&c->bad, 1);
+          else target[p] = make_int2(col, (int)a.vals[i]);
+        }
+      }
+    }
+  }
+}
+
+// Tier 2, second pass: copy scratch back into rows merged in place, and
+// publish the new row metadata of every tier-2 row.
+__global__ void __launch_bounds__(kThreads) k_merge_copy(MergeArgs a, const u32 *large_list) {
+  Ctl *c = a.ctl;
+  if (!merge_enabled(c)) return;
+  const u64 pk = ld_cg_u64(&c->copy_pack);
+  const u32 nlist = (u32)(pk >> 40), nch = (u32)(pk & kMask40);
+  for (u32 ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const u32 slot = chunk_owner(a.list_cb, nlist, ch);
+    const Seg sg = a.seg[__ldcg(a.list + slot)];
+    const int2 *src = a.scratch + sg.scratch;
+    int2 *dst = a.st[sg.dir].adj + sg.dest;
+    const long long e0 = (long long)(ch - __ldcg(a.list_cb + slot)) * kLargeChunk;
+    const long long e1 = e0 + kLargeChunk < sg.new_deg ? e0 + kLargeChunk : sg.new_deg;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) dst[e] = __ldcg(src + e);
+  }
+  const u32 nl = (u32)(ld_cg_u64(&c->large_pack) >> 40);
+  for (u32 li = blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += gridDim.x * blockDim.x) {
+    const Seg sg = a.seg[__ldcg(large_list + li)];
+    write_meta(a.st[sg.dir], sg);
   }
 }
 
@@ -705,6 +831,21 @@ sp_status store_grow_pool(sp_graph *g, Store *st, long long min_pool_slots) {
   return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
+sp_status ensure_owner_tables(sp_graph *g) {
+  const long long slots = std::max(g->fwd.slots, g->rev.slots);
+  const long long need = slots / kChunk + 64;
+  if (need <= g->own_cap && g->qown[0]) return SP_OK;
+  const long long c = std::max(need, g->own_cap * 2);
+  g->al.put(g->qown[0], (size_t)g->own_cap * 4);
+  g->al.put(g->qown[1], (size_t)g->own_cap * 4);
+  g->al.put(g->aown, (size_t)g->own_cap * 4);
+  g->qown[0] = (u32 *)g->al.get((size_t)c * 4);
+  g->qown[1] = (u32 *)g->al.get((size_t)c * 4);
+  g->aown = (u32 *)g->al.get((size_t)c * 4);
+  g->own_cap = c;
+  return (g->qown[0] && g->qown[1] && g->aown) ? SP_OK : SP_ENOMEM;
+}
+
 void launch_ctl_reset(sp_graph *g, int full, int *launches) {
   k_ctl_reset<<<1, 1, 0, g->stream>>>(g->ctl, full);
   ++*launches;
@@ -742,8 +883,13 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.seg = b.seg;
   a.flags = b.flags;
   a.itemv = b.itemv;
+  a.item_pref = b.item_pref;
   a.small_list = b.small_list;
+  a.medium_list = b.medium_list;
   a.large_list = b.large_list;
+  a.large_cb = b.large_cb;
+  a.copy_list = b.copy_list;
+  a.copy_cb = b.copy_cb;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
@@ -751,11 +897,13 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.scratch_cap = b.scratch_cap;
   a.n_items = (u32)ni;
   a.n = g->n;
-  k_count<<<blocks_for(ni * 32, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(a);
+  const unsigned grid = blocks_for(ni, kThreads, g->num_sms * 16);
+  k_count_items<<<grid, kThreads, 0, g->stream>>>(a);
   // item prefix counts (n_items + 1 entries; itemv[ni] is 0)
   cudaMemsetAsync(b.itemv + ni, 0, sizeof(u64), g->stream);
   scan_exclusive_u64(b.itemv, b.item_pref, ni + 1, b.tmp, g->stream, launches);
-  ++*launches;
+  k_count_segs<<<grid, kThreads, 0, g->stream>>>(a);
+  *launches += 2;
 }
 
 void launch_merge(sp_graph *g, long long ni, int *launches) {
@@ -773,10 +921,18 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.scratch = b.scratch;
   a.bits = g->bits;
   a.list = b.small_list;
+  a.list_cb = nullptr;
   k_merge_small<<<blocks_for(ni * 32, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(a);
+  a.list = b.medium_list;
+  k_merge_medium<<<(unsigned)std::max(1, g->num_sms * 2), kMedThreads, 0, g->stream>>>(a);
   a.list = b.large_list;
-  k_merge_large<<<(unsigned)std::max(1, g->num_sms * 4), kThreads, 0, g->stream>>>(a);
-  *launches += 2;
+  a.list_cb = b.large_cb;
+  k_merge_large<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
+  a.list = b.copy_list;
+  a.list_cb = b.copy_cb;
+  k_merge_copy<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(
+      a, b.large_list);
+  *launches += 4;
 }
 
 void launch_finish(sp_graph *g, int *launches) {

@@ -339,3 +339,47 @@ def test_static_recompute_equals_dynamic():
             d_dyn = g.get_dist()
             g.sssp_init(W.source)
             np.testing.assert_array_equal(g.get_dist(), d_dyn)
+
+
+def test_merge_tiers_hub_rows():
+    """A 15,000-edge hub row (chunked tier, in place via scratch and then
+    relocated), a 2,000-edge row (block tier) and small rows in one batch."""
+    n = 30000
+    rng = np.random.default_rng(11)
+    edges = {}
+    for v in range(2, n, 2):
+        edges[(0, v)] = int(rng.integers(1, 100))
+    for v in rng.choice(np.arange(2, n), 2000, replace=False):
+        edges[(1, int(v))] = int(rng.integers(1, 100))
+    for _ in range(60000):
+        a, b = int(rng.integers(n)), int(rng.integers(n))
+        if a != b and a > 1:
+            edges.setdefault((a, b), int(rng.integers(1, 100)))
+    keys = sorted(edges)
+    u = np.array([k[0] for k in keys], np.int64)
+    ro = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(u, minlength=n), out=ro[1:])
+    col = np.array([k[1] for k in keys], np.int32)
+    w = np.array([edges[k] for k in keys], np.int32)
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(0)
+        check_all(g, ref, 0)
+        for k, n_ins in enumerate((800, 6000)):
+            evens = np.arange(2, n, 2)
+            dels0 = rng.choice(evens, 700, replace=False).astype(np.int32)
+            odds = np.arange(3, n, 2)
+            ins0 = rng.choice(odds, n_ins, replace=False).astype(np.int32)
+            del_s = np.concatenate([np.zeros(700, np.int32), np.ones(50, np.int32)])
+            del_d = np.concatenate([dels0, col[ro[1]:ro[1] + 50]])
+            add_s = np.concatenate([np.zeros(n_ins, np.int32), np.ones(300, np.int32)])
+            add_d = np.concatenate([ins0, rng.choice(odds, 300, replace=False).astype(np.int32)])
+            add_w = rng.integers(1, 100, add_s.size).astype(np.int32)
+            st = g.apply_batch(del_s, del_d, add_s, add_d, add_w, stats=True)
+            cnt = ref.apply_batch(del_s, del_d, add_s, add_d, add_w)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == cnt
+            check_all(g, ref, 0)
+            ro2, col2, _ = ref.csr()
+            ro, col = ro2, col2
+        assert g.info().pool_used_fwd > 0      # the hub row moved on the second batch
