@@ -190,6 +190,28 @@ sp_status sp_graph_num_edges(const sp_graph *g, int64_t *m);
 sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off,
                         int32_t *col, int32_t *w, int out_on_device);
 
+/*
+ * Allocation-free form of sp_export_csr(g, reverse, row_off, col, w, 1): the
+ * same device-side export, for callers that must not allocate device memory
+ * during the call (a serving process snapshotting a live graph into buffers
+ * it reserved up front, or code held to a fixed memory footprint, where an
+ * allocation could fail or stall).  The paper has no counterpart; it is a
+ * property of this library's API.
+ *   row_off[n+1], col[m], w[m]: device arrays of the graph's device, owned
+ *   by the caller (m from sp_graph_num_edges); row_off doubles as the degree
+ *   buffer before the in-place prefix sum, so it must not alias col or w.
+ *   The graph's device must be current (else SP_EINVAL).
+ *   Graphs with more than 2^26 vertices are rejected with SP_EINVAL: the
+ *   scan's partial sums live in a fixed 512 KiB device array that every GPU
+ *   loading the library holds until exit.
+ *   The first call on each device looks that array's address up
+ *   (cudaGetSymbolAddress); make it before any stream capture.  All calls
+ *   share the array, so calls whose work overlaps on the GPU race; nothing
+ *   in it needs to start at zero.
+ */
+sp_status sp_export_csr_noalloc(sp_graph *g, int reverse, int64_t *row_off,
+                                int32_t *col, int32_t *w);
+
 /* Fill *info. */
 sp_status sp_graph_info_get(const sp_graph *g, sp_graph_info *info);
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "sp_get_dist": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "sp_graph_num_edges": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sp_export_csr": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]),
+    "sp_export_csr_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "sp_graph_info_get": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
     "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
     "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -280,6 +281,21 @@ class Graph:
                                   w.ctypes.data_as(ctypes.c_void_p), 0)
         _check(rc, "sp_export_csr")
         return ro, col[:m], w[:m]
+
+    def export_csr_device(self, row_off, col, w, reverse: bool = False,
+                          noalloc: bool = False):
+        """Export into caller-owned CUDA tensors (int64 row_off[n+1], int32
+        col[m], int32 w[m]).  noalloc=True uses sp_export_csr_noalloc, which
+        allocates no device memory during the call."""
+        lib = load()
+        p = [ctypes.c_void_p(t.data_ptr()) for t in (row_off, col, w)]
+        if noalloc:
+            rc = lib.sp_export_csr_noalloc(self._h, int(reverse), *p)
+            _check(rc, "sp_export_csr_noalloc")
+        else:
+            rc = lib.sp_export_csr(self._h, int(reverse), *p, 1)
+            _check(rc, "sp_export_csr")
+        return row_off, col, w
 
     def info(self) -> GraphInfo:
         gi = GraphInfo()
