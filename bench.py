@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--static-reps", type=int, default=3)
+    ap.add_argument("--delta", type=int, default=None,
+                    help="near-far bucket width of the push loop (default: 0 for R-MAT/ER, "
+                         "1500 for grids)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -244,6 +247,9 @@ def run_gb300(args):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         g = sp.Graph(W.n, W.row_off, W.col, W.w, stream=stream)
+    delta = args.delta if args.delta is not None else (1500 if W.name.startswith("grid") else 0)
+    g.set_delta(delta)
+    cfg["delta"] = delta
     g.sssp_init(W.source)
 
     tree = W.tree_fraction > 0

@@ -223,6 +223,18 @@ sp_status sp_graph_info_get(const sp_graph *g, sp_graph_info *info);
  */
 sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns);
 
+/*
+ * Near-far ordering of the push fixedPoint: with delta > 0 a round relaxes
+ * only vertices whose distance is below a threshold; improved vertices at or
+ * above it wait in a far pile, and the threshold rises by delta (from the
+ * pile's smallest distance) whenever the near frontier runs dry.  Distances
+ * are the same for every delta; delta trades rounds for redundant
+ * relaxations (large delta suits low-diameter graphs, a delta near a few
+ * edge weights suits high-diameter ones).  0 (the default) turns it off:
+ * plain frontier rounds, as in the paper's Incremental fixedPoint.
+ */
+sp_status sp_set_push_delta(sp_graph *g, int32_t delta);
+
 /* Static name of a status code. */
 const char *sp_status_str(sp_status s);
 

@@ -61,9 +61,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     al.put(b.flags, old); al.put(b.itemv, old * 8); al.put(b.item_pref, old * 8);
     al.put(b.head, old * 4); al.put(b.head_scan, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
-    al.put(b.small_list, old * 4); al.put(b.medium_list, old * 4);
-    al.put(b.large_list, old * 4); al.put(b.large_cb, old * 4);
-    al.put(b.copy_list, old * 4); al.put(b.copy_cb, old * 4);
+    al.put(b.ment, old * 8);
     al.put(b.tmp, b.tmp_bytes);
     b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
     b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
@@ -71,16 +69,12 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
     b.head = (u32 *)al.get(c * 4); b.head_scan = (u32 *)al.get(c * 4);
     b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
-    b.small_list = (u32 *)al.get(c * 4); b.medium_list = (u32 *)al.get(c * 4);
-    b.large_list = (u32 *)al.get(c * 4); b.large_cb = (u32 *)al.get(c * 4);
-    b.copy_list = (u32 *)al.get(c * 4); b.copy_cb = (u32 *)al.get(c * 4);
+    b.ment = (int2 *)al.get(c * 8);
     b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
     if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
-        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.small_list ||
-        !b.medium_list || !b.large_list || !b.large_cb || !b.copy_list || !b.copy_cb ||
-        !b.tmp) {
+        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.ment || !b.tmp) {
       return SP_ENOMEM;
     }
   }
@@ -97,11 +91,15 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
       return SP_ENOMEM;
   }
-  if (!b.scratch) {
-    long long c = std::max<long long>(1 << 20, g->m / 8);
-    b.scratch = (int2 *)g->al.get((size_t)c * sizeof(int2));
-    if (!b.scratch) return SP_ENOMEM;
-    b.scratch_cap = c;
+  // merge chunk-owner table: elements = old entries of touched rows (<= 2m)
+  // plus batch items
+  const long long mneed = (2 * g->m + ni) / sp::kChunk + 64;
+  if (mneed > b.mown_cap) {
+    const long long c = std::max(mneed, 2 * b.mown_cap);
+    g->al.put(b.mown, (size_t)b.mown_cap * 4);
+    b.mown = (u32 *)g->al.get((size_t)c * 4);
+    b.mown_cap = b.mown ? c : 0;
+    if (!b.mown) return SP_ENOMEM;
   }
   return SP_OK;
 }
@@ -160,9 +158,14 @@ sp_status read_ctl(sp_graph *g) {
 }
 
 void set_limits(sp_graph *g) {
+  // Bellman-Ford bound n + 1; near-far ordering adds split rounds, so the
+  // default cap is then 4 (n + 1)
+  const long long bf = (long long)g->n + 1;
+  const long long cap = g->delta_user > 0 ? 4 * bf : bf;
   g->lim.max_rounds = g->max_rounds_user > 0 ? (u32)g->max_rounds_user
-                                             : (u32)std::min<long long>((long long)g->n + 1, 0x7fffffffLL);
+                                             : (u32)std::min<long long>(cap, 0x7fffffffLL);
   g->lim.wait_ns = g->wait_ns_user > 0 ? (u64)g->wait_ns_user : 2000000000ull;
+  g->lim.delta = (u32)std::max(0, g->delta_user);
 }
 
 sp_status status_of_repair(sp_graph *g, const Ctl &c) {
@@ -213,23 +216,30 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(b.flags, c); al.put(b.itemv, c * 8); al.put(b.item_pref, c * 8);
   al.put(b.head, c * 4); al.put(b.head_scan, c * 4);
   al.put(b.seg, c * sizeof(sp::Seg));
-  al.put(b.small_list, c * 4); al.put(b.medium_list, c * 4);
-  al.put(b.large_list, c * 4); al.put(b.large_cb, c * 4);
-  al.put(b.copy_list, c * 4); al.put(b.copy_cb, c * 4);
+  al.put(b.ment, c * 8);
+  al.put(b.mown, (size_t)b.mown_cap * 4);
   al.put(b.tmp, b.tmp_bytes);
   c = b.cap_in;
   al.put(b.in_del_src, c * 4); al.put(b.in_del_dst, c * 4);
   al.put(b.in_add_src, c * 4); al.put(b.in_add_dst, c * 4); al.put(b.in_add_w, c * 4);
-  al.put(b.scratch, (size_t)b.scratch_cap * sizeof(int2));
   al.put(g->fwd.row, n * sizeof(sp::RowMeta));
+  al.put(g->fwd.alt, n * sizeof(long long));
+  al.put(g->rev.alt, n * sizeof(long long));
   al.put(g->fwd.adj, (size_t)g->fwd.slots * sizeof(int2));
   al.put(g->rev.row, n * sizeof(sp::RowMeta));
   al.put(g->rev.adj, (size_t)g->rev.slots * sizeof(int2));
   al.put(g->s, n * 8);
   al.put(g->qflag, n * 4);
-  al.put(g->qent[0], n * 8); al.put(g->qent[1], n * 8);
+  al.put(g->asv, n * 4);
+  for (int b = 0; b < 3; ++b) {
+    al.put(g->qent[b], n * 8);
+    al.put(g->qsv[b], n * 4);
+    al.put(g->fq[b], n * 4);
+    al.put(g->qown[b], (size_t)g->own_cap * 4);
+  }
   al.put(g->aent, n * 8);
-  al.put(g->qown[0], (size_t)g->own_cap * 4); al.put(g->qown[1], (size_t)g->own_cap * 4);
+  al.put(g->ftag, n * 4);
+  al.put(g->xdone, n * 8);
   al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
   al.put(g->ctl, sizeof(Ctl));
@@ -291,18 +301,29 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   const size_t nn = (size_t)n;
   g->s = (u64 *)g->al.get(nn * 8);
   g->qflag = (u32 *)g->al.get(nn * 4);
-  g->qent[0] = (int2 *)g->al.get(nn * 8);
-  g->qent[1] = (int2 *)g->al.get(nn * 8);
+  bool bufs_ok = true;
+  for (int b = 0; b < 3; ++b) {
+    g->qent[b] = (int2 *)g->al.get(nn * 8);
+    g->qsv[b] = (u32 *)g->al.get(nn * 4);
+    g->fq[b] = (u32 *)g->al.get(nn * 4);
+    bufs_ok = bufs_ok && g->qent[b] && g->qsv[b] && g->fq[b];
+  }
+  g->asv = (u32 *)g->al.get(nn * 4);
+  bufs_ok = bufs_ok && g->asv;
   g->aent = (int2 *)g->al.get(nn * 8);
+  g->ftag = (u32 *)g->al.get(nn * 4);
+  g->xdone = (u64 *)g->al.get(nn * 8);
   g->out_dist = (int *)g->al.get(nn * 4);
   g->out_parent = (int *)g->al.get(nn * 4);
-  if (!g->ctl || !g->s || !g->qflag || !g->qent[0] || !g->qent[1] || !g->aent ||
+  if (!g->ctl || !g->s || !g->qflag || !bufs_ok || !g->aent || !g->ftag || !g->xdone ||
       !g->out_dist || !g->out_parent) {
     sp_graph_destroy(g);
     return SP_ENOMEM;
   }
   cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream);
   cudaMemsetAsync(g->qflag, 0, nn * 4, g->stream);
+  cudaMemsetAsync(g->ftag, 0, nn * 4, g->stream);
+  cudaMemsetAsync(g->xdone, 0, nn * 8, g->stream);
   int launches = 0;
   sp::launch_ctl_reset(g, 1, &launches);
 
@@ -351,6 +372,13 @@ sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns) {
   if (!g || max_rounds < 0 || wait_ns < 0) return SP_EINVAL;
   g->max_rounds_user = max_rounds;
   g->wait_ns_user = wait_ns;
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
+  if (!g || delta < 0) return SP_EINVAL;
+  g->delta_user = delta;
   set_limits(g);
   return SP_OK;
 }
@@ -481,13 +509,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
       rc = sp::ensure_owner_tables(g);
       if (rc != SP_OK) return rc;
     }
-    if (c.need_grow & sp::kGrowScratch) {
-      long long want = std::max<long long>((long long)c.scratch_used + 1024, 2 * b.scratch_cap);
-      g->al.put(b.scratch, (size_t)b.scratch_cap * sizeof(int2));
-      b.scratch = (int2 *)g->al.get((size_t)want * sizeof(int2));
-      b.scratch_cap = b.scratch ? want : 0;
-      if (!b.scratch) return SP_ENOMEM;
-    }
+
   }
   const Ctl &c = *g->ctl_host;
   g->m += (long long)c.add_applied - (long long)c.del_applied;

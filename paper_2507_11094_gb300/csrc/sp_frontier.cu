@@ -33,6 +33,11 @@ namespace {
 
 constexpr int kOpPush = 0, kOpInval = 1;
 constexpr int K = kEdgesPerLane;
+// block stages of the persistent loops (dynamic shared memory)
+constexpr u32 kStageQ = 4096, kStageQS = 8192, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
+constexpr size_t kLoopSmem =
+    (2 * kStageQ + kStageQS + 2 * kStageA + kStageAS + kStageF) * sizeof(u32);
+constexpr u32 kStageK = 1024;    // stages of the one-pass kernels (static)
 constexpr u32 kNoEdge = 0xFFFFFFFFu;
 constexpr u32 kFull = 0xffffffffu;
 
@@ -62,101 +67,129 @@ __device__ __forceinline__ u64 shfl64_down(u64 x, int d) {
   return ((u64)hi << 32) | lo;
 }
 
-// Grid barrier: the last block to arrive runs `hook` (thread 0 only), then
-// releases the others.  Every wait is bounded by lim.wait_ns; a wait that runs
-// out sets ctl->timeout = 2 and returns, and every later wait returns at once.
-template <class Hook>
-__device__ __forceinline__ void grid_barrier(Ctl *c, const Limits &lim, Hook hook) {
+// Grid barrier over a monotone arrival count: barrier k of a launch waits
+// for k * gridDim.x arrivals (the count is zeroed at the start of every
+// call).  Every wait is bounded by lim.wait_ns; a wait that runs out sets
+// ctl->timeout = 2 and returns, and every later wait returns at once.
+__device__ __forceinline__ u64 ld_acquire_u64(const u64 *p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_sync(u64 *bar, u64 target, Ctl *c, const Limits &lim) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const u32 gen = ld_acquire_u32(&c->bar_gen);
     __threadfence();
-    const u32 arrived = atomicAdd(&c->bar_arrive, 1u);
-    if (arrived == gridDim.x - 1) {
-      __threadfence();
-      atomicExch(&c->bar_arrive, 0u);
-      hook();
-      __threadfence();
-      st_release_u32(&c->bar_gen, gen + 1);
-    } else {
+    atomicAdd((unsigned long long *)bar, 1ull);
+    if (ld_acquire_u64(bar) < target) {
       const u64 t0 = globaltimer_ns();
       u32 nap = 20;
-      while (ld_acquire_u32(&c->bar_gen) == gen) {
+      while (ld_acquire_u64(bar) < target) {
         if (ld_cg_i32(&c->timeout) != 0) break;
         if (globaltimer_ns() - t0 > lim.wait_ns) {
           atomicCAS(&c->timeout, 0, 2);
           break;
         }
         __nanosleep(nap);
-        if (nap < 320) nap += nap >> 1;
+        if (nap < 256) nap += nap >> 1;
       }
     }
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ volatile u64 *qcnt_of(volatile Ctl *c, u32 b) {
-  return b ? &c->qcnt1 : &c->qcnt0;
+__device__ __forceinline__ u64 *qcnt_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->qcnt0 : (b == 1 ? &c->qcnt1 : &c->qcnt2);
+}
+__device__ __forceinline__ u32 *fcnt_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->fcnt0 : (b == 1 ? &c->fcnt1 : &c->fcnt2);
+}
+__device__ __forceinline__ u32 *fmin_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->fmin0 : (b == 1 ? &c->fmin1 : &c->fmin2);
+}
+__device__ __forceinline__ u32 next3(u32 b) { return b == 2 ? 0u : b + 1u; }
+
+__device__ __forceinline__ u32 sat_add(u32 a, u32 b) {
+  const u64 x = (u64)a + b;
+  return x > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)x;
 }
 
-// Serial step between rounds (runs in one thread).  `first` is the step
-// before round 0, when the producers have filled frontier buffer `cur`.
-__device__ void serial_advance(Ctl *cc, const Limits &lim, bool first, int op) {
-  volatile Ctl *c = cc;
-  u32 cur = c->cur;
-  if (first) {
-    c->round = 0;
-    c->done = 0;
-  } else {
-    cur ^= 1u;
-    c->cur = cur;
-    c->round = c->round + 1;
+// Reserve `cnt` slots of a block stage (lane 0 only); false if it is full.
+__device__ __forceinline__ bool stage_reserve(Stage *st, u32 cnt, u32 &pos) {
+  u32 old = *(volatile u32 *)&st->n;
+  while (old + cnt <= st->cap) {
+    const u32 prev = atomicCAS(&st->n, old, old + cnt);
+    if (prev == old) {
+      pos = old;
+      return true;
+    }
+    old = prev;
   }
-  *qcnt_of(c, cur ^ 1u) = 0ull;          // the buffer this round fills
-  const u64 q = *qcnt_of(c, cur);
-  const u32 ne = (u32)(q >> 32), edges = (u32)q;
-  c->n_ent = ne;
-  c->n_edges = edges;
-  c->n_chunks = (edges + kChunk - 1) / kChunk;
-  c->epoch = c->epoch + 1;
-  bool done = false;
-  if (edges == 0) {
-    done = true;
-  } else if (c->round >= lim.max_rounds) {
-    c->timeout = 1;
-    done = true;
-  }
-  if (done) {
-    c->done = 1;
-    if (op == kOpPush) c->rounds_push = c->round;
-    else c->rounds_inval = c->round;
-    c->cur = 0;                          // leave the frontier empty
-    c->qcnt0 = 0ull;
-    c->qcnt1 = 0ull;
-    c->epoch = c->epoch + 1;
-  }
+  return false;
 }
 
-// Append up to K vertices per lane to queue q (warp-collective).  Each kept
-// vertex (want and degree > 0 in `row`) reserves deg slots of the queue's
-// edge space; the chunk-owner table gets its slot for every chunk whose first
-// edge falls in that range.
+// Append up to K vertices per lane to queue q (warp-collective).  A vertex
+// with 1..kSmallDeg edges goes to the small list; a larger one reserves deg
+// slots of the queue's edge space, and the chunk-owner table gets its slot
+// for every chunk whose first edge falls in that range.  With block stages
+// the vertices wait there and are published when the block flushes.
 __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, const u32 *x,
                                         const bool *want, int kk, u64 &n_enq) {
   const int lane = threadIdx.x & 31;
   int d[K];
-  u32 cnt = 0, sum = 0;
+  u32 cnt = 0, sum = 0, scount = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     d[k] = (k < kk && want[k]) ? __ldg(&row[x[k]].deg) : 0;
-    if (d[k] > 0) {
+    if (d[k] > kSmallDeg) {
       ++cnt;
       sum += (u32)d[k];
+    } else if (d[k] > 0) {
+      ++scount;
     }
   }
-  if (!__ballot_sync(kFull, cnt > 0)) return;
+  const u32 any = __ballot_sync(kFull, cnt > 0), sany = __ballot_sync(kFull, scount > 0);
+  if (!any && !sany) return;
+  n_enq += cnt + scount;
+  if (sany) {   // small list
+    const u32 si = warp_incl_scan(scount), stot = __shfl_sync(kFull, si, 31);
+    u32 pos = 0;
+    bool ok = false;
+    if (lane == 0) ok = q.sst && stage_reserve(q.sst, stot, pos);
+    ok = __shfl_sync(kFull, ok, 0);
+    u32 *dst;
+    if (ok) {
+      dst = q.sst->v;
+    } else {
+      if (lane == 0) pos = atomicAdd(q.scnt, stot);
+      dst = q.sv;
+    }
+    u32 p = __shfl_sync(kFull, pos, 0) + si - scount;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (d[k] > 0 && d[k] <= kSmallDeg) dst[p++] = x[k];
+  }
+  if (!any) return;
   const u32 ci = warp_incl_scan(cnt), si = warp_incl_scan(sum);
   const u32 ctot = __shfl_sync(kFull, ci, 31), stot = __shfl_sync(kFull, si, 31);
+  if (q.st) {
+    u32 pos = 0;
+    bool ok = false;
+    if (lane == 0) ok = stage_reserve(q.st, ctot, pos);
+    if (__shfl_sync(kFull, ok, 0)) {
+      u32 p = __shfl_sync(kFull, pos, 0) + ci - cnt;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (d[k] > kSmallDeg) {
+          q.st->v[p] = x[k];
+          q.st->d[p] = (u32)d[k];
+          ++p;
+        }
+      }
+      return;
+    }
+  }
   u64 base = 0;
   if (lane == 0) base = atomicAdd(q.cnt, ((u64)ctot << 32) | (u64)stot);
   base = shfl64(base, 0);
@@ -164,7 +197,7 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
   u32 eb = (u32)base + si - sum;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (d[k] > 0) {
+    if (d[k] > kSmallDeg) {
       q.ent[slot] = make_int2((int)x[k], (int)eb);
       const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + (u32)d[k] - 1) / kChunk;
       for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
@@ -172,7 +205,139 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
       eb += (u32)d[k];
     }
   }
-  n_enq += cnt;
+}
+
+// Block scan helper: exclusive prefix of one value per thread; the block
+// total goes to *total (smem scratch of 33 words).
+__device__ __forceinline__ u32 block_excl_scan(u32 x, u32 *scratch, u32 *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const u32 incl = warp_incl_scan(x);
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    u32 v = lane < nwarps ? scratch[lane] : 0u;
+    v = warp_incl_scan(v);
+    if (lane < nwarps) scratch[lane] = v;
+  }
+  __syncthreads();
+  const u32 r = (warp ? scratch[warp - 1] : 0u) + incl - x;
+  *total = scratch[nwarps - 1];
+  __syncthreads();
+  return r;
+}
+
+// Publish a block's staged queue entries (block-collective): one global
+// atomic for the whole block, then entries and chunk owners are written.
+__device__ __noinline__ void flush_queue(const Queue &q, u32 *scratch) {
+  Stage *st = q.st;
+  __syncthreads();
+  const u32 n = *(volatile u32 *)&st->n;
+  if (n) {
+    const u32 per = (n + blockDim.x - 1) / blockDim.x;
+    const u32 b = min(threadIdx.x * per, n), e = min(b + per, n);
+    u32 sum = 0;
+    for (u32 i = b; i < e; ++i) sum += st->d[i];
+    u32 total;
+    u32 run = block_excl_scan(sum, scratch, &total);
+    if (threadIdx.x == 0) {
+      const u64 base = atomicAdd(q.cnt, ((u64)n << 32) | (u64)total);
+      scratch[32] = (u32)(base >> 32);
+      scratch[33] = (u32)base;
+    }
+    __syncthreads();
+    u32 slot = scratch[32] + b;
+    u32 eb = scratch[33] + run;
+    for (u32 i = b; i < e; ++i) {
+      const u32 d = st->d[i];
+      q.ent[slot] = make_int2((int)st->v[i], (int)eb);
+      const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + d - 1) / kChunk;
+      for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
+      ++slot;
+      eb += d;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st->n = 0;
+  Stage *ss = q.sst;
+  if (ss) {   // small list: one atomic, then a coalesced copy
+    const u32 ns = *(volatile u32 *)&ss->n;
+    if (ns) {
+      if (threadIdx.x == 0) scratch[34] = atomicAdd(q.scnt, ns);
+      __syncthreads();
+      const u32 base = scratch[34];
+      for (u32 i = threadIdx.x; i < ns; i += blockDim.x) q.sv[base + i] = ss->v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ss->n = 0;
+  }
+  __syncthreads();
+}
+
+// Append each lane's wanted vertices to a far pile (warp-collective) and
+// lower far_min to the smallest distance appended (through the block stage
+// when there is one).
+__device__ __forceinline__ void far_append(u32 *pile, u32 *cnt, u32 *far_min, Stage *st,
+                                           const u32 *x, const bool *want, int kk,
+                                           u32 lane_min) {
+  const int lane = threadIdx.x & 31;
+  u32 n = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) n += (k < kk && want[k]) ? 1u : 0u;
+  if (!__ballot_sync(kFull, n > 0)) return;
+  const u32 ni = warp_incl_scan(n), tot = __shfl_sync(kFull, ni, 31);
+  u32 mn = lane_min;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u32 y = __shfl_xor_sync(kFull, mn, o);
+    mn = y < mn ? y : mn;
+  }
+  if (st) {
+    u32 pos = 0;
+    bool ok = false;
+    if (lane == 0) {
+      ok = stage_reserve(st, tot, pos);
+      if (ok) atomicMin(&st->vmin, mn);
+    }
+    if (__shfl_sync(kFull, ok, 0)) {
+      u32 p = __shfl_sync(kFull, pos, 0) + ni - n;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (k < kk && want[k]) st->v[p++] = x[k];
+      return;
+    }
+  }
+  u32 base = 0;
+  if (lane == 0) {
+    base = atomicAdd(cnt, tot);
+    atomicMin(far_min, mn);
+  }
+  base = __shfl_sync(kFull, base, 0);
+  u32 slot = base + ni - n;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (k < kk && want[k]) pile[slot++] = x[k];
+}
+
+// Publish a block's staged far-pile entries (block-collective).
+__device__ __noinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *far_min,
+                                       u32 *scratch) {
+  __syncthreads();
+  const u32 n = *(volatile u32 *)&st->n;
+  if (n) {
+    if (threadIdx.x == 0) {
+      scratch[32] = atomicAdd(cnt, n);
+      atomicMin(far_min, *(volatile u32 *)&st->vmin);
+    }
+    __syncthreads();
+    const u32 base = scratch[32];
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) pile[base + i] = st->v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->n = 0;
+    st->vmin = 0xFFFFFFFFu;
+  }
+  __syncthreads();
 }
 
 // --- edge operations ------------------------------------------------------
@@ -182,13 +347,19 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
 // lane's edges followed by the warp-collective enqueue of what they queue).
 
 // Incremental fixedPoint body: <dist, parent>[x] = <Min(dist[x], dist[v] + w), v>
-// as one packed atomicMin; an improved x joins the next frontier once.
+// as one packed atomicMin; an improved x joins the next frontier once, or,
+// under near-far ordering with a distance >= thresh, the far pile once per
+// phase.
 struct PushOp {
   u64 *s;
   u32 *qflag;
   u32 tag;
   Queue next;
   const RowMeta *row;
+  u32 thresh;
+  u32 *pile, *pcnt, *far_min, *ftag;
+  u32 phase;
+  Stage *fst;
   u64 n_edges = 0, n_imp = 0, n_enq = 0;
   int range_err = 0;
 
@@ -197,10 +368,12 @@ struct PushOp {
   __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *od,
                                       const int2 *ed, const u64 *sx) {
     u32 tx[K];
-    bool want[K];
+    bool want[K], far[K];
+    u32 fmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       want[k] = false;
+      far[k] = false;
       tx[k] = (u32)ed[k].x;
       if (act[k]) {
         ++n_edges;
@@ -214,7 +387,12 @@ struct PushOp {
               const u64 old = atomicMin((unsigned long long *)(s + ed[k].x), cand);
               if (cand < old) {
                 ++n_imp;
-                want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
+                if (nd < thresh) {
+                  want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
+                } else {
+                  far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
+                  if (far[k] && nd < fmin) fmin = nd;
+                }
               }
             }
           }
@@ -222,6 +400,7 @@ struct PushOp {
       }
     }
     enqueue(next, row, tx, want, K, n_enq);
+    if (pile) far_append(pile, pcnt, far_min, fst, tx, far, K, fmin);
   }
 };
 
@@ -267,6 +446,7 @@ struct PullOp {
   u32 tag;
   Queue next;
   const RowMeta *row;
+  u32 *seed_min;
   u64 n_edges = 0, n_enq = 0;
   int range_err = 0;
 
@@ -275,7 +455,9 @@ struct PullOp {
   __device__ __forceinline__ bool offer(u32 v, u64 best) {
     if (best == ~0ull || best >= ld_cg_u64(s + v)) return false;
     const u64 old = atomicMin((unsigned long long *)(s + v), best);
-    return best < old && atomicExch(qflag + v, tag) != tag;
+    if (!(best < old)) return false;
+    atomicMin(seed_min, dist_of(best));
+    return atomicExch(qflag + v, tag) != tag;
   }
   __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
                                       const int2 *ed, const u64 *sx) {
@@ -435,30 +617,110 @@ __device__ __forceinline__ bool repair_enabled(Ctl *c) {
          ld_cg_i32(&c->timeout) == 0 && ld_cg_i32(&c->bad) == 0;
 }
 
-__device__ __forceinline__ Queue make_queue(int2 *ent, u32 *own, u64 *cnt) {
+__device__ __forceinline__ Queue make_queue(int2 *ent, u32 *own, u64 *cnt, u32 *sv, u32 *scnt,
+                                            Stage *st = nullptr, Stage *sst = nullptr) {
   Queue q;
   q.ent = ent;
   q.owner = own;
   q.cnt = (unsigned long long *)cnt;
+  q.sv = sv;
+  q.scnt = scnt;
+  q.st = st;
+  q.sst = sst;
   return q;
 }
 
+__device__ __forceinline__ u32 *scnt_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->scnt0 : (b == 1 ? &c->scnt1 : &c->scnt2);
+}
+
+// Expand up to 32 small-list vertices, one lane each, K edges per step (the
+// warp takes as many steps as its largest vertex needs).
+template <class Op>
+__device__ __forceinline__ void process_small(Op &op, const u32 *sv, u32 n_small, u32 group,
+                                              const Store &st, int n, Ctl *c) {
+  const int lane = threadIdx.x & 31;
+  const u32 idx = group * 32 + lane;
+  u32 v = 0, dv = 0;
+  int deg = 0;
+  long long start = 0;
+  if (idx < n_small) {
+    v = __ldcg(sv + idx);
+    if (v < (u32)n) {
+      const RowMeta rm = st.row[v];
+      deg = rm.deg;
+      start = rm.start;
+      dv = op.vdata(v);
+    } else {                             // never expected: record and skip
+      atomicExch(&c->bad, 1);
+      v = 0;
+    }
+  }
+  int steps = (deg + K - 1) / K;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int y = __shfl_xor_sync(kFull, steps, o);
+    steps = y > steps ? y : steps;
+  }
+  for (int t = 0; t < steps; ++t) {
+    bool act[K];
+    u32 ov[K], od[K];
+    int2 ed[K];
+    u64 sx[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = t * K + k;
+      act[k] = e < deg;
+      ov[k] = v;
+      od[k] = dv;
+      ed[k] = act[k] ? __ldg(st.adj + start + e) : make_int2(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) sx[k] = act[k] ? op.load(ed[k]) : 0ull;
+    op.run(act, ov, od, ed, sx);
+  }
+}
+
 // --- persistent loop ------------------------------------------------------
+//
+// Every block keeps the loop state (current buffer, round, threshold, far
+// pile, phase) in registers and derives it from the same counters after each
+// barrier, so a round costs one barrier and no serial step.  Buffers rotate
+// over three slots: round r reads frontier slot r%3, appends to (r+1)%3, and
+// block 0 zeroes (r+2)%3, which nobody touches until round r+1.  Far piles
+// rotate the same way: a split round reads pile f, keeps entries in f+1 and
+// zeroes f+2.
 
 template <int OP>
-__global__ void __launch_bounds__(kLoopThreads, 2) k_loop(LoopArgs a) {
+__global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
+  extern __shared__ u32 dsm[];
+  __shared__ Stage sq, sqs, sa, sas, sf;
+  __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
   if (!repair_enabled(c)) return;
+  if (threadIdx.x == 0) {
+    u32 *p = dsm;
+    sq.n = 0; sq.cap = kStageQ; sq.vmin = kInf; sq.v = p; sq.d = p + kStageQ; p += 2 * kStageQ;
+    sqs.n = 0; sqs.cap = kStageQS; sqs.vmin = kInf; sqs.v = p; sqs.d = nullptr; p += kStageQS;
+    sa.n = 0; sa.cap = kStageA; sa.vmin = kInf; sa.v = p; sa.d = p + kStageA; p += 2 * kStageA;
+    sas.n = 0; sas.cap = kStageAS; sas.vmin = kInf; sas.v = p; sas.d = nullptr; p += kStageAS;
+    sf.n = 0; sf.cap = kStageF; sf.vmin = 0xFFFFFFFFu; sf.v = p; sf.d = nullptr;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // warp ids interleaved across blocks, so that a round with few chunks
+  // still spreads over every SM
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  u64 n_edges = 0, n_imp = 0, n_enq = 0, n_aff = 0;
+  u64 n_edges = 0, n_imp = 0, n_enq = 0, n_aff = 0, moved = 0;
   int range_err = 0;
+  u64 *bar = OP == kOpPush ? &c->bar_push : &c->bar_inval;
+  u64 target = 0;
 
   if (OP == kOpInval && a.n_del > 0) {
     // OnDelete: a deleted edge u -> v that is v's parent edge invalidates v.
-    const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0);
-    const Queue qa = make_queue(a.aent, a.aown, &c->acnt);
+    const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &sq, &sqs);
+    const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
     for (long long base = (long long)gw * 32; base < a.n_del; base += (long long)nw * 32) {
       const long long i = base + lane;
       bool hit[K] = {};
@@ -475,67 +737,199 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_loop(LoopArgs a) {
       u64 dummy = 0;
       enqueue(qa, a.rev.row, v, hit, 1, dummy);
     }
+    flush_queue(q0, scratch);
+    flush_queue(qa, scratch);
   }
 
-  grid_barrier(c, a.lim, [&] { serial_advance(c, a.lim, true, OP); });
+  // state shared by all blocks (read before the first barrier; only block 0
+  // writes it back, after the last barrier)
+  const u32 tag0 = ld_cg_u32(&c->epoch);
+  const u32 phase0 = ld_cg_u32(&c->phase);
+  target += gridDim.x;
+  grid_sync(bar, target, c, a.lim);
+
+  const bool nf = OP == kOpPush && a.lim.delta > 0;
+  u32 thresh = 0xFFFFFFFFu;
+  if (nf) {
+    const u32 sm = ld_cg_u32(&c->seed_min);
+    thresh = sat_add(sm < kInf ? sm : 0u, a.lim.delta);
+  }
+  u32 cur = 0, f = 0, round = 0, splits = 0;
+  bool capped = false;
   for (;;) {
-    if (ld_cg_u32(&c->done) || ld_cg_i32(&c->timeout)) break;
-    const u32 cur = ld_cg_u32(&c->cur), nxt = cur ^ 1u;
-    const u32 ne = ld_cg_u32(&c->n_ent), nedge = ld_cg_u32(&c->n_edges);
-    const u32 nch = ld_cg_u32(&c->n_chunks);
-    const u32 tag = ld_cg_u32(&c->epoch);
-    const Queue qn = make_queue(a.qent[nxt], a.qown[nxt], nxt ? &c->qcnt1 : &c->qcnt0);
+    if (ld_cg_i32(&c->timeout)) break;
+    if (round >= a.lim.max_rounds) {
+      capped = true;
+      break;
+    }
+    const u64 q = ld_cg_u64(qcnt_ptr(c, cur));
+    const u32 ne = (u32)(q >> 32), nedge = (u32)q;
+    const u32 nsmall = ld_cg_u32(scnt_ptr(c, cur));
+    const u32 sgroups = (nsmall + 31) / 32;
+    const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
+    bool split = false;
+    u32 n_far = 0;
+    if (items == 0) {
+      if (nf) n_far = ld_cg_u32(fcnt_ptr(c, f));
+      if (n_far == 0) break;                       // fixed point reached
+      split = true;
+      const u32 fm = ld_cg_u32(fmin_ptr(c, f));
+      thresh = sat_add(thresh > fm ? thresh : fm, a.lim.delta);
+    }
+    const u32 nxt = next3(cur);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      *(volatile u64 *)qcnt_ptr(c, next3(nxt)) = 0ull;
+      *(volatile u32 *)scnt_ptr(c, next3(nxt)) = 0u;
+      if (split) {
+        const u32 fz = next3(next3(f));
+        *(volatile u32 *)fcnt_ptr(c, fz) = 0u;
+        *(volatile u32 *)fmin_ptr(c, fz) = kInf;
+      }
+    }
+    const u32 tag = tag0 + 1u + round;
+    const u32 phase = phase0 + 1u + splits;
+    const Queue qn =
+        make_queue(a.qent[nxt], a.qown[nxt], qcnt_ptr(c, nxt), a.qsv[nxt], scnt_ptr(c, nxt), &sq, &sqs);
+    const u32 fk = next3(f);
     if (OP == kOpPush) {
-      PushOp op{a.s, a.qflag, tag, qn, a.fwd.row};
-      for (u32 ch = gw; ch < nch; ch += nw)
-        process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, ch, a.fwd, a.n, c);
-      n_edges += op.n_edges;
-      n_imp += op.n_imp;
-      n_enq += op.n_enq;
-      range_err |= op.range_err;
+      if (split) {
+        // far entries below thresh go back to the near frontier, the rest
+        // move to the next pile.  An entry whose vertex was expanded since it
+        // was piled is expanded again: skipping it would need the distance
+        // every chunk of that expansion used, and chunks of one vertex can
+        // read different distances within a round.
+        const u32 *pin = a.fq[f];
+        for (u32 base = gw * 32; base < n_far; base += nw * 32) {
+          const u32 i = base + lane;
+          bool near[K] = {}, keep[K] = {};
+          u32 x[K] = {};
+          u32 kmin = 0xFFFFFFFFu;
+          if (i < n_far) {
+            x[0] = __ldcg(pin + i);
+            const u32 d = dist_of(ld_cg_u64(a.s + x[0]));
+            if (d < kInf) {
+              if (d < thresh) {
+                near[0] = atomicExch(a.qflag + x[0], tag) != tag;
+              } else {
+                keep[0] = true;
+                a.ftag[x[0]] = phase + 1u;
+                kmin = d;
+              }
+            }
+          }
+          moved += near[0];
+          enqueue(qn, a.fwd.row, x, near, 1, n_enq);
+          far_append(a.fq[fk], fcnt_ptr(c, fk), fmin_ptr(c, fk), &sf, x, keep, 1, kmin);
+        }
+      } else {
+        PushOp op{a.s, a.qflag, tag, qn, a.fwd.row, thresh,
+                  nf ? a.fq[f] : nullptr, fcnt_ptr(c, f), fmin_ptr(c, f), a.ftag,
+                  phase, &sf};
+        for (u32 it = gw; it < items; it += nw) {
+          if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
+          else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
+        }
+        n_edges += op.n_edges;
+        n_imp += op.n_imp;
+        n_enq += op.n_enq;
+        range_err |= op.range_err;
+      }
     } else {
-      InvalOp op{a.s, qn, make_queue(a.aent, a.aown, &c->acnt), a.fwd.row, a.rev.row};
-      for (u32 ch = gw; ch < nch; ch += nw)
-        process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, ch, a.fwd, a.n, c);
+      const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
+      InvalOp op{a.s, qn, qa, a.fwd.row, a.rev.row};
+      for (u32 it = gw; it < items; it += nw) {
+        if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
+        else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
+      }
       n_edges += op.n_edges;
       n_enq += op.n_enq;
       n_aff += op.n_aff;
+      flush_queue(qa, scratch);
     }
-    grid_barrier(c, a.lim, [&] { serial_advance(c, a.lim, false, OP); });
+    // publish this block's staged appends before the barrier
+    flush_queue(qn, scratch);
+    if (nf) {
+      const u32 fp = split ? fk : f;
+      flush_far(&sf, a.fq[fp], fcnt_ptr(c, fp), fmin_ptr(c, fp), scratch);
+    }
+    if (split) {
+      f = next3(f);
+      ++splits;
+    }
+    cur = nxt;
+    ++round;
+    target += gridDim.x;
+    grid_sync(bar, target, c, a.lim);
   }
   n_edges = warp_sum(n_edges);
   n_imp = warp_sum(n_imp);
   n_enq = warp_sum(n_enq);
   n_aff = warp_sum(n_aff);
+  moved = warp_sum(moved);
   range_err = __any_sync(kFull, range_err);
   if (lane == 0) {
     if (OP == kOpPush) {
       if (n_edges) atomicAdd(&c->relaxed, n_edges);
       if (n_imp) atomicAdd(&c->improved, n_imp);
       if (n_enq) atomicAdd(&c->enqueued, n_enq);
+      if (moved) atomicAdd(&c->far_moves, moved);
     } else {
       if (n_edges) atomicAdd(&c->inval_edges, n_edges);
       if (n_aff) atomicAdd(&c->affected, n_aff);
     }
     if (range_err) atomicExch(&c->range_err, 1);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // every block has read the counters of the final round: leave the
+    // frontier slots empty for the next producer and publish the tags
+    volatile Ctl *vc = c;
+    vc->epoch = tag0 + round + 2u;
+    vc->phase = phase0 + splits + 2u;
+    vc->qcnt0 = 0ull;
+    vc->qcnt1 = 0ull;
+    vc->qcnt2 = 0ull;
+    vc->scnt0 = 0u;
+    vc->scnt1 = 0u;
+    vc->scnt2 = 0u;
+    if (OP == kOpPush) {
+      vc->rounds_push = round;
+      vc->splits = splits;
+    } else {
+      vc->rounds_inval = round;
+    }
+    if (capped) atomicCAS(&c->timeout, 0, 1);
+  }
 }
 
 // --- pull (one pass over A) -----------------------------------------------
 
 __global__ void __launch_bounds__(kLoopThreads) k_pull(LoopArgs a) {
+  __shared__ u32 sv[kStageK], sd[kStageK], ssv[kStageK];
+  __shared__ Stage st, sst;
+  __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
   if (!repair_enabled(c)) return;
+  if (threadIdx.x == 0) {
+    st.n = 0; st.cap = kStageK; st.vmin = kInf; st.v = sv; st.d = sd;
+    sst.n = 0; sst.cap = kStageK; sst.vmin = kInf; sst.v = ssv; sst.d = nullptr;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const u64 ac = ld_cg_u64(&c->acnt);
   const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
-  const u32 nch = (nedge + kChunk - 1) / kChunk;
+  const u32 nsmall = ld_cg_u32(&c->ascnt);
+  const u32 sgroups = (nsmall + 31) / 32;
+  const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
   const u32 tag = ld_cg_u32(&c->epoch);
-  PullOp op{a.s, a.qflag, tag, make_queue(a.qent[0], a.qown[0], &c->qcnt0), a.fwd.row};
-  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &st, &sst);
+  PullOp op{a.s, a.qflag, tag, q0, a.fwd.row, &c->seed_min};
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 ch = gw; ch < nch; ch += nw)
-    process_chunk(op, a.aent, a.aown, ne, nedge, ch, a.rev, a.n, c);
+  for (u32 it = gw; it < items; it += nw) {
+    if (it < sgroups) process_small(op, a.asv, nsmall, it, a.rev, a.n, c);
+    else process_chunk(op, a.aent, a.aown, ne, nedge, it - sgroups, a.rev, a.n, c);
+  }
+  flush_queue(q0, scratch);
   u64 e = warp_sum(op.n_edges), q = warp_sum(op.n_enq);
   int re = __any_sync(kFull, op.range_err);
   if (lane == 0) {
@@ -557,13 +951,22 @@ struct AddArgs {
 };
 
 __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
+  __shared__ u32 sv[kStageK], sd[kStageK], ssv[kStageK];
+  __shared__ Stage st, sst;
+  __shared__ u32 scratch[40];
   Ctl *c = a.la.ctl;
   if (!repair_enabled(c)) return;
+  if (threadIdx.x == 0) {
+    st.n = 0; st.cap = kStageK; st.vmin = kInf; st.v = sv; st.d = sd;
+    sst.n = 0; sst.cap = kStageK; sst.vmin = kInf; sst.v = ssv; sst.d = nullptr;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const u32 tag = ld_cg_u32(&c->epoch);
-  const Queue q0 = make_queue(a.la.qent[0], a.la.qown[0], &c->qcnt0);
+  const Queue q0 =
+      make_queue(a.la.qent[0], a.la.qown[0], &c->qcnt0, a.la.qsv[0], &c->scnt0, &st, &sst);
   const u64 cmask = (1ull << a.bits) - 1;
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long gw = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   int range_err = 0;
   u64 n_enq = 0;
@@ -586,7 +989,10 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
             const u64 cand = pack(nd, u);
             if (cand < ld_cg_u64(a.la.s + v[0])) {
               const u64 old = atomicMin((unsigned long long *)(a.la.s + v[0]), cand);
-              if (cand < old) want[0] = atomicExch(a.la.qflag + v[0], tag) != tag;
+              if (cand < old) {
+                atomicMin(&c->seed_min, nd);
+                want[0] = atomicExch(a.la.qflag + v[0], tag) != tag;
+              }
             }
           }
         }
@@ -594,6 +1000,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
     }
     enqueue(q0, a.la.fwd.row, v, want, 1, n_enq);
   }
+  flush_queue(q0, scratch);
   u64 q = warp_sum(n_enq);
   int re = __any_sync(kFull, range_err);
   if (lane == 0) {
@@ -605,19 +1012,23 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
 // --- from-scratch init, unpack ----------------------------------------------
 
 __global__ void k_init(u64 *s, int n, int src, Ctl *c, u32 *qflag, int2 *qent, u32 *qown,
-                       const RowMeta *row) {
+                       u32 *qsv, const RowMeta *row) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x)
     s[v] = v == src ? pack(0, kNoParent) : kInfPack;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     qflag[src] = c->epoch;
     const int d = row[src].deg;
-    if (d > 0) {
+    if (d > kSmallDeg) {
       qent[0] = make_int2(src, 0);
       for (u32 ch = 0; ch <= (u32)(d - 1) / kChunk; ++ch) qown[ch] = 0;
       c->qcnt0 = (1ull << 32) | (u64)d;
+    } else if (d > 0) {
+      qsv[0] = (u32)src;
+      c->scnt0 = 1;
     }
     c->seeds = 1;
+    c->seed_min = 0;
   }
 }
 
@@ -638,12 +1049,17 @@ LoopArgs make_args(sp_graph *g) {
   a.rev = g->rev;
   a.s = g->s;
   a.qflag = g->qflag;
-  a.qent[0] = g->qent[0];
-  a.qent[1] = g->qent[1];
-  a.qown[0] = g->qown[0];
-  a.qown[1] = g->qown[1];
+  for (int b = 0; b < 3; ++b) {
+    a.qent[b] = g->qent[b];
+    a.qown[b] = g->qown[b];
+    a.qsv[b] = g->qsv[b];
+    a.fq[b] = g->fq[b];
+  }
+  a.asv = g->asv;
   a.aent = g->aent;
   a.aown = g->aown;
+  a.ftag = g->ftag;
+  a.xdone = g->xdone;
   a.n = g->n;
   a.del_src = nullptr;
   a.del_dst = nullptr;
@@ -656,7 +1072,10 @@ LoopArgs make_args(sp_graph *g) {
 int loop_blocks(int which, int num_sms) {
   int per_sm = 0;
   const void *fn = which == kOpPush ? (const void *)k_loop<kOpPush> : (const void *)k_loop<kOpInval>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopThreads, 0) != cudaSuccess ||
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopThreads, kLoopSmem) !=
+          cudaSuccess ||
       per_sm < 1)
     return 0;
   return per_sm * num_sms;
@@ -664,7 +1083,7 @@ int loop_blocks(int which, int num_sms) {
 
 void launch_init(sp_graph *g, int source, int *launches) {
   k_init<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(
-      g->s, g->n, source, g->ctl, g->qflag, g->qent[0], g->qown[0], g->fwd.row);
+      g->s, g->n, source, g->ctl, g->qflag, g->qent[0], g->qown[0], g->qsv[0], g->fwd.row);
   ++*launches;
 }
 
@@ -673,7 +1092,8 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) 
   void *args[] = {&a};
   const void *fn = op == kOpPush ? (const void *)k_loop<kOpPush> : (const void *)k_loop<kOpInval>;
   ++*launches;
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kLoopThreads), args, 0, g->stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kLoopThreads), args, kLoopSmem,
+                                     g->stream);
 }
 
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches) {

@@ -11,7 +11,22 @@ namespace sp {
 // kChunk edges, one warp per chunk, 8 consecutive edges per lane.
 constexpr int kChunk = 256;
 constexpr int kEdgesPerLane = kChunk / 32;
-constexpr int kLoopThreads = 512;
+// Vertices with at most kSmallDeg edges go to a frontier's small list and
+// are expanded one lane per vertex; larger ones get edge ranges and chunks.
+constexpr int kSmallDeg = 8;
+constexpr int kLoopThreads = 1024;
+
+// Per-block staging area (shared memory) for appends to a queue or a far
+// pile: warps append here with shared-memory atomics and the block publishes
+// everything with one global atomic when it flushes, instead of one global
+// atomic per warp on a single counter (those serialize at one L2 slice).
+struct Stage {
+  u32 n;        // entries staged
+  u32 cap;
+  u32 vmin;     // far piles: smallest distance staged
+  u32 *v;       // [cap] vertices
+  u32 *d;       // [cap] degrees (queues with edge ranges)
+};
 
 // A frontier queue: entries (v, first edge) in slot order, and for every
 // chunk the slot of the entry holding the chunk's first edge.
@@ -19,6 +34,10 @@ struct Queue {
   int2 *ent = nullptr;
   u32 *owner = nullptr;
   unsigned long long *cnt = nullptr;   // count << 32 | edges (in Ctl)
+  Stage *st = nullptr;                 // block staging, or direct appends
+  u32 *sv = nullptr;                   // small list
+  u32 *scnt = nullptr;
+  Stage *sst = nullptr;
 };
 
 // One touched (store, row) pair of a batch, after sorting.
@@ -26,13 +45,13 @@ struct Seg {
   u32 first, end;        // item range in the sorted batch
   int row;
   int dir;               // 0 = forward store, 1 = reverse store
-  long long dest;        // slot where the merged row is written
-  long long scratch;     // scratch slot for a large in-place merge, else -1
-  long long old_start;   // the row's slots before the merge
+  long long old_start;   // the row's active region before the merge
+  long long dest;        // region the merged row is written to
+  long long new_alt;     // the row's alternate region after the merge
   int old_deg;
   int new_deg;
   int new_cap;
-  int tier;              // 0 warp, 1 block, 2 chunked
+  int pad;
 };
 
 // Per-call buffers that grow on demand.
@@ -45,16 +64,14 @@ struct BatchBufs {
   u64 *item_pref = nullptr;         // exclusive scan of itemv
   u32 *head = nullptr, *head_scan = nullptr;
   Seg *seg = nullptr;
-  u32 *small_list = nullptr, *medium_list = nullptr;
-  u32 *large_list = nullptr, *large_cb = nullptr;   // large tier + first chunk
-  u32 *copy_list = nullptr, *copy_cb = nullptr;     // scratch copy-back
+  int2 *ment = nullptr;             // merge queue: (segment, first element)
+  u32 *mown = nullptr;              // merge chunk -> queue slot
+  long long mown_cap = 0;
   void *tmp = nullptr;
   size_t tmp_bytes = 0;
   long long cap_in = 0;             // staging for host inputs
   int *in_del_src = nullptr, *in_del_dst = nullptr;
   int *in_add_src = nullptr, *in_add_dst = nullptr, *in_add_w = nullptr;
-  int2 *scratch = nullptr;          // merge scratch
-  long long scratch_cap = 0;
 };
 
 // Arguments of the frontier kernels.
@@ -64,10 +81,15 @@ struct LoopArgs {
   Store fwd, rev;
   u64 *s;
   u32 *qflag;
-  int2 *qent[2];         // frontier double buffer
-  u32 *qown[2];
+  int2 *qent[3];         // frontier buffers (rotating)
+  u32 *qown[3];
+  u32 *qsv[3];           // their small lists
+  u32 *asv;              // small list of A
   int2 *aent;            // affected list A (entries carry reverse edges)
   u32 *aown;
+  u32 *fq[3];            // far piles of the near-far push (rotating)
+  u32 *ftag;             // far dedupe tags
+  u64 *xdone;            // call << 32 | distance a vertex was expanded with
   int n;
   // fused OnDelete mark (invalidation loop only)
   const int *del_src, *del_dst;
@@ -88,10 +110,16 @@ struct sp_graph {
   long long m = 0;
   sp::u64 *s = nullptr;
   sp::u32 *qflag = nullptr;
-  int2 *qent[2] = {nullptr, nullptr};
-  sp::u32 *qown[2] = {nullptr, nullptr};
+  int2 *qent[3] = {nullptr, nullptr, nullptr};
+  sp::u32 *qown[3] = {nullptr, nullptr, nullptr};
+  sp::u32 *qsv[3] = {nullptr, nullptr, nullptr};
+  sp::u32 *asv = nullptr;
   int2 *aent = nullptr;
   sp::u32 *aown = nullptr;
+  sp::u32 *fq[3] = {nullptr, nullptr, nullptr};
+  sp::u32 *ftag = nullptr;
+  sp::u64 *xdone = nullptr;
+  int32_t delta_user = 0;
   long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device
   sp::Ctl *ctl_host = nullptr;  // pinned

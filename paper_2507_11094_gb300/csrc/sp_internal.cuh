@@ -30,11 +30,13 @@ __host__ __device__ __forceinline__ u32 dist_of(u64 s) { return (u32)(s >> 32); 
 __host__ __device__ __forceinline__ u32 parent_of(u64 s) { return (u32)s; }
 
 // ---------------------------------------------------------------------------
-// Slack CSR.  Row r occupies adj[start, start+cap); its first deg slots hold
-// (col, w) pairs sorted by col.  Row starts are multiples of 4 slots (32 B,
-// one DRAM sector).  Rows that outgrow their capacity move to the spare pool
-// at the end of adj.
-// ---------------------------------------------------------------------------
+// Slack CSR.  Row r owns two regions of cap slots: the active one,
+// adj[start, start+cap), whose first deg slots hold (col, w) pairs sorted by
+// col, and an alternate one at alt[r].  A batch merge reads the active region
+// and writes the alternate one, then the two swap roles.  Row regions start
+// at multiples of 4 slots (32 B, one DRAM sector).  Rows that outgrow their
+// capacity move to a fresh pair of regions in the spare pool at the end of
+// adj.
 struct __align__(16) RowMeta {
   long long start;
   int deg;
@@ -43,6 +45,7 @@ struct __align__(16) RowMeta {
 
 struct Store {
   RowMeta *row = nullptr;   // [n]
+  long long *alt = nullptr; // [n] start of each row's alternate region
   int2 *adj = nullptr;      // [slots]  (x = col, y = w)
   long long main_slots = 0; // end of the per-row region
   long long slots = 0;      // total = main + pool
@@ -55,7 +58,6 @@ struct Store {
 enum : int {
   kGrowPoolFwd = 1,
   kGrowPoolRev = 2,
-  kGrowScratch = 4,
 };
 
 // Fields that many SMs hit at once (barrier words, queue counters) sit on
@@ -66,42 +68,51 @@ struct Ctl {
   int range_err;         // a candidate distance reached SP_INF
   int timeout;           // 1 = round cap, 2 = barrier wait bound
   int bad;               // an internal bounds check failed (write skipped)
-  // grid barrier (persistent kernels)
-  alignas(128) u32 bar_arrive;
-  alignas(128) u32 bar_gen;
-  // round state, written by the serial step between rounds
-  alignas(128) u32 cur;  // which frontier buffer is current (0/1)
-  u32 round;
-  u32 done;
-  u32 epoch;             // dedupe tag of the frontier being built
-  u32 n_ent;             // entries of the current frontier
-  u32 n_edges;           // edges of the current frontier
-  u32 n_chunks;          // edge chunks of the current frontier
-  // frontier counters (atomics): count << 32 | edges
+  // grid barriers of the two persistent loops (monotone arrival counts)
+  alignas(128) u64 bar_inval;
+  alignas(128) u64 bar_push;
+  // loop bookkeeping shared across launches
+  alignas(128) u32 epoch;          // dedupe tag of the last frontier built
+  u32 phase;                       // far dedupe tag of the last phase
+  u32 call;                        // call id (tags the per-vertex expanded distance)
+  // frontier counters (atomics), triple-buffered: count << 32 | edges
   alignas(128) u64 qcnt0;
   alignas(128) u64 qcnt1;
+  alignas(128) u64 qcnt2;
   alignas(128) u64 acnt;           // affected list A (reverse-store edges)
+  // small-degree lists (one lane per vertex), triple-buffered, and A's
+  alignas(128) u32 scnt0;
+  alignas(128) u32 scnt1;
+  alignas(128) u32 scnt2;
+  alignas(128) u32 ascnt;
+  // far piles of the near-far push, triple-buffered
+  alignas(128) u32 fcnt0;
+  alignas(128) u32 fcnt1;
+  alignas(128) u32 fcnt2;
+  alignas(128) u32 fmin0;
+  alignas(128) u32 fmin1;
+  alignas(128) u32 fmin2;
+  alignas(128) u32 seed_min;       // smallest distance seeded into the push
   // batch bookkeeping
+  alignas(128) u64 mcnt;           // merge elements: segments << 32 | elements
   alignas(128) u32 n_seg;          // touched (dir,row) segments
-  u32 n_small, n_medium;           // segments of the warp / block merge tiers
-  u64 large_pack;                  // large tier: count << 40 | chunks
-  u64 copy_pack;                   // scratch copy-back: count << 40 | chunks
   u64 pool_used[2];      // spare slots taken (fwd, rev), persistent
   u64 pool_need[2];      // demand seen by the last count pass
-  u64 scratch_used;      // merge scratch slots reserved this batch
   // counters of the call
   alignas(128) u64 del_applied;
   u64 del_absent, add_applied, add_present;
   u64 affected, seeds, relaxed, improved, rows_touched, rows_relocated;
   u64 inval_edges, pull_edges, push_vertices, enqueued;
   u64 merge_slots;       // old + new slots of all merged rows
-  u32 rounds_inval, rounds_push;
+  u64 far_moves;         // far-pile entries moved back to near
+  u32 rounds_inval, rounds_push, splits;
 };
 
-// Launch-time limits.
+// Launch-time limits and knobs.
 struct Limits {
   u32 max_rounds;        // per fixedPoint loop
   u64 wait_ns;           // per barrier wait
+  u32 delta;             // near-far bucket width of the push loop (0 = off)
 };
 
 // ---------------------------------------------------------------------------

@@ -27,11 +27,15 @@ k_hist(const u64 *__restrict__ keys, long long n, int shift, u32 *__restrict__ c
   h[threadIdx.x] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * kTile;
+  u32 d[kItems];
 #pragma unroll
-  for (int k = 0; k < kItems; ++k) {
+  for (int k = 0; k < kItems; ++k) {   // all loads first, then the counts
     long long i = base + k * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1)], 1u);
+    d[k] = i < n ? (u32)((keys[i] >> shift) & (kBins - 1)) : 0xFFFFFFFFu;
   }
+#pragma unroll
+  for (int k = 0; k < kItems; ++k)
+    if (d[k] != 0xFFFFFFFFu) atomicAdd(&h[d[k]], 1u);
   __syncthreads();
   counts[(long long)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
@@ -51,13 +55,21 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
   __syncthreads();
   const long long base = (long long)blockIdx.x * kTile;
   const u32 lt = lanemask_lt();
-#pragma unroll 1
+  u64 rk[kItems];
+  u32 rv[kItems];
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {   // the whole tile is in flight at once
+    const long long i = base + k * kThreads + t;
+    rk[k] = i < n ? keys[i] : 0ull;
+    rv[k] = i < n ? vals[i] : 0u;
+  }
+#pragma unroll
   for (int k = 0; k < kItems; ++k) {
     const int p = k & 1;
     const long long i = base + k * kThreads + t;
     const bool valid = i < n;
-    u64 key = valid ? keys[i] : 0ull;
-    u32 val = valid ? vals[i] : 0u;
+    const u64 key = rk[k];
+    const u32 val = rv[k];
     u32 d = valid ? (u32)((key >> shift) & (kBins - 1)) : (u32)(kBins + lane);
     u32 peers = __match_any_sync(0xffffffffu, d);
     u32 rank = __popc(peers & lt);

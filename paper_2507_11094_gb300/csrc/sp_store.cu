@@ -18,9 +18,7 @@ namespace sp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSmallRow = 256;     // rows merged by one warp: deg <= this
-constexpr int kSmallItems = 256;   // ... and at most this many batch items
-constexpr int kPerLane = kSmallRow / 32;
+constexpr u32 kFull = 0xffffffffu;
 
 inline unsigned blocks_for(long long work, int per_block, int cap) {
   long long b = (work + per_block - 1) / per_block;
@@ -30,6 +28,44 @@ inline unsigned blocks_for(long long work, int per_block, int cap) {
 }
 
 __device__ __forceinline__ void set_status(Ctl *c, int st) { atomicCAS(&c->status, 0, st); }
+
+__device__ __forceinline__ u32 warp_incl_scan_u32(u32 x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive prefix of one value per thread over the block (smem scratch of
+// 32 words); the block total goes to *total.
+__device__ __forceinline__ u32 block_excl_scan_u32(u32 x, u32 *scratch, u32 *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const u32 incl = warp_incl_scan_u32(x);
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    u32 v = lane < nwarps ? scratch[lane] : 0u;
+    v = warp_incl_scan_u32(v);
+    if (lane < nwarps) scratch[lane] = v;
+  }
+  __syncthreads();
+  const u32 r = (warp ? scratch[warp - 1] : 0u) + incl - x;
+  *total = scratch[nwarps - 1];
+  __syncthreads();
+  return r;
+}
+
+// Add per-thread counters into global ones with one atomic per block.
+__device__ __forceinline__ void block_add(u64 v, u64 *sm, u64 *global) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long *)sm, v);
+  __syncthreads();
+  if (threadIdx.x == 0 && *sm) atomicAdd((unsigned long long *)global, *sm);
+}
 
 // --------------------------------------------------------------------------
 // building a store from a CSR
@@ -89,11 +125,12 @@ __global__ void k_row_caps(const long long *__restrict__ first, const long long 
                            int n, float slack, u64 *cap_out) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x)
-    cap_out[r] = (u64)row_capacity(last[r] - first[r], slack);
+    cap_out[r] = 2ull * (u64)row_capacity(last[r] - first[r], slack);   // two regions
 }
 
 __global__ void k_row_meta(const long long *__restrict__ first, const long long *__restrict__ last,
-                           const u64 *__restrict__ cap_scan, int n, float slack, RowMeta *row) {
+                           const u64 *__restrict__ cap_scan, int n, float slack, RowMeta *row,
+                           long long *alt) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
     long long d = last[r] - first[r];
@@ -102,6 +139,7 @@ __global__ void k_row_meta(const long long *__restrict__ first, const long long 
     rm.deg = (int)d;
     rm.cap = row_capacity(d, slack);
     row[r] = rm;
+    alt[r] = rm.start + rm.cap;
   }
 }
 
@@ -161,26 +199,29 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->range_err = 0;
   c->timeout = 0;
   c->bad = 0;
-  c->bar_arrive = 0;
-  c->cur = 0;
-  c->round = 0;
-  c->done = 0;
-  c->n_ent = c->n_edges = c->n_chunks = 0;
-  c->qcnt0 = c->qcnt1 = c->acnt = 0;
-  c->n_seg = c->n_small = c->n_medium = 0;
-  c->large_pack = c->copy_pack = 0;
+  c->bar_inval = 0;
+  c->bar_push = 0;
+  c->qcnt0 = c->qcnt1 = c->qcnt2 = c->acnt = 0;
+  c->scnt0 = c->scnt1 = c->scnt2 = c->ascnt = 0;
+  c->fcnt0 = c->fcnt1 = c->fcnt2 = 0;
+  c->fmin0 = c->fmin1 = c->fmin2 = kInf;
+  c->seed_min = kInf;
+  c->mcnt = 0;
+  c->n_seg = 0;
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
-  c->scratch_used = 0;
   c->del_applied = c->del_absent = c->add_applied = c->add_present = 0;
   c->affected = c->seeds = c->relaxed = c->improved = 0;
   c->rows_touched = c->rows_relocated = 0;
   c->inval_edges = c->pull_edges = c->push_vertices = c->enqueued = 0;
   c->merge_slots = 0;
-  c->rounds_inval = c->rounds_push = 0;
+  c->far_moves = 0;
+  c->rounds_inval = c->rounds_push = c->splits = 0;
+  c->call = c->call + 1;
   if (full) {
-    c->bar_gen = 0;
     c->epoch = 1;
+    c->phase = 1;
+    c->call = 1;
     c->pool_used[0] = c->pool_used[1] = 0;
     c->pool_need[0] = c->pool_need[1] = 0;
   }
@@ -251,11 +292,7 @@ __global__ void k_seg_emit(const u64 *__restrict__ keys, const u32 *__restrict__
 // batch: count pass (which updates apply, new row sizes, where rows go)
 // --------------------------------------------------------------------------
 
-constexpr int kMedRow = 4096;      // rows merged in place by one block
-constexpr int kMedThreads = 512;
-constexpr int kMedPer = kMedRow / kMedThreads;
-constexpr int kLargeChunk = 4096;  // elements per block in the chunked tier
-constexpr u64 kMask40 = (1ull << 40) - 1;
+constexpr int kElemPerLane = kChunk / 32;   // merge elements per lane
 
 // First slot j in [0, deg) of a sorted row with row[j].x >= c.
 __device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) {
@@ -284,11 +321,11 @@ struct CountArgs {
   unsigned char *flags;
   u64 *itemv;
   const u64 *item_pref;
-  u32 *small_list, *medium_list, *large_list, *large_cb, *copy_list, *copy_cb;
+  int2 *ment;
+  u32 *mown;
   Store st[2];
   int bits;
   float slack;
-  long long scratch_cap;
   u32 n_items;
   int n;
 };
@@ -345,25 +382,22 @@ __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
       }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    del_ok += __shfl_xor_sync(0xffffffffu, del_ok, o);
-    del_abs += __shfl_xor_sync(0xffffffffu, del_abs, o);
-    add_ok += __shfl_xor_sync(0xffffffffu, add_ok, o);
-    add_pres += __shfl_xor_sync(0xffffffffu, add_pres, o);
-  }
-  if (lane == 0) {
-    if (del_ok) atomicAdd(&c->del_applied, del_ok);
-    if (del_abs) atomicAdd(&c->del_absent, del_abs);
-    if (add_ok) atomicAdd(&c->add_applied, add_ok);
-    if (add_pres) atomicAdd(&c->add_present, add_pres);
-  }
+  __shared__ u64 sums[4];
+  if (threadIdx.x < 4) sums[threadIdx.x] = 0;
+  __syncthreads();
+  (void)lane;
+  block_add(del_ok, &sums[0], &c->del_applied);
+  block_add(del_abs, &sums[1], &c->del_absent);
+  block_add(add_ok, &sums[2], &c->add_applied);
+  block_add(add_pres, &sums[3], &c->add_present);
 }
 
-// One thread per touched row: new size (from the item prefix counts), merge
-// tier, destination (in place, or a fresh spare-pool segment when the row
-// outgrows its capacity), scratch and chunk reservations.
+// One thread per touched row: new size (from the item prefix counts),
+// destination (the row's alternate region, or a fresh pair of regions in the
+// spare pool when the row outgrows its capacity), and a reservation of the
+// row's merge elements (old entries, then batch items) in the merge queue.
 __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
+  __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
   if (ld_cg_i32(&c->status) != 0) return;
   const int lane = threadIdx.x & 31;
@@ -371,77 +405,78 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
   u64 touched = 0, relocated = 0, slots = 0;
   for (u32 base = blockIdx.x * blockDim.x; base < nseg; base += gridDim.x * blockDim.x) {
     const u32 si = base + threadIdx.x;
-    if (si >= nseg) continue;
-    Seg sg = a.seg[si];
-    if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
-        sg.dir < 0 || sg.dir > 1) {  // never expected: record and skip
-      atomicExch(&c->bad, 1);
-      continue;
-    }
-    const Store &st = a.st[sg.dir];
-    const RowMeta rm = st.row[sg.row];
-    const u64 p = a.item_pref[sg.end] - a.item_pref[sg.first];
-    const int new_deg = rm.deg - (int)(u32)p + (int)(u32)(p >> 32);
-    const int nitems = (int)(sg.end - sg.first);
-    sg.old_start = rm.start;
-    sg.old_deg = rm.deg;
-    sg.new_deg = new_deg;
-    sg.scratch = -1;
-    sg.tier = (rm.deg <= kSmallRow && nitems <= kSmallItems) ? 0
-            : (rm.deg <= kMedRow && nitems <= kMedRow) ? 1 : 2;
-    const bool reloc = new_deg > rm.cap;
-    if (reloc) {
-      long long nc = row_capacity(new_deg, a.slack);
-      const long long dbl = round_up4(2LL * rm.cap);
-      if (dbl > nc) nc = dbl;
-      const u64 off = atomicAdd(&c->pool_need[sg.dir], (u64)nc);
-      if ((long long)(off + nc) > st.slots - st.main_slots)
-        atomicOr(&c->need_grow, sg.dir ? kGrowPoolRev : kGrowPoolFwd);
-      sg.dest = st.main_slots + (long long)off;
-      sg.new_cap = (int)nc;
-      ++relocated;
-    } else {
-      sg.dest = rm.start;
-      sg.new_cap = rm.cap;
-    }
-    if (sg.tier == 0) {
-      a.small_list[atomicAdd(&c->n_small, 1u)] = si;
-    } else if (sg.tier == 1) {
-      a.medium_list[atomicAdd(&c->n_medium, 1u)] = si;
-    } else {
-      if (!reloc && new_deg > 0) {  // written to scratch, then copied back
-        const u64 off = atomicAdd(&c->scratch_used, (u64)new_deg);
-        if ((long long)(off + new_deg) > a.scratch_cap) atomicOr(&c->need_grow, kGrowScratch);
-        sg.scratch = (long long)off;
-        const u64 nch = (u64)((new_deg + kLargeChunk - 1) / kLargeChunk);
-        const u64 o2 = atomicAdd((unsigned long long *)&c->copy_pack, (1ull << 40) | nch);
-        a.copy_list[o2 >> 40] = si;
-        a.copy_cb[o2 >> 40] = (u32)(o2 & kMask40);
+    bool ok = si < nseg;
+    Seg sg;
+    u32 tot = 0;
+    if (ok) {
+      sg = a.seg[si];
+      if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
+          sg.dir < 0 || sg.dir > 1) {  // never expected: record and skip
+        atomicExch(&c->bad, 1);
+        ok = false;
       }
-      const u64 nch = (u64)((rm.deg + nitems + kLargeChunk - 1) / kLargeChunk);
-      const u64 o = atomicAdd((unsigned long long *)&c->large_pack, (1ull << 40) | nch);
-      a.large_list[o >> 40] = si;
-      a.large_cb[o >> 40] = (u32)(o & kMask40);
     }
-    a.seg[si] = sg;
-    ++touched;
-    slots += (u64)rm.deg + (u64)new_deg;
+    if (ok) {
+      const Store &st = a.st[sg.dir];
+      const RowMeta rm = st.row[sg.row];
+      const u64 p = a.item_pref[sg.end] - a.item_pref[sg.first];
+      const int new_deg = rm.deg - (int)(u32)p + (int)(u32)(p >> 32);
+      sg.old_start = rm.start;
+      sg.old_deg = rm.deg;
+      sg.new_deg = new_deg;
+      sg.pad = 0;
+      if (new_deg > rm.cap) {
+        long long nc = row_capacity(new_deg, a.slack);
+        const long long dbl = round_up4(2LL * rm.cap);
+        if (dbl > nc) nc = dbl;
+        const u64 off = atomicAdd(&c->pool_need[sg.dir], (u64)(2 * nc));
+        if ((long long)(off + 2 * nc) > st.slots - st.main_slots)
+          atomicOr(&c->need_grow, sg.dir ? kGrowPoolRev : kGrowPoolFwd);
+        sg.dest = st.main_slots + (long long)off;
+        sg.new_alt = sg.dest + nc;
+        sg.new_cap = (int)nc;
+        ++relocated;
+      } else {
+        sg.dest = st.alt[sg.row];
+        sg.new_alt = rm.start;
+        sg.new_cap = rm.cap;
+      }
+      a.seg[si] = sg;
+      tot = (u32)rm.deg + (sg.end - sg.first);
+      ++touched;
+      slots += (u64)rm.deg + (u64)new_deg;
+    }
+    // reserve merge elements: one packed atomic per block
+    const u32 cnt = ok ? 1u : 0u;
+    u32 ctot, ttot;
+    const u32 ce = block_excl_scan_u32(cnt, scratch, &ctot);
+    const u32 te = block_excl_scan_u32(tot, scratch, &ttot);
+    if (threadIdx.x == 0) {
+      const u64 b = ctot ? atomicAdd((unsigned long long *)&c->mcnt, ((u64)ctot << 32) | ttot) : 0;
+      scratch[32] = (u32)(b >> 32);
+      scratch[33] = (u32)b;
+    }
+    __syncthreads();
+    const u32 bhi = scratch[32], blo = scratch[33];
+    __syncthreads();
+    if (ok) {
+      const u32 slot = bhi + ce, eb = blo + te;
+      a.ment[slot] = make_int2((int)si, (int)eb);
+      const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + tot - 1) / kChunk;
+      for (u32 ch = c0; ch <= c1; ++ch) a.mown[ch] = slot;
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    touched += __shfl_xor_sync(0xffffffffu, touched, o);
-    relocated += __shfl_xor_sync(0xffffffffu, relocated, o);
-    slots += __shfl_xor_sync(0xffffffffu, slots, o);
-  }
-  if (lane == 0) {
-    if (touched) atomicAdd(&c->rows_touched, touched);
-    if (relocated) atomicAdd(&c->rows_relocated, relocated);
-    if (slots) atomicAdd(&c->merge_slots, slots);
-  }
+  __shared__ u64 sums[3];
+  if (threadIdx.x < 3) sums[threadIdx.x] = 0;
+  __syncthreads();
+  (void)lane;
+  block_add(touched, &sums[0], &c->rows_touched);
+  block_add(relocated, &sums[1], &c->rows_relocated);
+  block_add(slots, &sums[2], &c->merge_slots);
 }
 
 // --------------------------------------------------------------------------
-// batch: merge pass (rewrite each touched row)
+// batch: merge pass (rewrite each touched row into its other region)
 // --------------------------------------------------------------------------
 
 struct MergeArgs {
@@ -451,9 +486,9 @@ struct MergeArgs {
   const unsigned char *flags;
   const u64 *item_pref;   // exclusive scan of itemv, n_items + 1 entries
   const Seg *seg;
-  const u32 *list, *list_cb;
+  const int2 *ment;
+  const u32 *mown;
   Store st[2];
-  int2 *scratch;
   int bits;
 };
 
@@ -462,220 +497,143 @@ __device__ __forceinline__ bool merge_enabled(Ctl *c) {
          ld_cg_i32(&c->bad) == 0;
 }
 
-// Output slot of old entry j (col c) of a row, or -1 if the batch deletes it.
-// Items with col < c are [first, i); the new row holds the kept old entries
-// and the applied insertions in col order.
-__device__ __forceinline__ int old_entry_pos(const MergeArgs &a, const Seg &sg, u64 prefix,
-                                             u64 base_pref, int j, int c) {
-  const u64 k = prefix | ((u64)(unsigned)c << 1);
-  const u32 i = items_lower_bound(a.keys, sg.first, sg.end, k);
-  if (i < sg.end && a.keys[i] == k && (a.flags[i] & 1)) return -1;  // applied deletion
-  const u64 p = a.item_pref[i] - base_pref;
-  return j - (int)(u32)p + (int)(u32)(p >> 32);
-}
-
-// Output slot of applied insertion item i (col c).
-__device__ __forceinline__ int add_entry_pos(const MergeArgs &a, const Seg &sg, u64 prefix,
-                                             u64 base_pref, const int2 *old, int deg, u32 i,
-                                             int c) {
-  const int pos_old = row_lower_bound(old, deg, c);
-  const u32 i0 = items_lower_bound(a.keys, sg.first, i, prefix | ((u64)(unsigned)c << 1));
-  const u64 p0 = a.item_pref[i0] - base_pref;
-  const u64 pi = a.item_pref[i] - base_pref;
-  return pos_old - (int)(u32)p0 + (int)(u32)(pi >> 32);
-}
-
-__device__ __forceinline__ void write_meta(const Store &st, const Seg &sg) {
-  RowMeta nm;
-  nm.start = sg.dest;
-  nm.deg = sg.new_deg;
-  nm.cap = sg.new_cap;
-  st.row[sg.row] = nm;
-}
-
-// Tier 0: one warp per row with deg <= 256 and <= 256 items.  All reads go to
-// registers before any write, so the row is rewritten in place.
-__global__ void __launch_bounds__(kThreads) k_merge_small(MergeArgs a) {
+// The merged row holds the kept old entries and the applied insertions in
+// col order, so every element knows its output slot from prefix counts:
+//   old entry j (col c):      j - #applied deletions with col < c
+//                               + #applied insertions with col < c
+//   applied insertion (col c): #old entries with col < c
+//                               - #applied deletions with col < c
+//                               + #applied insertions before it.
+// Items are sorted by (col, deletion before insertion), so "col < c" is an
+// item index range [first, i).  Elements are independent: the queue spreads
+// them over all warps, kElemPerLane consecutive elements per lane, and each
+// lane walks its run segment by segment.
+__global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
   Ctl *c = a.ctl;
   if (!merge_enabled(c)) return;
   const int lane = threadIdx.x & 31;
-  const u32 nlist = ld_cg_u32(&c->n_small);
-  const u32 warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u32 nwarps = (gridDim.x * blockDim.x) >> 5;
+  const u64 pk = ld_cg_u64(&c->mcnt);
+  const u32 ne = (u32)(pk >> 32), nel = (u32)pk;
+  const u32 nch = (nel + kChunk - 1) / kChunk;
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
   const u64 cmask = (1ull << a.bits) - 1;
-  for (u32 li = warp0; li < nlist; li += nwarps) {
-    const Seg sg = a.seg[a.list[li]];
-    const Store &st = a.st[sg.dir];
-    const int2 *old = st.adj + sg.old_start;
-    const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
-    const u64 base_pref = a.item_pref[sg.first];
-    int2 ent[kPerLane];
-    int pos[kPerLane];
+  const u64 kmask = ~((2ull << a.bits) - 1);
+  bool bad = false;
+  for (u32 ch = gw; ch < nch; ch += nw) {
+    const u32 e0 = ch * kChunk;
+    const u32 e_end = e0 + kChunk < nel ? e0 + kChunk : nel;
+    const u32 jw = __ldcg(a.mown + ch);
+    // owner of this lane's first element: search a window of 32 queue entries
+    const u32 wj = jw + lane;
+    const u32 web = wj < ne ? (u32)__ldcg(&a.ment[wj].y) : 0xFFFFFFFFu;
+    const u32 ebeg = e0 + (u32)(kElemPerLane * lane);
+    int o = 0;
 #pragma unroll
-    for (int t = 0; t < kPerLane; ++t) {
-      const int j = lane + 32 * t;
-      pos[t] = -1;
-      if (j < sg.old_deg) {
-        ent[t] = old[j];
-        pos[t] = old_entry_pos(a, sg, prefix, base_pref, j, ent[t].x);
-      }
+    for (int step = 16; step > 0; step >>= 1) {
+      const u32 ebc = __shfl_sync(kFull, web, (o + step) & 31);
+      if (o + step < 32 && ebc <= ebeg) o += step;
     }
-    int2 aent[kPerLane];
-    int apos[kPerLane];
+    if (ebeg >= e_end) continue;
+    // every entry holds >= 1 element and entries after jw start inside this
+    // chunk, so the entry holding any element of the chunk is below jw + 256
+    const u32 slot_hi = (jw + kChunk < ne ? jw + kChunk : ne) - 1;
+    u32 slot_lo = jw + (u32)o;
+    const u32 eL = ebeg + kElemPerLane < e_end ? ebeg + kElemPerLane : e_end;
+    u32 e = ebeg;
+    while (e < eL) {
+      // entry holding e: last slot in [slot_lo, slot_hi] whose first element <= e
+      u32 slot = slot_lo;
+      if (slot < slot_hi && (u32)__ldcg(&a.ment[slot + 1].y) <= e) {
+        u32 lo = slot + 1, hi = slot_hi;
+        while (lo < hi) {
+          const u32 mid = (lo + hi + 1) >> 1;
+          if ((u32)__ldcg(&a.ment[mid].y) <= e) lo = mid; else hi = mid - 1;
+        }
+        slot = lo;
+      }
+      const int2 en0 = __ldcg(a.ment + slot);
+      const Seg sg = a.seg[en0.x];
+      const Store &st = a.st[sg.dir];
+      const int2 *old = st.adj + sg.old_start;
+      int2 *dst = st.adj + sg.dest;
+      const u64 prefix = a.keys[sg.first] & kmask;
+      const u64 base_pref = a.item_pref[sg.first];
+      const u32 eb = (u32)en0.y;
+      const u32 tot = (u32)sg.old_deg + (sg.end - sg.first);
+      const u32 r_end = eL < eb + tot ? eL : eb + tot;
+      if (e == eb) {  // first element of the row publishes the new metadata
+        RowMeta nm;
+        nm.start = sg.dest;
+        nm.deg = sg.new_deg;
+        nm.cap = sg.new_cap;
+        st.row[sg.row] = nm;
+        st.alt[sg.row] = sg.new_alt;
+      }
+      // old entries of the run, loaded together
+      const u32 j0 = e - eb;
+      const u32 jl = r_end - eb < (u32)sg.old_deg ? r_end - eb : (u32)sg.old_deg;
+      int2 en[kElemPerLane];
 #pragma unroll
-    for (int t = 0; t < kPerLane; ++t) {
-      const u32 i = sg.first + lane + 32 * t;
-      apos[t] = -1;
-      if (i < sg.end && (a.keys[i] & 1) && (a.flags[i] & 1)) {
-        const int col = (int)((a.keys[i] >> 1) & cmask);
-        aent[t] = make_int2(col, (int)a.vals[i]);
-        apos[t] = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
-      }
-    }
-    __syncwarp();
-    int2 *dst = st.adj + sg.dest;
-    bool bad = false;
+      for (int t = 0; t < kElemPerLane; ++t)
+        en[t] = (j0 + t < jl) ? old[j0 + t] : make_int2(0, 0);
+      if (j0 < jl) {
+        // item cursor: first item with col >= the run's first col, then walk
+        u32 ic;
+        {
+          u32 lo = sg.first, hi = sg.end;
+          const u64 k0 = prefix | ((u64)(unsigned)en[0].x << 1);
+          while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            if (a.keys[mid] < k0) lo = mid + 1; else hi = mid;
+          }
+          ic = lo;
+        }
 #pragma unroll
-    for (int t = 0; t < kPerLane; ++t) {
-      if (pos[t] >= 0) {
-        if (pos[t] < sg.new_deg) dst[pos[t]] = ent[t]; else bad = true;
-      }
-      if (apos[t] >= 0) {
-        if (apos[t] < sg.new_deg) dst[apos[t]] = aent[t]; else bad = true;
-      }
-    }
-    if (bad) atomicExch(&c->bad, 1);
-    if (lane == 0) write_meta(st, sg);
-    __syncwarp();
-  }
-}
-
-// Tier 1: one block per row with deg <= 4096 and <= 4096 items, rewritten in
-// place: every thread holds its entries in registers across a block barrier.
-__global__ void __launch_bounds__(kMedThreads) k_merge_medium(MergeArgs a) {
-  Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
-  const u32 nlist = ld_cg_u32(&c->n_medium);
-  const u64 cmask = (1ull << a.bits) - 1;
-  for (u32 li = blockIdx.x; li < nlist; li += gridDim.x) {
-    const Seg sg = a.seg[a.list[li]];
-    const Store &st = a.st[sg.dir];
-    const int2 *old = st.adj + sg.old_start;
-    const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
-    const u64 base_pref = a.item_pref[sg.first];
-    int2 ent[kMedPer];
-    int pos[kMedPer];
-#pragma unroll
-    for (int t = 0; t < kMedPer; ++t) {
-      const int j = threadIdx.x + kMedThreads * t;
-      pos[t] = -1;
-      if (j < sg.old_deg) {
-        ent[t] = old[j];
-        pos[t] = old_entry_pos(a, sg, prefix, base_pref, j, ent[t].x);
-      }
-    }
-    int2 aent[kMedPer];
-    int apos[kMedPer];
-#pragma unroll
-    for (int t = 0; t < kMedPer; ++t) {
-      const u32 i = sg.first + threadIdx.x + kMedThreads * t;
-      apos[t] = -1;
-      if (i < sg.end && (a.keys[i] & 1) && (a.flags[i] & 1)) {
-        const int col = (int)((a.keys[i] >> 1) & cmask);
-        aent[t] = make_int2(col, (int)a.vals[i]);
-        apos[t] = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
-      }
-    }
-    __syncthreads();
-    int2 *dst = st.adj + sg.dest;
-    bool bad = false;
-#pragma unroll
-    for (int t = 0; t < kMedPer; ++t) {
-      if (pos[t] >= 0) {
-        if (pos[t] < sg.new_deg) dst[pos[t]] = ent[t]; else bad = true;
-      }
-      if (apos[t] >= 0) {
-        if (apos[t] < sg.new_deg) dst[apos[t]] = aent[t]; else bad = true;
-      }
-    }
-    if (bad) atomicExch(&c->bad, 1);
-    if (threadIdx.x == 0) write_meta(st, sg);
-    __syncthreads();
-  }
-}
-
-// Slot in a packed (count << 40 | chunks) list owning chunk `ch`.
-__device__ __forceinline__ u32 chunk_owner(const u32 *cb, u32 count, u32 ch) {
-  u32 lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const u32 mid = (lo + hi + 1) >> 1;
-    if (__ldcg(cb + mid) <= ch) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Tier 2: rows too large for one block, split into chunks of 4096 elements
-// (old entries, then batch items) over all blocks.  Output goes out of place:
-// to the row's new pool segment, or to scratch and then back (k_merge_copy),
-// so no chunk reads a slot another chunk has rewritten.
-__global__ void __launch_bounds__(kThreads) k_merge_large(MergeArgs a) {
-  Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
-  const u64 pk = ld_cg_u64(&c->large_pack);
-  const u32 nlist = (u32)(pk >> 40), nch = (u32)(pk & kMask40);
-  const u64 cmask = (1ull << a.bits) - 1;
-  for (u32 ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const u32 slot = chunk_owner(a.list_cb, nlist, ch);
-    const Seg sg = a.seg[__ldcg(a.list + slot)];
-    const Store &st = a.st[sg.dir];
-    const int2 *old = st.adj + sg.old_start;
-    const u64 prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
-    const u64 base_pref = a.item_pref[sg.first];
-    int2 *target = sg.scratch >= 0 ? a.scratch + sg.scratch : st.adj + sg.dest;
-    const long long e0 = (long long)(ch - __ldcg(a.list_cb + slot)) * kLargeChunk;
-    const long long ne = (long long)sg.old_deg + (sg.end - sg.first);
-    const long long e1 = e0 + kLargeChunk < ne ? e0 + kLargeChunk : ne;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      if (e < sg.old_deg) {
-        const int j = (int)e;
-        const int2 en = old[j];
-        const int p = old_entry_pos(a, sg, prefix, base_pref, j, en.x);
-        if (p >= sg.new_deg) atomicExch(&c->bad, 1);
-        else if (p >= 0) target[p] = en;
-      } else {
-        const u32 i = sg.first + (u32)(e - sg.old_deg);
-        if ((a.keys[i] & 1) && (a.flags[i] & 1)) {
-          const int col = (int)((a.keys[i] >> 1) & cmask);
-          const int p = add_entry_pos(a, sg, prefix, base_pref, old, sg.old_deg, i, col);
-          if (p < 0 || p >= sg.new_deg) atomicExch(&c->bad, 1);
-          else target[p] = make_int2(col, (int)a.vals[i]);
+        for (int t = 0; t < kElemPerLane; ++t) {
+          if (j0 + t < jl) {
+            const u64 kc = prefix | ((u64)(unsigned)en[t].x << 1);
+            while (ic < sg.end && a.keys[ic] < kc) ++ic;
+            const bool del = ic < sg.end && a.keys[ic] == kc && (a.flags[ic] & 1);
+            if (!del) {
+              const u64 pp = a.item_pref[ic] - base_pref;
+              const int pos = (int)(j0 + t) - (int)(u32)pp + (int)(u32)(pp >> 32);
+              if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
+              else bad = true;
+            }
+          }
         }
       }
+      // batch items of the run: applied insertions
+      const u32 i_lo = (e - eb > (u32)sg.old_deg ? e - eb : (u32)sg.old_deg) - sg.old_deg;
+      const u32 i_hi = r_end - eb > (u32)sg.old_deg ? r_end - eb - sg.old_deg : 0u;
+      for (u32 ii = i_lo; ii < i_hi; ++ii) {
+        const u32 i = sg.first + ii;
+        const u64 key = a.keys[i];
+        if ((key & 1) && (a.flags[i] & 1)) {
+          const int col = (int)((key >> 1) & cmask);
+          int lo = 0, hi = sg.old_deg;   // old entries with col < this col
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (old[mid].x < col) lo = mid + 1; else hi = mid;
+          }
+          u32 l2 = sg.first, h2 = i;     // items with col < this col
+          const u64 k0 = prefix | ((u64)(unsigned)col << 1);
+          while (l2 < h2) {
+            const u32 mid = (l2 + h2) >> 1;
+            if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
+          }
+          const u64 p0 = a.item_pref[l2] - base_pref, pi = a.item_pref[i] - base_pref;
+          const int pos = lo - (int)(u32)p0 + (int)(u32)(pi >> 32);
+          if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
+          else bad = true;
+        }
+      }
+      e = r_end;
+      slot_lo = slot + 1;
     }
   }
-}
-
-// Tier 2, second pass: copy scratch back into rows merged in place, and
-// publish the new row metadata of every tier-2 row.
-__global__ void __launch_bounds__(kThreads) k_merge_copy(MergeArgs a, const u32 *large_list) {
-  Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
-  const u64 pk = ld_cg_u64(&c->copy_pack);
-  const u32 nlist = (u32)(pk >> 40), nch = (u32)(pk & kMask40);
-  for (u32 ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const u32 slot = chunk_owner(a.list_cb, nlist, ch);
-    const Seg sg = a.seg[__ldcg(a.list + slot)];
-    const int2 *src = a.scratch + sg.scratch;
-    int2 *dst = a.st[sg.dir].adj + sg.dest;
-    const long long e0 = (long long)(ch - __ldcg(a.list_cb + slot)) * kLargeChunk;
-    const long long e1 = e0 + kLargeChunk < sg.new_deg ? e0 + kLargeChunk : sg.new_deg;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) dst[e] = __ldcg(src + e);
-  }
-  const u32 nl = (u32)(ld_cg_u64(&c->large_pack) >> 40);
-  for (u32 li = blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += gridDim.x * blockDim.x) {
-    const Seg sg = a.seg[__ldcg(large_list + li)];
-    write_meta(a.st[sg.dir], sg);
-  }
+  if (bad) atomicExch(&c->bad, 1);
 }
 
 __global__ void k_finish(Ctl *c) {
@@ -762,11 +720,12 @@ sp_status store_build(sp_graph *g, Store *st, const long long *row_off_d, const 
       st->main_slots = (long long)main_slots;
       st->slots = st->main_slots + pool;
       st->row = (RowMeta *)g->al.get((size_t)n * sizeof(RowMeta));
+      st->alt = (long long *)g->al.get((size_t)n * sizeof(long long));
       st->adj = (int2 *)g->al.get((size_t)st->slots * sizeof(int2));
-      if (!st->row || !st->adj) rc = SP_ENOMEM;
+      if (!st->row || !st->alt || !st->adj) rc = SP_ENOMEM;
     }
     if (rc == SP_OK) {
-      k_row_meta<<<grid, kThreads, 0, s>>>(first, last, caps, n, g->slack, st->row);
+      k_row_meta<<<grid, kThreads, 0, s>>>(first, last, caps, n, g->slack, st->row, st->alt);
       ++*launches;
       if (m > 0) {
         k_fill_adj<<<grid, kThreads, 0, s>>>(keys, vals, m, bits, first, st->row, st->adj);
@@ -836,14 +795,16 @@ sp_status ensure_owner_tables(sp_graph *g) {
   const long long need = slots / kChunk + 64;
   if (need <= g->own_cap && g->qown[0]) return SP_OK;
   const long long c = std::max(need, g->own_cap * 2);
-  g->al.put(g->qown[0], (size_t)g->own_cap * 4);
-  g->al.put(g->qown[1], (size_t)g->own_cap * 4);
+  for (int b = 0; b < 3; ++b) g->al.put(g->qown[b], (size_t)g->own_cap * 4);
   g->al.put(g->aown, (size_t)g->own_cap * 4);
-  g->qown[0] = (u32 *)g->al.get((size_t)c * 4);
-  g->qown[1] = (u32 *)g->al.get((size_t)c * 4);
+  bool ok = true;
+  for (int b = 0; b < 3; ++b) {
+    g->qown[b] = (u32 *)g->al.get((size_t)c * 4);
+    ok = ok && g->qown[b];
+  }
   g->aown = (u32 *)g->al.get((size_t)c * 4);
   g->own_cap = c;
-  return (g->qown[0] && g->qown[1] && g->aown) ? SP_OK : SP_ENOMEM;
+  return (ok && g->aown) ? SP_OK : SP_ENOMEM;
 }
 
 void launch_ctl_reset(sp_graph *g, int full, int *launches) {
@@ -884,17 +845,12 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.flags = b.flags;
   a.itemv = b.itemv;
   a.item_pref = b.item_pref;
-  a.small_list = b.small_list;
-  a.medium_list = b.medium_list;
-  a.large_list = b.large_list;
-  a.large_cb = b.large_cb;
-  a.copy_list = b.copy_list;
-  a.copy_cb = b.copy_cb;
+  a.ment = b.ment;
+  a.mown = b.mown;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
   a.slack = g->slack;
-  a.scratch_cap = b.scratch_cap;
   a.n_items = (u32)ni;
   a.n = g->n;
   const unsigned grid = blocks_for(ni, kThreads, g->num_sms * 16);
@@ -916,23 +872,13 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.flags = b.flags;
   a.item_pref = b.item_pref;
   a.seg = b.seg;
+  a.ment = b.ment;
+  a.mown = b.mown;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
-  a.scratch = b.scratch;
   a.bits = g->bits;
-  a.list = b.small_list;
-  a.list_cb = nullptr;
-  k_merge_small<<<blocks_for(ni * 32, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(a);
-  a.list = b.medium_list;
-  k_merge_medium<<<(unsigned)std::max(1, g->num_sms * 2), kMedThreads, 0, g->stream>>>(a);
-  a.list = b.large_list;
-  a.list_cb = b.large_cb;
-  k_merge_large<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  a.list = b.copy_list;
-  a.list_cb = b.copy_cb;
-  k_merge_copy<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(
-      a, b.large_list);
-  *launches += 4;
+  k_merge<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
+  *launches += 1;
 }
 
 void launch_finish(sp_graph *g, int *launches) {

@@ -89,6 +89,7 @@ SIGNATURES = {
     "sp_export_csr_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "sp_graph_info_get": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
     "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
+    "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
     "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sp_version": (ctypes.c_char_p, []),
 }
@@ -301,6 +302,10 @@ class Graph:
         gi = GraphInfo()
         _check(load().sp_graph_info_get(self._h, ctypes.byref(gi)), "sp_graph_info_get")
         return gi
+
+    def set_delta(self, delta: int):
+        """Near-far bucket width of the push loop (0 = plain frontier rounds)."""
+        _check(load().sp_set_push_delta(self._h, int(delta)), "sp_set_push_delta")
 
     def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
         _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")

@@ -383,3 +383,44 @@ def test_merge_tiers_hub_rows():
             ro2, col2, _ = ref.csr()
             ro, col = ro2, col2
         assert g.info().pool_used_fwd > 0      # the hub row moved on the second batch
+
+
+@pytest.mark.parametrize("delta", [1, 300, 2500])
+def test_grid_near_far_matches_oracle(delta):
+    W = wl.grid(48, 48, batch_frac=0.03, seed=4)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        g.set_delta(delta)
+        g.sssp_init(W.source)
+        d = check_all(g, ref, W.source, store=False)
+        for k in range(4):
+            b = W.batch(k, dist=d)
+            g.apply(b)
+            ref.apply(b)
+            d = check_all(g, ref, W.source, store=False)
+
+
+@pytest.mark.parametrize("delta", [7, 60])
+def test_rmat_near_far_matches_oracle(delta):
+    W = wl.rmat(scale=12, batch_frac=0.02, seed=8)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        g.set_delta(delta)
+        g.sssp_init(W.source)
+        check_all(g, ref, W.source, store=False)
+        for k in range(4):
+            b = W.batch(k)
+            g.apply(b)
+            ref.apply(b)
+            check_all(g, ref, W.source, store=False)
+
+
+def test_near_far_static_equals_plain_and_does_less_work():
+    W = wl.grid(128, 128, seed=6)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        plain = g.sssp_init(W.source, stats=True)
+        d_plain = g.get_dist()
+        g.set_delta(1500)
+        nf = g.sssp_init(W.source, stats=True)
+        np.testing.assert_array_equal(g.get_dist(), d_plain)
+        assert nf.relaxed_edges < plain.relaxed_edges
