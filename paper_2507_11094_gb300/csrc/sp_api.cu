@@ -91,6 +91,15 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
       return SP_ENOMEM;
   }
+  // big-row strips: at most (old entries of touched rows) / 256 + one per row
+  const long long sneed = (2 * g->m) / 256 + ni + 64;
+  if (sneed > b.strips_cap) {
+    const long long c = std::max(sneed, 2 * b.strips_cap);
+    g->al.put(b.strips, (size_t)b.strips_cap * 8);
+    b.strips = (int2 *)g->al.get((size_t)c * 8);
+    b.strips_cap = b.strips ? c : 0;
+    if (!b.strips) return SP_ENOMEM;
+  }
   // merge chunk-owner table: elements = old entries of touched rows (<= 2m)
   // plus batch items
   const long long mneed = (2 * g->m + ni) / sp::kChunk + 64;
@@ -218,6 +227,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(b.seg, c * sizeof(sp::Seg));
   al.put(b.ment, c * 8);
   al.put(b.mown, (size_t)b.mown_cap * 4);
+  al.put(b.strips, (size_t)b.strips_cap * 8);
   al.put(b.tmp, b.tmp_bytes);
   c = b.cap_in;
   al.put(b.in_del_src, c * 4); al.put(b.in_del_dst, c * 4);

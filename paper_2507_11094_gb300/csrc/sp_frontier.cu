@@ -1106,7 +1106,7 @@ cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd
 
 void launch_pull(sp_graph *g, int *launches) {
   LoopArgs a = make_args(g);
-  k_pull<<<(unsigned)std::max(1, g->num_sms * 4), kLoopThreads, 0, g->stream>>>(a);
+  k_pull<<<(unsigned)std::max(1, g->num_sms), kLoopThreads, 0, g->stream>>>(a);   // one wave
   ++*launches;
 }
 
@@ -1120,7 +1120,7 @@ void launch_add(sp_graph *g, long long n_items, int *launches) {
   a.n_items = n_items;
   a.bits = g->bits;
   long long blocks = (n_items + kLoopThreads - 1) / kLoopThreads;
-  blocks = std::min<long long>(std::max<long long>(blocks, 1), g->num_sms * 8);
+  blocks = std::min<long long>(std::max<long long>(blocks, 1), g->num_sms);   // one wave
   k_add<<<(unsigned)blocks, kLoopThreads, 0, g->stream>>>(a);
   ++*launches;
 }

@@ -48,6 +48,8 @@ struct Seg {
   long long old_start;   // the row's active region before the merge
   long long dest;        // region the merged row is written to
   long long new_alt;     // the row's alternate region after the merge
+  unsigned long long prefix;     // key bits of (store, row)
+  unsigned long long base_pref;  // item_pref[first]
   int old_deg;
   int new_deg;
   int new_cap;
@@ -67,6 +69,8 @@ struct BatchBufs {
   int2 *ment = nullptr;             // merge queue: (segment, first element)
   u32 *mown = nullptr;              // merge chunk -> queue slot
   long long mown_cap = 0;
+  int2 *strips = nullptr;           // big-row strips: (segment, first entry)
+  long long strips_cap = 0;
   void *tmp = nullptr;
   size_t tmp_bytes = 0;
   long long cap_in = 0;             // staging for host inputs

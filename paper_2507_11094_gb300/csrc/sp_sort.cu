@@ -4,27 +4,32 @@
 // merged once (updateCSRDel / updateCSRAdd of the DynSSSP driver, done as a
 // sort-merge), and orders graph edges when a store is built.
 //
-// Per 8-bit digit: a histogram kernel (per-tile digit counts), a device-wide
-// scan of the digit-major count table, and a scatter kernel that ranks keys
-// stably inside the tile with warp match_any + per-warp digit counters.
+// Per 9-bit digit, three launches:
+//   k_hist       per-tile digit counts (count table is digit-major);
+//   k_digit_scan one block per digit: prefix of its counts over the tiles,
+//                and the digit's total;
+//   k_scatter    digit bases from the totals (block scan), then a stable
+//                in-tile rank with warp match_any + per-warp digit counters.
 #include "sp_internal.cuh"
 
 namespace sp {
 
 namespace {
 
-constexpr int kBits = 8;
+constexpr int kBits = 9;
 constexpr int kBins = 1 << kBits;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;
+constexpr int kItems = 4;
 constexpr int kTile = kThreads * kItems;
+constexpr int kBinsPerThread = kBins / kThreads;
 
 __global__ void __launch_bounds__(kThreads)
 k_hist(const u64 *__restrict__ keys, long long n, int shift, u32 *__restrict__ counts,
        u32 tiles) {
   __shared__ u32 h[kBins];
-  h[threadIdx.x] = 0;
+#pragma unroll
+  for (int j = 0; j < kBinsPerThread; ++j) h[threadIdx.x + j * kThreads] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * kTile;
   u32 d[kItems];
@@ -37,24 +42,71 @@ k_hist(const u64 *__restrict__ keys, long long n, int shift, u32 *__restrict__ c
   for (int k = 0; k < kItems; ++k)
     if (d[k] != 0xFFFFFFFFu) atomicAdd(&h[d[k]], 1u);
   __syncthreads();
-  counts[(long long)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+  for (int j = 0; j < kBinsPerThread; ++j) {
+    const int b = threadIdx.x + j * kThreads;
+    counts[(long long)b * tiles + blockIdx.x] = h[b];
+  }
+}
+
+__device__ __forceinline__ u32 warp_incl_scan(u32 x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ u32 block_excl_scan(u32 x, u32 *ws, u32 *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 incl = warp_incl_scan(x);
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    u32 v = lane < kWarps ? ws[lane] : 0u;
+    v = warp_incl_scan(v);
+    if (lane < kWarps) ws[lane] = v;
+  }
+  __syncthreads();
+  const u32 r = (warp ? ws[warp - 1] : 0u) + incl - x;
+  *total = ws[kWarps - 1];
+  __syncthreads();
+  return r;
+}
+
+// Block d: exclusive prefix of counts[d][0..tiles) in place, total to totals[d].
+__global__ void __launch_bounds__(kThreads)
+k_digit_scan(u32 *__restrict__ counts, u32 tiles, u32 *__restrict__ totals) {
+  __shared__ u32 ws[kWarps];
+  u32 *row = counts + (long long)blockIdx.x * tiles;
+  const u32 per = (tiles + kThreads - 1) / kThreads;
+  const u32 b = threadIdx.x * per < tiles ? threadIdx.x * per : tiles;
+  const u32 e = b + per < tiles ? b + per : tiles;
+  u32 sum = 0;
+  for (u32 i = b; i < e; ++i) sum += row[i];
+  u32 total;
+  u32 run = block_excl_scan(sum, ws, &total);
+  for (u32 i = b; i < e; ++i) {
+    const u32 x = row[i];
+    row[i] = run;
+    run += x;
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long n, int shift,
-          const u32 *__restrict__ offs, u32 tiles, u64 *__restrict__ keys_out,
-          u32 *__restrict__ vals_out) {
+          const u32 *__restrict__ offs, const u32 *__restrict__ totals, u32 tiles,
+          u64 *__restrict__ keys_out, u32 *__restrict__ vals_out) {
   __shared__ u32 s_off[kBins];
   __shared__ u32 s_run[kBins];
   __shared__ u32 s_cnt[2][kWarps][kBins];
+  __shared__ u32 ws[kWarps];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  s_off[t] = offs[(long long)t * tiles + blockIdx.x];
-  s_run[t] = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) s_cnt[0][w][t] = 0;
-  __syncthreads();
   const long long base = (long long)blockIdx.x * kTile;
-  const u32 lt = lanemask_lt();
   u64 rk[kItems];
   u32 rv[kItems];
 #pragma unroll
@@ -63,6 +115,31 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
     rk[k] = i < n ? keys[i] : 0ull;
     rv[k] = i < n ? vals[i] : 0u;
   }
+  // digit bases: exclusive scan of the digit totals (each thread owns
+  // kBinsPerThread consecutive digits)
+  {
+    u32 tot[kBinsPerThread], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      tot[j] = totals[t * kBinsPerThread + j];
+      sum += tot[j];
+    }
+    u32 all;
+    u32 run = block_excl_scan(sum, ws, &all);
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      const int dgt = t * kBinsPerThread + j;
+      s_off[dgt] = run + offs[(long long)dgt * tiles + blockIdx.x];
+      run += tot[j];
+      s_run[dgt] = 0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kBinsPerThread; ++j)
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_cnt[0][w][t + j * kThreads] = 0;
+  __syncthreads();
+  const u32 lt = lanemask_lt();
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     const int p = k & 1;
@@ -75,16 +152,18 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
     u32 rank = __popc(peers & lt);
     if (valid && rank == 0) s_cnt[p][warp][d] = __popc(peers);
     __syncthreads();
-    {  // thread t owns digit t: exclusive scan over warps, carry across k
-      u32 run = s_run[t];
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {   // digit-owners: scan over warps
+      const int dgt = t + j * kThreads;
+      u32 run = s_run[dgt];
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
-        u32 c = s_cnt[p][w][t];
-        s_cnt[p][w][t] = run;
+        u32 c = s_cnt[p][w][dgt];
+        s_cnt[p][w][dgt] = run;
         run += c;
-        s_cnt[p ^ 1][w][t] = 0;
+        s_cnt[p ^ 1][w][dgt] = 0;
       }
-      s_run[t] = run;
+      s_run[dgt] = run;
     }
     __syncthreads();
     if (valid) {
@@ -100,7 +179,7 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
 size_t sort_tmp_bytes(long long n) {
   long long tiles = (n + kTile - 1) / kTile;
   long long cnt = tiles * kBins;
-  return (size_t)(2 * cnt + 64) * sizeof(u32) + scan_tmp_bytes(cnt) + 256;
+  return (size_t)(cnt + kBins + 64) * sizeof(u32) + 256;
 }
 
 void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,
@@ -109,17 +188,16 @@ void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,
   const u32 tiles = (u32)((n + kTile - 1) / kTile);
   const long long cnt = (long long)tiles * kBins;
   u32 *counts = (u32 *)tmp;
-  u32 *offs = counts + cnt;
-  void *scan_tmp = (void *)(((uintptr_t)(offs + cnt) + 255) & ~(uintptr_t)255);
+  u32 *totals = counts + cnt;
   u64 *kin = keys, *kout = keys_alt;
   u32 *vin = vals, *vout = vals_alt;
   int passes = (key_bits + kBits - 1) / kBits;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass * kBits;
     k_hist<<<tiles, kThreads, 0, st>>>(kin, n, shift, counts, tiles);
-    scan_exclusive_u32(counts, offs, cnt, scan_tmp, st, launches);
-    k_scatter<<<tiles, kThreads, 0, st>>>(kin, vin, n, shift, offs, tiles, kout, vout);
-    if (launches) *launches += 2;
+    k_digit_scan<<<kBins, kThreads, 0, st>>>(counts, tiles, totals);
+    k_scatter<<<tiles, kThreads, 0, st>>>(kin, vin, n, shift, counts, totals, tiles, kout, vout);
+    if (launches) *launches += 3;
     u64 *tk = kin; kin = kout; kout = tk;
     u32 *tv = vin; vin = vout; vout = tv;
   }

@@ -207,6 +207,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->fmin0 = c->fmin1 = c->fmin2 = kInf;
   c->seed_min = kInf;
   c->mcnt = 0;
+  c->bstrips = 0;
   c->n_seg = 0;
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
@@ -323,12 +324,18 @@ struct CountArgs {
   const u64 *item_pref;
   int2 *ment;
   u32 *mown;
+  int2 *strips;
   Store st[2];
   int bits;
   float slack;
   u32 n_items;
   int n;
 };
+
+// Rows with at least kBigRow old entries are merged strip by strip
+// (k_merge_big); smaller ones element by element (k_merge).
+constexpr int kBigRow = 256;
+constexpr int kStrip = 256;
 
 // One thread per batch item: does this deletion / insertion apply?
 //  - a deletion applies if the edge is in the row and it is the first
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
     const u32 si = base + threadIdx.x;
     bool ok = si < nseg;
     Seg sg;
-    u32 tot = 0;
+    u32 tot = 0, nstr = 0;
     if (ok) {
       sg = a.seg[si];
       if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
@@ -425,6 +432,8 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
       sg.old_deg = rm.deg;
       sg.new_deg = new_deg;
       sg.pad = 0;
+      sg.prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
+      sg.base_pref = a.item_pref[sg.first];
       if (new_deg > rm.cap) {
         long long nc = row_capacity(new_deg, a.slack);
         const long long dbl = round_up4(2LL * rm.cap);
@@ -442,12 +451,23 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
         sg.new_cap = rm.cap;
       }
       a.seg[si] = sg;
-      tot = (u32)rm.deg + (sg.end - sg.first);
+      if (rm.deg >= kBigRow) nstr = (u32)((rm.deg + kStrip - 1) / kStrip);
+      else tot = (u32)rm.deg + (sg.end - sg.first);
       ++touched;
       slots += (u64)rm.deg + (u64)new_deg;
     }
-    // reserve merge elements: one packed atomic per block
-    const u32 cnt = ok ? 1u : 0u;
+    // reserve big-row strips: one atomic per block
+    {
+      u32 stot;
+      const u32 se = block_excl_scan_u32(nstr, scratch, &stot);
+      if (threadIdx.x == 0) scratch[35] = stot ? atomicAdd(&c->bstrips, stot) : 0u;
+      __syncthreads();
+      const u32 sb = scratch[35] + se;
+      __syncthreads();
+      for (u32 k = 0; k < nstr; ++k) a.strips[sb + k] = make_int2((int)si, (int)(k * kStrip));
+    }
+    // reserve merge elements of small rows: one packed atomic per block
+    const u32 cnt = (ok && tot > 0) ? 1u : 0u;
     u32 ctot, ttot;
     const u32 ce = block_excl_scan_u32(cnt, scratch, &ctot);
     const u32 te = block_excl_scan_u32(tot, scratch, &ttot);
@@ -459,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
     __syncthreads();
     const u32 bhi = scratch[32], blo = scratch[33];
     __syncthreads();
-    if (ok) {
+    if (cnt) {
       const u32 slot = bhi + ce, eb = blo + te;
       a.ment[slot] = make_int2((int)si, (int)eb);
       const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + tot - 1) / kChunk;
@@ -488,8 +508,11 @@ struct MergeArgs {
   const Seg *seg;
   const int2 *ment;
   const u32 *mown;
+  const int2 *strips;
+  const u32 *head, *head_scan;   // item -> segment
   Store st[2];
   int bits;
+  u32 n_items;
 };
 
 __device__ __forceinline__ bool merge_enabled(Ctl *c) {
@@ -557,8 +580,8 @@ __global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
       const Store &st = a.st[sg.dir];
       const int2 *old = st.adj + sg.old_start;
       int2 *dst = st.adj + sg.dest;
-      const u64 prefix = a.keys[sg.first] & kmask;
-      const u64 base_pref = a.item_pref[sg.first];
+      const u64 prefix = sg.prefix;
+      const u64 base_pref = sg.base_pref;
       const u32 eb = (u32)en0.y;
       const u32 tot = (u32)sg.old_deg + (sg.end - sg.first);
       const u32 r_end = eL < eb + tot ? eL : eb + tot;
@@ -589,6 +612,26 @@ __global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
           }
           ic = lo;
         }
+        // fast path: no batch item among this run's cols, so every entry
+        // keeps its order and moves by one shift
+        const u32 nl = jl - j0;
+        int lastc = en[0].x;
+#pragma unroll
+        for (int t = 1; t < kElemPerLane; ++t)
+          if (t < (int)nl) lastc = en[t].x;
+        const u64 knext = ic < sg.end ? a.keys[ic] : ~0ull;
+        if ((prefix | ((u64)(unsigned)lastc << 1)) < knext) {
+          const u64 pp = a.item_pref[ic] - base_pref;
+          const int shift = (int)(u32)(pp >> 32) - (int)(u32)pp;
+          const int p0 = (int)j0 + shift;
+          if (p0 >= 0 && p0 + (int)nl <= sg.new_deg) {
+#pragma unroll
+            for (int t = 0; t < kElemPerLane; ++t)
+              if (t < (int)nl) dst[p0 + t] = en[t];
+          } else {
+            bad = true;
+          }
+        } else
 #pragma unroll
         for (int t = 0; t < kElemPerLane; ++t) {
           if (j0 + t < jl) {
@@ -632,6 +675,131 @@ __global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
       e = r_end;
       slot_lo = slot + 1;
     }
+  }
+  if (bad) atomicExch(&c->bad, 1);
+}
+
+// Big rows: one warp per 256-entry strip of old entries.  The strip's col
+// range bounds the batch items that can fall inside it (two warp-uniform
+// searches); with none, every entry moves by one shift; otherwise each entry
+// finds its own item position inside that short range.  Loads and stores
+// are strided by 32 so a warp touches contiguous bytes.
+__global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
+  Ctl *c = a.ctl;
+  if (!merge_enabled(c)) return;
+  const int lane = threadIdx.x & 31;
+  const u32 nstrips = ld_cg_u32(&c->bstrips);
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+  for (u32 sidx = gw; sidx < nstrips; sidx += nw) {
+    const int2 sp = __ldcg(a.strips + sidx);
+    const Seg sg = a.seg[sp.x];
+    const Store &st = a.st[sg.dir];
+    const int2 *old = st.adj + sg.old_start;
+    int2 *dst = st.adj + sg.dest;
+    const int j0 = sp.y;
+    const int jl = j0 + kStrip < sg.old_deg ? j0 + kStrip : sg.old_deg;
+    if (j0 == 0 && lane == 0) {
+      RowMeta nm;
+      nm.start = sg.dest;
+      nm.deg = sg.new_deg;
+      nm.cap = sg.new_cap;
+      st.row[sg.row] = nm;
+      st.alt[sg.row] = sg.new_alt;
+    }
+    int2 en[kStrip / 32];
+#pragma unroll
+    for (int t = 0; t < kStrip / 32; ++t) {
+      const int j = j0 + lane + 32 * t;
+      en[t] = j < jl ? old[j] : make_int2(0x7fffffff, 0);
+    }
+    // items whose cols lie in [col(j0), col(jl-1)]
+    const u64 klo = sg.prefix | ((u64)(unsigned)old[j0].x << 1);
+    const u64 khi = sg.prefix | ((u64)(unsigned)old[jl - 1].x << 1) | 1ull;
+    u32 ilo = sg.first, ihi = sg.end;
+    {
+      u32 lo = sg.first, hi = sg.end;
+      while (lo < hi) {
+        const u32 mid = (lo + hi) >> 1;
+        if (a.keys[mid] < klo) lo = mid + 1; else hi = mid;
+      }
+      ilo = lo;
+      hi = sg.end;
+      while (lo < hi) {
+        const u32 mid = (lo + hi) >> 1;
+        if (a.keys[mid] <= khi) lo = mid + 1; else hi = mid;
+      }
+      ihi = lo;
+    }
+    const u64 p0 = a.item_pref[ilo] - sg.base_pref;
+    if (ilo == ihi) {
+      const int shift = (int)(u32)(p0 >> 32) - (int)(u32)p0;
+#pragma unroll
+      for (int t = 0; t < kStrip / 32; ++t) {
+        const int j = j0 + lane + 32 * t;
+        if (j < jl) {
+          const int pos = j + shift;
+          if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
+          else bad = true;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < kStrip / 32; ++t) {
+        const int j = j0 + lane + 32 * t;
+        if (j < jl) {
+          const u64 kc = sg.prefix | ((u64)(unsigned)en[t].x << 1);
+          u32 lo = ilo, hi = ihi;
+          while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            if (a.keys[mid] < kc) lo = mid + 1; else hi = mid;
+          }
+          const bool del = lo < sg.end && a.keys[lo] == kc && (a.flags[lo] & 1);
+          if (!del) {
+            const u64 pp = a.item_pref[lo] - sg.base_pref;
+            const int pos = j - (int)(u32)pp + (int)(u32)(pp >> 32);
+            if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
+            else bad = true;
+          }
+        }
+      }
+    }
+  }
+  if (bad) atomicExch(&c->bad, 1);
+}
+
+// Applied insertions of big rows, one thread per batch item.
+__global__ void __launch_bounds__(kThreads) k_merge_big_items(MergeArgs a) {
+  Ctl *c = a.ctl;
+  if (!merge_enabled(c)) return;
+  const u64 cmask = (1ull << a.bits) - 1;
+  bool bad = false;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_items;
+       i += gridDim.x * blockDim.x) {
+    const u64 key = a.keys[i];
+    if (!((key & 1) && (a.flags[i] & 1))) continue;
+    const Seg sg = a.seg[a.head_scan[i] + a.head[i] - 1];
+    if (sg.old_deg < kBigRow) continue;
+    const int col = (int)((key >> 1) & cmask);
+    const int2 *old = a.st[sg.dir].adj + sg.old_start;
+    int lo = 0, hi = sg.old_deg;   // old entries with col < this col
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (old[mid].x < col) lo = mid + 1; else hi = mid;
+    }
+    u32 l2 = sg.first, h2 = i;     // items with col < this col
+    const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
+    while (l2 < h2) {
+      const u32 mid = (l2 + h2) >> 1;
+      if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
+    }
+    const u64 q0 = a.item_pref[l2] - sg.base_pref, qi = a.item_pref[i] - sg.base_pref;
+    const int pos = lo - (int)(u32)q0 + (int)(u32)(qi >> 32);
+    if (pos >= 0 && pos < sg.new_deg)
+      a.st[sg.dir].adj[sg.dest + pos] = make_int2(col, (int)a.vals[i]);
+    else
+      bad = true;
   }
   if (bad) atomicExch(&c->bad, 1);
 }
@@ -847,6 +1015,7 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.item_pref = b.item_pref;
   a.ment = b.ment;
   a.mown = b.mown;
+  a.strips = b.strips;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
@@ -874,11 +1043,17 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.seg = b.seg;
   a.ment = b.ment;
   a.mown = b.mown;
+  a.strips = b.strips;
+  a.head = b.head;
+  a.head_scan = b.head_scan;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
+  a.n_items = (u32)ni;
   k_merge<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  *launches += 1;
+  k_merge_big<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
+  k_merge_big_items<<<blocks_for(ni, kThreads, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
+  *launches += 3;
 }
 
 void launch_finish(sp_graph *g, int *launches) {
