@@ -235,6 +235,64 @@ sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns);
  */
 sp_status sp_set_push_delta(sp_graph *g, int32_t delta);
 
+/*
+ * Multi-source form of sp_sssp_init: dist[v] is the shortest distance from
+ * the nearest of sources[0..k) (each source has dist 0 and parent -1).  On
+ * a graph made of k disjoint components with one source each -- the batched
+ * form, many independent graphs packed into one handle with offset vertex
+ * ids -- every component gets exactly its own single-source distances, and
+ * one batch call then repairs all of them in the same launches.  `sources`
+ * is host or device memory (sources_on_device).  SP_EINVAL if k < 1 or a
+ * source is out of range.
+ */
+sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
+                             int sources_on_device, sp_batch_stats *stats);
+
+/*
+ * Capturable batch path.  sp_reserve sizes every per-batch buffer for
+ * batches of up to max_updates deletions + insertions, so that
+ * sp_apply_batch_async never allocates.  sp_apply_batch_async enqueues the
+ * whole batch (same kernels and semantics as sp_apply_batch, device inputs
+ * only) on the graph's stream without any host synchronisation and copies a
+ * result record into `result` (device or pinned host memory,
+ * sp_async_result_bytes() bytes) at the end; it can therefore be recorded
+ * into a CUDA graph (sp_capture_apply) and replayed with new contents in the
+ * same input buffers.  After the stream work completes, sp_apply_batch_finish
+ * reads the record, updates the handle's host-side state (edge count,
+ * validity) and fills stats; it returns the batch's status.  A batch that
+ * would need a larger spare pool is not applied and finishes with
+ * SP_ENOMEM: apply it with sp_apply_batch, which grows the pool.
+ * Returns SP_ENOMEM from sp_apply_batch_async if the reservation is too
+ * small, SP_ESTATE without valid distances.
+ */
+sp_status sp_reserve(sp_graph *g, int64_t max_updates);
+size_t sp_async_result_bytes(void);
+sp_status sp_apply_batch_async(sp_graph *g,
+                               int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                               int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                               const int32_t *add_w, void *result);
+sp_status sp_apply_batch_finish(sp_graph *g, const void *result_host, sp_batch_stats *stats);
+
+/* A CUDA graph holding one recorded sp_apply_batch_async call. */
+typedef struct sp_exec sp_exec;
+
+/*
+ * Record sp_apply_batch_async(g, ...) into a CUDA graph (stream capture on
+ * the graph's stream) and instantiate it.  The pointers and counts are fixed
+ * in the recording: to apply another batch of the same sizes, write it into
+ * the same device buffers and call sp_exec_launch.
+ */
+sp_status sp_capture_apply(sp_graph *g,
+                           int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                           int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                           const int32_t *add_w, void *result, sp_exec **out);
+/* Launch a recorded batch on the graph's stream (asynchronous). */
+sp_status sp_exec_launch(sp_exec *e);
+/* Release a recording (NULL is accepted). */
+sp_status sp_exec_destroy(sp_exec *e);
+/* Wait for all work queued on the graph's stream. */
+sp_status sp_sync(sp_graph *g);
+
 /* Static name of a status code. */
 const char *sp_status_str(sp_status s);
 

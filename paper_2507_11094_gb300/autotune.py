@@ -1,0 +1,62 @@
+"""Schedule autotuner for the push fixedPoint.
+
+The knob is the near-far bucket width delta (sp_set_push_delta): 0 gives
+plain frontier rounds (few rounds, some redundant relaxations -- right for
+low-diameter graphs), a delta of a few edge weights gives ordered rounds
+(far fewer relaxations, more rounds -- right for high-diameter graphs).
+The tuner times a from-scratch solve on the handle for each candidate and
+keeps the fastest; results are cached per graph signature.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+_cache: dict = {}
+
+
+def signature(n: int, m: int, w) -> str:
+    w = np.asarray(w)
+    return f"n{n}-m{m}-wmax{int(w.max()) if w.size else 0}-wmean{int(w.mean()) if w.size else 0}"
+
+
+def candidates(w) -> list[int]:
+    w = np.asarray(w)
+    if w.size == 0:
+        return [0]
+    mean = max(1, int(w.mean()))
+    return sorted({0, mean, 2 * mean, 4 * mean, 16 * mean})
+
+
+def tune_delta(g, init, w, reps: int = 2, cache_file: str | None = None) -> dict:
+    """Pick delta for handle g.  init(g, stats=True) runs one from-scratch
+    solve (sssp_init or sssp_init_multi) and returns its BatchStats.
+    Returns {"delta": best, "ms": {delta: ms}}; g is left with the best
+    delta set and valid distances."""
+    sig = signature(g.n, g.m, w)
+    if cache_file and os.path.exists(cache_file):
+        with open(cache_file) as f:
+            _cache.update(json.load(f))
+    if sig in _cache:
+        g.set_delta(_cache[sig]["delta"])
+        init(g)
+        return _cache[sig]
+    timings = {}
+    for d in candidates(w):
+        g.set_delta(d)
+        best = None
+        for _ in range(reps):
+            st = init(g, stats=True)
+            best = st.ms_total if best is None else min(best, st.ms_total)
+        timings[d] = best
+    delta = min(timings, key=timings.get)
+    g.set_delta(delta)
+    init(g)
+    res = {"delta": int(delta), "ms": {str(k): float(v) for k, v in timings.items()}}
+    _cache[sig] = res
+    if cache_file:
+        with open(cache_file, "w") as f:
+            json.dump(_cache, f, indent=1)
+    return res

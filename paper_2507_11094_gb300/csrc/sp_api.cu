@@ -7,6 +7,7 @@
 // iteration, Section 5.3).
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "sp_graph.cuh"
 
@@ -193,7 +194,48 @@ sp_status status_of_repair(sp_graph *g, const Ctl &c) {
   return SP_OK;
 }
 
+// The kernel sequence of one batch (no host synchronisation).
+cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n_del,
+                          const int *as, const int *ad, const int *aw, long long n_add,
+                          bool timed, int *launches) {
+  const long long ni = 2 * (n_del + n_add);
+  sp::launch_ctl_reset(g, 0, launches);
+  sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, launches);
+  sp::launch_segments(g, ni, launches);
+  rec(g, timed, 1);
+  sp::launch_count(g, ni, launches);
+  rec(g, timed, 2);
+  sp::launch_merge(g, ni, launches);
+  rec(g, timed, 3);
+  cudaError_t e = cudaSuccess;
+  if (n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, launches);
+  rec(g, timed, 4);
+  if (n_del > 0) sp::launch_pull(g, launches);
+  rec(g, timed, 5);
+  sp::launch_add(g, ni, launches);
+  rec(g, timed, 6);
+  if (e == cudaSuccess) e = sp::launch_push(g, launches);
+  rec(g, timed, 7);
+  sp::launch_finish(g, launches);
+  rec(g, timed, 8);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+// Buffers big enough for an asynchronous batch of ni items?
+bool reserved_for(const sp_graph *g, long long ni) {
+  const sp::BatchBufs &b = g->bb;
+  return ni + 1 <= b.cap_items && (2 * g->m + ni) / sp::kChunk + 64 <= b.mown_cap &&
+         (2 * g->m) / 256 + ni + 64 <= b.strips_cap;
+}
+
 }  // namespace
+
+struct sp_exec {
+  sp_graph *g = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
 
 extern "C" {
 
@@ -469,26 +511,8 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   for (int attempt = 0;; ++attempt) {
     launches = 0;
     if (attempt) rec(g, timed, 0);
-    sp::launch_ctl_reset(g, 0, &launches);
-    sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
-    sp::launch_segments(g, ni, &launches);
-    rec(g, timed, 1);
-    sp::launch_count(g, ni, &launches);
-    rec(g, timed, 2);
-    sp::launch_merge(g, ni, &launches);
-    rec(g, timed, 3);
-    cudaError_t e = cudaSuccess;
-    if (n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, &launches);
-    rec(g, timed, 4);
-    if (n_del > 0) sp::launch_pull(g, &launches);
-    rec(g, timed, 5);
-    sp::launch_add(g, ni, &launches);
-    rec(g, timed, 6);
-    if (e == cudaSuccess) e = sp::launch_push(g, &launches);
-    rec(g, timed, 7);
-    sp::launch_finish(g, &launches);
-    rec(g, timed, 8);
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaError_t e = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &launches);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       cudaStreamSynchronize(g->stream);
       g->state = 2;
@@ -525,6 +549,149 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   g->m += (long long)c.add_applied - (long long)c.del_applied;
   fill_stats(g, c, stats, launches, regrows, ni, timed);
   return status_of_repair(g, c);
+}
+
+sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
+                             int sources_on_device, sp_batch_stats *stats) {
+  if (!g || !sources || k < 1) return SP_EINVAL;
+  std::vector<int32_t> hs((size_t)k);
+  if (sources_on_device) {
+    if (cudaMemcpy(hs.data(), sources, (size_t)k * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return SP_ECUDA;
+    }
+  } else {
+    std::copy(sources, sources + k, hs.begin());
+  }
+  for (int32_t v : hs)
+    if (v < 0 || v >= g->n) return SP_EINVAL;
+  int *src_d = (int *)g->al.get((size_t)k * 4);
+  if (!src_d) return SP_ENOMEM;
+  const bool timed = stats != nullptr;
+  int launches = 0;
+  for (int i = 0; i < SP_NPHASE; ++i) rec(g, timed, i);
+  cudaMemcpyAsync(src_d, hs.data(), (size_t)k * 4, cudaMemcpyHostToDevice, g->stream);
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_init_multi(g, src_d, k, &launches);
+  cudaError_t e = sp::launch_push(g, &launches);
+  rec(g, timed, SP_NPHASE - 1);
+  sp::launch_finish(g, &launches);
+  rec(g, timed, SP_NPHASE);
+  sp_status rc = read_ctl(g);
+  g->al.put(src_d, (size_t)k * 4);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g->state = 2;
+    return SP_ECUDA;
+  }
+  if (rc != SP_OK) {
+    g->state = 2;
+    return rc;
+  }
+  const Ctl &c = *g->ctl_host;
+  fill_stats(g, c, stats, launches, 0, 0, timed);
+  rc = status_of_repair(g, c);
+  g->source = hs[0];
+  if (rc == SP_OK) g->state = 1;
+  return rc;
+}
+
+sp_status sp_reserve(sp_graph *g, int64_t max_updates) {
+  if (!g || max_updates < 0 || max_updates > (1LL << 30)) return SP_EINVAL;
+  return ensure_batch_buffers(g, 2 * max_updates, 0);
+}
+
+size_t sp_async_result_bytes(void) { return sizeof(Ctl); }
+
+sp_status sp_apply_batch_async(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                               const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                               const int32_t *add_dst, const int32_t *add_w, void *result) {
+  if (!g || !result || n_del < 0 || n_add < 0) return SP_EINVAL;
+  if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
+    return SP_EINVAL;
+  if (g->state != 1) return SP_ESTATE;
+  const long long ni = 2 * (n_del + n_add);
+  if (!reserved_for(g, ni)) return SP_ENOMEM;
+  int launches = 0;
+  cudaError_t e = enqueue_batch(g, del_src, del_dst, n_del, add_src, add_dst, add_w, n_add,
+                                false, &launches);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(result, g->ctl, sizeof(Ctl), cudaMemcpyDefault, g->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  g->async_ni = ni;
+  g->async_launches = launches + 1;
+  return SP_OK;
+}
+
+sp_status sp_apply_batch_finish(sp_graph *g, const void *result_host, sp_batch_stats *stats) {
+  if (!g || !result_host) return SP_EINVAL;
+  const Ctl &c = *(const Ctl *)result_host;
+  if (c.status != 0) return (sp_status)c.status;   // nothing changed
+  if (c.need_grow) return SP_ENOMEM;               // nothing changed: use sp_apply_batch
+  g->m += (long long)c.add_applied - (long long)c.del_applied;
+  fill_stats(g, c, stats, g->async_launches, 0, g->async_ni, false);
+  return status_of_repair(g, c);
+}
+
+sp_status sp_capture_apply(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                           const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                           const int32_t *add_dst, const int32_t *add_w, void *result,
+                           sp_exec **out) {
+  if (!g || !out) return SP_EINVAL;
+  *out = nullptr;
+  if (!g->stream) return SP_EINVAL;   // the legacy default stream cannot be captured
+  if (g->state != 1) return SP_ESTATE;
+  if (!reserved_for(g, 2 * (n_del + n_add))) return SP_ENOMEM;
+  sp_exec *x = new (std::nothrow) sp_exec();
+  if (!x) return SP_ENOMEM;
+  x->g = g;
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    delete x;
+    return SP_ECUDA;
+  }
+  sp_status rc = sp_apply_batch_async(g, n_del, del_src, del_dst, n_add, add_src, add_dst,
+                                      add_w, result);
+  cudaError_t e = cudaStreamEndCapture(g->stream, &x->graph);
+  if (rc == SP_OK && e == cudaSuccess)
+    e = cudaGraphInstantiate(&x->exec, x->graph, 0);
+  if (rc != SP_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    if (x->graph) cudaGraphDestroy(x->graph);
+    delete x;
+    return rc != SP_OK ? rc : SP_ECUDA;
+  }
+  *out = x;
+  return SP_OK;
+}
+
+sp_status sp_exec_launch(sp_exec *x) {
+  if (!x || !x->exec) return SP_EINVAL;
+  if (cudaGraphLaunch(x->exec, x->g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  return SP_OK;
+}
+
+sp_status sp_exec_destroy(sp_exec *x) {
+  if (!x) return SP_OK;
+  if (x->exec) cudaGraphExecDestroy(x->exec);
+  if (x->graph) cudaGraphDestroy(x->graph);
+  delete x;
+  return SP_OK;
+}
+
+sp_status sp_sync(sp_graph *g) {
+  if (!g) return SP_EINVAL;
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  return SP_OK;
 }
 
 sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_device) {

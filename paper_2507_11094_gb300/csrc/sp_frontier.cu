@@ -1016,7 +1016,7 @@ __global__ void k_init(u64 *s, int n, int src, Ctl *c, u32 *qflag, int2 *qent, u
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x)
     s[v] = v == src ? pack(0, kNoParent) : kInfPack;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (src >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
     qflag[src] = c->epoch;
     const int d = row[src].deg;
     if (d > kSmallDeg) {
@@ -1029,6 +1029,30 @@ __global__ void k_init(u64 *s, int n, int src, Ctl *c, u32 *qflag, int2 *qent, u
     }
     c->seeds = 1;
     c->seed_min = 0;
+  }
+}
+
+// Multi-source init, second step (after every state is INF): each source
+// gets distance 0 and parent -1 and joins the first frontier once.
+__global__ void k_seed_sources(u64 *s, const int *src, int k, Ctl *c, u32 *qflag, int2 *qent,
+                               u32 *qown, u32 *qsv, const RowMeta *row) {
+  const Queue q0 = make_queue(qent, qown, &c->qcnt0, qsv, &c->scnt0);
+  const u32 tag = ld_cg_u32(&c->epoch);
+  u64 n_enq = 0;
+  for (int base = blockIdx.x * blockDim.x; base < k; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    bool want[K] = {};
+    u32 v[K] = {};
+    if (i < k) {
+      v[0] = (u32)src[i];
+      s[v[0]] = pack(0, kNoParent);
+      want[0] = atomicExch(qflag + v[0], tag) != tag;
+    }
+    enqueue(q0, row, v, want, 1, n_enq);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->seed_min = 0;
+    c->seeds = (u64)k;
   }
 }
 
@@ -1081,6 +1105,14 @@ int loop_blocks(int which, int num_sms) {
   return per_sm * num_sms;
 }
 
+void launch_init_multi(sp_graph *g, const int *src_d, int k, int *launches) {
+  k_init<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(
+      g->s, g->n, -1, g->ctl, g->qflag, g->qent[0], g->qown[0], g->qsv[0], g->fwd.row);
+  k_seed_sources<<<(unsigned)std::max(1, (k + 255) / 256), 256, 0, g->stream>>>(
+      g->s, src_d, k, g->ctl, g->qflag, g->qent[0], g->qown[0], g->qsv[0], g->fwd.row);
+  *launches += 2;
+}
+
 void launch_init(sp_graph *g, int source, int *launches) {
   k_init<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(
       g->s, g->n, source, g->ctl, g->qflag, g->qent[0], g->qown[0], g->qsv[0], g->fwd.row);
@@ -1088,12 +1120,20 @@ void launch_init(sp_graph *g, int source, int *launches) {
 }
 
 static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) {
-  int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
-  void *args[] = {&a};
-  const void *fn = op == kOpPush ? (const void *)k_loop<kOpPush> : (const void *)k_loop<kOpInval>;
+  const int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kLoopThreads);
+  cfg.dynamicSmemBytes = kLoopSmem;
+  cfg.stream = g->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   ++*launches;
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kLoopThreads), args, kLoopSmem,
-                                     g->stream);
+  return op == kOpPush ? cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a)
+                       : cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
 }
 
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches) {

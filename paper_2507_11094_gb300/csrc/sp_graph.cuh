@@ -136,6 +136,8 @@ struct sp_graph {
   long long wait_ns_user = 0;
   int loop_blocks_push = 0, loop_blocks_inval = 0;
   cudaEvent_t ev[SP_NPHASE + 1] = {};
+  long long async_ni = 0;       // items of the last enqueued async batch
+  int async_launches = 0;
 };
 
 namespace sp {
@@ -159,6 +161,7 @@ void launch_finish(sp_graph *g, int *launches);
 // sp_frontier.cu
 int loop_blocks(int which, int num_sms);
 void launch_init(sp_graph *g, int source, int *launches);
+void launch_init_multi(sp_graph *g, const int *src_d, int k, int *launches);
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd,
                          int *launches);
 void launch_pull(sp_graph *g, int *launches);

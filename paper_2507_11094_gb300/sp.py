@@ -90,6 +90,16 @@ SIGNATURES = {
     "sp_graph_info_get": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
     "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
     "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
+    "sp_sssp_init_multi": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P]),
+    "sp_reserve": (ctypes.c_int, [_P, _I64]),
+    "sp_async_result_bytes": (ctypes.c_size_t, []),
+    "sp_apply_batch_async": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P]),
+    "sp_apply_batch_finish": (ctypes.c_int, [_P, _P, _P]),
+    "sp_capture_apply": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "sp_exec_launch": (ctypes.c_int, [_P]),
+    "sp_exec_destroy": (ctypes.c_int, [_P]),
+    "sp_sync": (ctypes.c_int, [_P]),
     "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sp_version": (ctypes.c_char_p, []),
 }
@@ -249,6 +259,28 @@ class Graph:
         return self.apply_batch(batch.del_src, batch.del_dst, batch.add_src,
                                 batch.add_dst, batch.add_w, stats=stats)
 
+    def sssp_init_multi(self, sources, stats: bool = False):
+        """Distances from the nearest of several sources (batched form)."""
+        arr = _Arrays([sources], [np.int32])
+        k = int(arr.keep[0].numel() if arr.on_device else arr.keep[0].size)
+        st = BatchStats() if stats else None
+        rc = load().sp_sssp_init_multi(self._h, arr.ptrs[0], k, int(arr.on_device),
+                                       ctypes.byref(st) if st else None)
+        _check(rc, "sp_sssp_init_multi")
+        return st
+
+    def reserve(self, max_updates: int):
+        """Size per-batch buffers so apply_async never allocates."""
+        _check(load().sp_reserve(self._h, int(max_updates)), "sp_reserve")
+
+    def capture(self, del_src, del_dst, add_src, add_dst, add_w):
+        """Record one asynchronous batch (CUDA tensors, fixed addresses and
+        sizes) into a CUDA graph; returns an Exec to replay it."""
+        return Exec(self, del_src, del_dst, add_src, add_dst, add_w)
+
+    def sync(self):
+        _check(load().sp_sync(self._h), "sp_sync")
+
     def get_dist(self, parent: bool = False, out=None):
         """dist (and parent) as numpy arrays, or into CUDA tensors ``out``
         = (dist, parent_or_None)."""
@@ -309,6 +341,53 @@ class Graph:
 
     def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
         _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")
+
+
+class Exec:
+    """A captured batch: launch() replays it on the graph's stream; finish()
+    waits and reports the batch status and statistics."""
+
+    def __init__(self, g: Graph, del_src, del_dst, add_src, add_dst, add_w):
+        lib = load()
+        torch = _torch()
+        self.g = g
+        self.inputs = (del_src, del_dst, add_src, add_dst, add_w)
+        for t in self.inputs:
+            if not _is_cuda_tensor(t) or t.dtype != torch.int32 or not t.is_contiguous():
+                raise TypeError("capture needs contiguous int32 CUDA tensors")
+        self.nd, self.na = int(del_src.numel()), int(add_src.numel())
+        nbytes = int(lib.sp_async_result_bytes())
+        self.result = torch.zeros(nbytes, dtype=torch.uint8, pin_memory=True)
+        h = ctypes.c_void_p()
+        p = [ctypes.c_void_p(t.data_ptr()) for t in self.inputs]
+        rc = lib.sp_capture_apply(g._h, self.nd, p[0], p[1], self.na, p[2], p[3], p[4],
+                                  ctypes.c_void_p(self.result.data_ptr()), ctypes.byref(h))
+        _check(rc, "sp_capture_apply")
+        self._h = h
+
+    def launch(self):
+        _check(load().sp_exec_launch(self._h), "sp_exec_launch")
+
+    def finish(self, stats: bool = False, raise_on_error: bool = True):
+        self.g.sync()
+        st = BatchStats() if stats else None
+        rc = load().sp_apply_batch_finish(self.g._h, ctypes.c_void_p(self.result.data_ptr()),
+                                          ctypes.byref(st) if st else None)
+        if raise_on_error:
+            _check(rc, "sp_apply_batch_finish")
+            return st
+        return rc, st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sp_exec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def status_str(code: int) -> str:
