@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20",
-                    help="rmat20 | rmat<scale> | er1k | grid<side>-<pct> (e.g. grid4096-1)")
+                    help="rmat20 | rmat<scale> | er1k | grid<side>-<pct> (e.g. grid4096-1) "
+                         "| batched64 | serving")
     ap.add_argument("--batch-pct", type=float, default=None)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,6 +60,9 @@ def parse():
                     help="near-far bucket width of the push loop (default: 0 for R-MAT/ER, "
                          "1500 for grids)")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--serving-big-scale", type=int, default=22)
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -185,6 +189,22 @@ def oracle_sample(W, batches, budget_s: float, min_batches: int = 2):
 
 def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+def aggregate_ranks(distributed: bool, times, works):
+    """Whole-job figures of replicas: the max over ranks of each time and the
+    sum over ranks of each work count (a barrier on both sides)."""
+    if not distributed:
+        return [float(x) for x in times], [float(x) for x in works]
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(x) for x in works], dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return t.tolist(), u.tolist()
 
 
 def run_reference(args):
@@ -348,17 +368,8 @@ def run_gb300(args):
     bo = dist_host.nbytes
 
     # aggregate over ranks: max time, summed work
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([ups, sum(e2e_sizes)], dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ms_all, e2e_ms_all = float(t[0]), float(t[1])
-        ups_all, e2e_ups_all = float(u[0]), float(u[1])
-    else:
-        total_ms_all, e2e_ms_all = total_ms, sum(e2e_ms)
-        ups_all, e2e_ups_all = ups, sum(e2e_sizes)
+    (total_ms_all, e2e_ms_all), (ups_all, e2e_ups_all) = aggregate_ranks(
+        pg is not None, [total_ms, sum(e2e_ms)], [ups, sum(e2e_sizes)])
 
     # dominant kernel: the phase with the largest device time over the steps
     phases = list(sp.PHASES)
@@ -532,12 +543,148 @@ def run_batched(args):
     return 0
 
 
+def serving_workloads(seed: int, big_scale: int = 22):
+    """2 R-MAT graphs of scale big_scale + 6 of scale ~U{16..20}, edge factor
+    16, w~U[1,100], each with its own source (max out-degree vertex)."""
+    rng = np.random.default_rng(seed)
+    scales = [big_scale, big_scale] + [int(x) for x in rng.integers(16, 21, size=6)]
+    return [wl.rmat(scale=sc, batch_frac=0.001, seed=seed * 100 + 50 + i)
+            for i, sc in enumerate(scales)]
+
+
+def serving_requests(ws, count: int, seed: int):
+    """`count` batches: graph uniform over ws, size log-uniform in [1e3, 1e6]
+    (at most half the graph's edges), 50/50 deletions/insertions; a query of
+    1024 random vertices of the same graph after every 4th batch."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        gi = int(rng.integers(0, len(ws)))
+        W = ws[gi]
+        size = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        size = max(2, min(size, W.m // 2))
+        b = W.stream.next(size // 2, size - size // 2, seed=seed * 100000 + i)
+        q = (rng.integers(0, W.n, size=1024).astype(np.int32) if i % 4 == 3 else None)
+        reqs.append((gi, b, q))
+    return reqs
+
+
+def run_serving(args):
+    """C5: the serving runtime over 8 graphs under an HBM budget that fits
+    about 5 of them.  Sustained edge-updates/s with every request submitted
+    at once, then Poisson arrivals at 0.5x and 0.9x of it with
+    arrival-to-completion p50/p99."""
+    import torch
+
+    from paper_2507_11094_gb300 import sp
+    torch.cuda.set_device(0)
+    sp.load(build_if_missing=True)
+    t_gen = time.perf_counter()
+    ws = serving_workloads(args.seed, args.serving_big_scale)
+    n_req = args.serving_requests
+    phases = {name: serving_requests(ws, n_req // 3 if name == "warm" else n_req,
+                                     args.seed * 10 + j)
+              for j, name in enumerate(("warm", "sustained", "rate0.5", "rate0.9"))}
+    t_gen = time.perf_counter() - t_gen
+
+    # footprint of each graph after a large batch, measured alone
+    sizes = []
+    with sp.Server(hbm_budget_bytes=200 << 30, n_slots=1, delta=0) as probe:
+        for W in ws:
+            before = probe.stats().resident_bytes
+            gid = probe.add_graph(W.n, W.row_off, W.col, W.w, W.source)
+            probe.wait(probe.submit_query(gid, np.arange(4)))
+            sizes.append(probe.stats().resident_bytes - before)
+    batch_buf = 160 << 20          # batch buffers of a 1e6-update batch
+    budget = int(sum(sorted(sizes)[-5:]) + 5 * batch_buf)
+
+    srv = sp.Server(hbm_budget_bytes=budget, n_slots=args.serving_slots, delta=0)
+    gids = [srv.add_graph(W.n, W.row_off, W.col, W.w, W.source) for W in ws]
+
+    def submit_all(reqs, rate=None, rng=None):
+        out = []
+        t0 = time.perf_counter()
+        t_next = 0.0
+        for gi, b, q in reqs:
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                dt = t0 + t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            out.append((srv.submit(gids[gi], b), b.size))
+            if q is not None:
+                out.append((srv.submit_query(gids[gi], q), 0))
+        return out
+
+    def collect(ids):
+        infos = []
+        for rid, size in ids:
+            info, _ = srv.wait(rid)
+            if info.status != sp.SP_OK:
+                raise SystemExit(f"request failed: {sp.STATUS.get(info.status)}")
+            infos.append((info.as_dict(), size))
+        return infos
+
+    collect(submit_all(phases["warm"]))
+    st0 = srv.stats().as_dict()
+    t0 = time.perf_counter()
+    sus = collect(submit_all(phases["sustained"]))
+    t_sus = time.perf_counter() - t0
+    ups = sum(sz for _, sz in sus)
+    sustained = ups / t_sus
+    st1 = srv.stats().as_dict()
+    mean_batch = ups / n_req
+    runs = {}
+    for name, frac in (("rate0.5", 0.5), ("rate0.9", 0.9)):
+        rate = frac * sustained / mean_batch           # batches per second
+        t0 = time.perf_counter()
+        res = collect(submit_all(phases[name], rate, np.random.default_rng(args.seed + 7)))
+        dt = time.perf_counter() - t0
+        lat = [i["done_ms"] - i["submit_ms"] for i, sz in res if i["kind"] == 0]
+        svc = [i["done_ms"] - i["start_ms"] for i, sz in res if i["kind"] == 0]
+        qlat = [i["done_ms"] - i["submit_ms"] for i, sz in res if i["kind"] == 1]
+        runs[name] = {"offered_batches_per_s": rate,
+                      "achieved_updates_per_s": sum(sz for _, sz in res) / dt,
+                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                      "service_p50_ms": percentile(svc, 50),
+                      "service_p99_ms": percentile(svc, 99),
+                      "query_p50_ms": percentile(qlat, 50) if qlat else None,
+                      "query_p99_ms": percentile(qlat, 99) if qlat else None,
+                      "loads": sum(i["loaded"] for i, _ in res)}
+    st2 = srv.stats().as_dict()
+    srv.close()
+    line = {
+        "metric": METRIC + " [serving form]", "value": sustained, "unit": "edge_updates/s",
+        "n_gpus": 1, "steps": n_req, "warmup": n_req // 3, "ms_per_step": 1e3 * t_sus / n_req,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": f"serving-2xrmat{args.serving_big_scale}+6xrmat16..20",
+                   "graphs": [{"n": W.n, "m": W.m} for W in ws],
+                   "device_bytes": sizes, "hbm_budget_bytes": budget,
+                   "slots": args.serving_slots, "requests_per_phase": n_req,
+                   "inputs": "host arrays copied by the server (H2D inside every request)"},
+        "sustained": {"updates_per_s": sustained, "seconds": t_sus,
+                      "loads": st1["loads"] - st0["loads"],
+                      "evictions": st1["evictions"] - st0["evictions"]},
+        "rates": runs,
+        "server_stats": st2,
+        "generation_s": t_gen,
+    }
+    print(json.dumps(line), flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            json.dump(line, f, indent=1)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gb300(args)
 
 

@@ -293,6 +293,87 @@ sp_status sp_exec_destroy(sp_exec *e);
 /* Wait for all work queued on the graph's stream. */
 sp_status sp_sync(sp_graph *g);
 
+/*
+ * Distances of k chosen vertices: dist_out[i] = dist[vertices[i]] (SP_INF if
+ * unreachable).  Both arrays are host or device memory (on_device).  One
+ * gather kernel; the call returns when the values are in dist_out.
+ */
+sp_status sp_query(sp_graph *g, int32_t k, const int32_t *vertices, int32_t *dist_out,
+                   int on_device);
+
+/*
+ * Blocks of the persistent repair loops (one per SM at most; 0 = one per
+ * SM).  A server running several graphs at once gives each a share of the
+ * SMs so their loops can be resident together.
+ */
+sp_status sp_set_loop_blocks(sp_graph *g, int32_t blocks);
+
+/* ------------------------------------------------------------------------
+ * Serving runtime: a request loop over several resident graphs.
+ *
+ * Update batches and distance queries are submitted per graph and answered
+ * asynchronously.  Requests of one graph run in submission order; requests
+ * of different graphs run concurrently on n_slots worker slots (one CUDA
+ * stream each), so their work overlaps on the device and a request that
+ * arrives while others are running starts as soon as a slot is free
+ * (continuous batching).  Graphs are admitted by an HBM budget: when a
+ * request needs a graph that is not resident, idle resident graphs are
+ * evicted least-recently-used (their edge set is checkpointed to host
+ * memory) until the graph fits, and the graph is rebuilt from its checkpoint
+ * with distances recomputed from its source.  Distances are unique, so a
+ * query's answer does not depend on the mix it ran in.
+ * ---------------------------------------------------------------------- */
+typedef struct sp_server sp_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device bytes all resident graphs may hold  */
+    int32_t n_slots;           /* requests in flight on the GPU at once      */
+    int32_t loop_blocks;       /* persistent-loop blocks per graph (0: SMs/n_slots) */
+    float slack;               /* per-row slack of every graph               */
+    int32_t delta;             /* near-far width of every graph (0 = off)    */
+} sp_server_config;
+
+typedef struct {
+    int32_t status;            /* sp_status of the request                   */
+    int32_t kind;              /* 0 = batch, 1 = query                       */
+    int32_t graph;
+    int32_t slot;
+    int64_t updates;           /* deletions + insertions of a batch          */
+    double submit_ms, start_ms, done_ms;   /* server clock                   */
+    int32_t loaded;            /* 1 if the graph was (re)loaded for it       */
+} sp_request_info;
+
+typedef struct {
+    int64_t resident_bytes, max_resident_bytes;
+    int64_t loads, evictions, batches, queries, updates;
+    int32_t resident_graphs, registered_graphs;
+} sp_server_stats;
+
+sp_status sp_server_create(const sp_server_config *cfg, sp_server **out);
+sp_status sp_server_destroy(sp_server *s);
+/* Register a graph (host CSR, copied) with its source; it is loaded on
+ * demand.  SP_ENOMEM_BUDGET if it alone would not fit the budget. */
+sp_status sp_server_add_graph(sp_server *s, int32_t n, int64_t m, const int64_t *row_off,
+                              const int32_t *col, const int32_t *w, int32_t source,
+                              int32_t *graph_id);
+/* Submit a batch (host arrays, copied); *request_id identifies it. */
+sp_status sp_server_submit_batch(sp_server *s, int32_t graph_id,
+                                 int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                                 int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                                 const int32_t *add_w, int64_t *request_id);
+/* Submit a query for k vertices (host array, copied). */
+sp_status sp_server_submit_query(sp_server *s, int32_t graph_id, int32_t k,
+                                 const int32_t *vertices, int64_t *request_id);
+/* Wait up to timeout_ms (< 0: no limit) for a request; fills *info and, for
+ * a query, dist_out[k].  SP_ETIMEOUT if it is not done in time. */
+sp_status sp_server_wait(sp_server *s, int64_t request_id, sp_request_info *info,
+                         int32_t *dist_out, int32_t timeout_ms);
+/* Wait for every submitted request. */
+sp_status sp_server_drain(sp_server *s);
+sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out);
+/* Current distances of a graph (loads it if needed), host array of n. */
+sp_status sp_server_get_dist(sp_server *s, int32_t graph_id, int32_t *dist);
+
 /* Static name of a status code. */
 const char *sp_status_str(sp_status s);
 

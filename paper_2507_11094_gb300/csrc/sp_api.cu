@@ -685,6 +685,40 @@ sp_status sp_exec_destroy(sp_exec *x) {
   return SP_OK;
 }
 
+sp_status sp_query(sp_graph *g, int32_t k, const int32_t *vertices, int32_t *dist_out,
+                   int on_device) {
+  if (!g || k < 0 || (k > 0 && (!vertices || !dist_out))) return SP_EINVAL;
+  if (g->state != 1) return SP_ESTATE;
+  if (k == 0) return SP_OK;
+  int launches = 0;
+  const int *vs = vertices;
+  int *out = dist_out;
+  void *buf = nullptr;
+  const size_t bytes = (size_t)k * 8 + 256;
+  if (!on_device) {
+    buf = g->al.get(bytes);
+    if (!buf) return SP_ENOMEM;
+    int *vd = (int *)buf;
+    out = vd + k;
+    cudaMemcpyAsync(vd, vertices, (size_t)k * 4, cudaMemcpyHostToDevice, g->stream);
+    vs = vd;
+  }
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_gather(g, vs, k, out, &launches);
+  if (!on_device)
+    cudaMemcpyAsync(dist_out, out, (size_t)k * 4, cudaMemcpyDeviceToHost, g->stream);
+  sp_status rc = read_ctl(g);
+  if (buf) g->al.put(buf, bytes);
+  if (rc != SP_OK) return rc;
+  return g->ctl_host->status != 0 ? (sp_status)g->ctl_host->status : SP_OK;
+}
+
+sp_status sp_set_loop_blocks(sp_graph *g, int32_t blocks) {
+  if (!g || blocks < 0) return SP_EINVAL;
+  g->loop_blocks_user = blocks;
+  return SP_OK;
+}
+
 sp_status sp_sync(sp_graph *g) {
   if (!g) return SP_EINVAL;
   if (cudaStreamSynchronize(g->stream) != cudaSuccess) {

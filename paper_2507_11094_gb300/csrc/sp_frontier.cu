@@ -1056,6 +1056,15 @@ __global__ void k_seed_sources(u64 *s, const int *src, int k, Ctl *c, u32 *qflag
   }
 }
 
+__global__ void k_gather_dist(const u64 *__restrict__ s, int n, const int *__restrict__ vs, int k,
+                              int *out, Ctl *c) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const int v = vs[i];
+    if (v >= 0 && v < n) out[i] = (int)dist_of(s[v]);
+    else atomicCAS(&c->status, 0, SP_EINVAL);
+  }
+}
+
 __global__ void k_unpack(const u64 *__restrict__ s, int n, int *dist, int *parent) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
@@ -1120,7 +1129,8 @@ void launch_init(sp_graph *g, int source, int *launches) {
 }
 
 static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) {
-  const int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
+  int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
+  if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kLoopThreads);
@@ -1168,6 +1178,12 @@ void launch_add(sp_graph *g, long long n_items, int *launches) {
 cudaError_t launch_push(sp_graph *g, int *launches) {
   LoopArgs a = make_args(g);
   return launch_loop(g, kOpPush, a, launches);
+}
+
+void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches) {
+  k_gather_dist<<<(unsigned)std::max(1, std::min(g->num_sms * 4, (k + 255) / 256)), 256, 0,
+                  g->stream>>>(g->s, g->n, vs_d, k, out_d, g->ctl);
+  ++*launches;
 }
 
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches) {

@@ -135,6 +135,7 @@ struct sp_graph {
   int32_t max_rounds_user = 0;
   long long wait_ns_user = 0;
   int loop_blocks_push = 0, loop_blocks_inval = 0;
+  int loop_blocks_user = 0;
   cudaEvent_t ev[SP_NPHASE + 1] = {};
   long long async_ni = 0;       // items of the last enqueued async batch
   int async_launches = 0;
@@ -168,5 +169,6 @@ void launch_pull(sp_graph *g, int *launches);
 void launch_add(sp_graph *g, long long n_items, int *launches);
 cudaError_t launch_push(sp_graph *g, int *launches);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches);
 
 }  // namespace sp

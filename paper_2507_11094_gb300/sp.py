@@ -71,6 +71,34 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size
                            ctypes.c_void_p)
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("loop_blocks", ctypes.c_int32), ("slack", ctypes.c_float),
+                ("delta", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("graph", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("updates", ctypes.c_int64), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("loaded", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("resident_bytes", ctypes.c_int64), ("max_resident_bytes", ctypes.c_int64),
+                ("loads", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("queries", ctypes.c_int64),
+                ("updates", ctypes.c_int64), ("resident_graphs", ctypes.c_int32),
+                ("registered_graphs", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Allocator(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
 
@@ -100,6 +128,20 @@ SIGNATURES = {
     "sp_exec_launch": (ctypes.c_int, [_P]),
     "sp_exec_destroy": (ctypes.c_int, [_P]),
     "sp_sync": (ctypes.c_int, [_P]),
+    "sp_query": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_int]),
+    "sp_set_loop_blocks": (ctypes.c_int, [_P, _I32]),
+    "sp_server_create": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
+    "sp_server_destroy": (ctypes.c_int, [_P]),
+    "sp_server_add_graph": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _I32,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "sp_server_submit_batch": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _I64, _P, _P, _P,
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    "sp_server_submit_query": (ctypes.c_int, [_P, _I32, _I32, _P,
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    "sp_server_wait": (ctypes.c_int, [_P, _I64, _P, _P, _I32]),
+    "sp_server_drain": (ctypes.c_int, [_P]),
+    "sp_server_stats_get": (ctypes.c_int, [_P, _P]),
+    "sp_server_get_dist": (ctypes.c_int, [_P, _I32, _P]),
     "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sp_version": (ctypes.c_char_p, []),
 }
@@ -281,6 +323,18 @@ class Graph:
     def sync(self):
         _check(load().sp_sync(self._h), "sp_sync")
 
+    def query(self, vertices):
+        """Distances of the given vertices (numpy in, numpy out)."""
+        v = np.ascontiguousarray(vertices, dtype=np.int32)
+        out = np.empty(v.size, dtype=np.int32)
+        rc = load().sp_query(self._h, v.size, v.ctypes.data_as(ctypes.c_void_p),
+                             out.ctypes.data_as(ctypes.c_void_p), 0)
+        _check(rc, "sp_query")
+        return out
+
+    def set_loop_blocks(self, blocks: int):
+        _check(load().sp_set_loop_blocks(self._h, int(blocks)), "sp_set_loop_blocks")
+
     def get_dist(self, parent: bool = False, out=None):
         """dist (and parent) as numpy arrays, or into CUDA tensors ``out``
         = (dist, parent_or_None)."""
@@ -388,6 +442,107 @@ class Exec:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Serving runtime (sp_server_*): many graphs, requests submitted
+    asynchronously and run by worker slots, graphs admitted under an HBM
+    budget with least-recently-used eviction.  All arrays are host (numpy)."""
+
+    def __init__(self, hbm_budget_bytes: int, n_slots: int = 2, loop_blocks: int = 0,
+                 slack: float = 0.25, delta: int = 0):
+        _torch()
+        cfg = ServerConfig(int(hbm_budget_bytes), int(n_slots), int(loop_blocks),
+                           float(slack), int(delta))
+        h = ctypes.c_void_p()
+        _check(load().sp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sp_server_create")
+        self._h = h
+        self._n = {}
+        self._k = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_graph(self, n, row_off, col, w, source: int) -> int:
+        ro = np.ascontiguousarray(row_off, dtype=np.int64)
+        c = np.ascontiguousarray(col, dtype=np.int32)
+        ww = np.ascontiguousarray(w, dtype=np.int32)
+        gid = ctypes.c_int32()
+        rc = load().sp_server_add_graph(self._h, int(n), int(c.size),
+                                        ro.ctypes.data_as(ctypes.c_void_p),
+                                        c.ctypes.data_as(ctypes.c_void_p),
+                                        ww.ctypes.data_as(ctypes.c_void_p), int(source),
+                                        ctypes.byref(gid))
+        _check(rc, "sp_server_add_graph")
+        self._n[gid.value] = int(n)
+        return gid.value
+
+    def submit_batch(self, graph: int, del_src, del_dst, add_src, add_dst, add_w) -> int:
+        a = [np.ascontiguousarray(x, dtype=np.int32)
+             for x in (del_src, del_dst, add_src, add_dst, add_w)]
+        if a[0].size != a[1].size or not (a[2].size == a[3].size == a[4].size):
+            raise SpError(SP_EINVAL, "batch array sizes")
+        p = [x.ctypes.data_as(ctypes.c_void_p) for x in a]
+        rid = ctypes.c_int64()
+        rc = load().sp_server_submit_batch(self._h, int(graph), a[0].size, p[0], p[1],
+                                           a[2].size, p[2], p[3], p[4], ctypes.byref(rid))
+        _check(rc, "sp_server_submit_batch")
+        return rid.value
+
+    def submit(self, graph: int, batch) -> int:
+        """Submit a ``workloads.Batch``."""
+        return self.submit_batch(graph, batch.del_src, batch.del_dst, batch.add_src,
+                                 batch.add_dst, batch.add_w)
+
+    def submit_query(self, graph: int, vertices) -> int:
+        v = np.ascontiguousarray(vertices, dtype=np.int32)
+        rid = ctypes.c_int64()
+        rc = load().sp_server_submit_query(self._h, int(graph), v.size,
+                                           v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid))
+        _check(rc, "sp_server_submit_query")
+        self._k[rid.value] = v.size
+        return rid.value
+
+    def wait(self, request_id: int, timeout_ms: int = -1):
+        """(RequestInfo, distances or None); raises on a failed request."""
+        info = RequestInfo()
+        k = self._k.pop(request_id, None)
+        out = np.empty(k, dtype=np.int32) if k is not None else None
+        rc = load().sp_server_wait(self._h, int(request_id), ctypes.byref(info),
+                                   out.ctypes.data_as(ctypes.c_void_p) if k else None,
+                                   int(timeout_ms))
+        if rc != SP_OK and k is not None:
+            self._k[request_id] = k
+        _check(rc, "sp_server_wait")
+        return info, out
+
+    def drain(self):
+        _check(load().sp_server_drain(self._h), "sp_server_drain")
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(load().sp_server_stats_get(self._h, ctypes.byref(st)), "sp_server_stats_get")
+        return st
+
+    def get_dist(self, graph: int):
+        d = np.empty(self._n[graph], dtype=np.int32)
+        rc = load().sp_server_get_dist(self._h, int(graph), d.ctypes.data_as(ctypes.c_void_p))
+        _check(rc, "sp_server_get_dist")
+        return d
 
 
 def status_str(code: int) -> str:

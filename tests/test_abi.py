@@ -62,6 +62,15 @@ def test_argument_checks_need_no_device(lib):
     assert lib.sp_graph_destroy(None) == 0
     assert lib.sp_sssp_init(None, 0, None) == -1
     assert lib.sp_apply_batch(None, 0, None, None, 0, None, None, None, 0, None) == -1
+    from paper_2507_11094_gb300 import sp
+    srv = ctypes.c_void_p()
+    assert lib.sp_server_create(None, ctypes.byref(srv)) == -1
+    bad = sp.ServerConfig(1 << 30, 0, 0, 0.25, 0)           # no worker slots
+    assert lib.sp_server_create(ctypes.byref(bad), ctypes.byref(srv)) == -1
+    bad = sp.ServerConfig(0, 2, 0, 0.25, 0)                 # no budget
+    assert lib.sp_server_create(ctypes.byref(bad), ctypes.byref(srv)) == -1
+    assert lib.sp_server_destroy(None) == 0
+    assert lib.sp_server_drain(None) == -1
 
 
 def test_stats_struct_layout_matches_header():
@@ -78,3 +87,33 @@ def test_product_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof/offsetof of every struct of the header, as gcc lays them out,
+    equal the ctypes mirrors."""
+    from paper_2507_11094_gb300 import sp
+    mirrors = {"sp_batch_stats": sp.BatchStats, "sp_graph_info": sp.GraphInfo,
+               "sp_server_config": sp.ServerConfig, "sp_request_info": sp.RequestInfo,
+               "sp_server_stats": sp.ServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sp.h"',
+             "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
