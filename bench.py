@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--delta", type=int, default=None,
                     help="near-far bucket width of the push loop (default: 0 for R-MAT/ER, "
                          "1500 for grids)")
+    ap.add_argument("--inval-switch", type=int, default=None,
+                    help="frontier rounds of the invalidation before pointer jumping "
+                         "(-1 never; default: the library's)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--serving-big-scale", type=int, default=22)
     ap.add_argument("--serving-requests", type=int, default=48)
@@ -270,6 +273,9 @@ def run_gb300(args):
     delta = args.delta if args.delta is not None else (1500 if W.name.startswith("grid") else 0)
     g.set_delta(delta)
     cfg["delta"] = delta
+    if args.inval_switch is not None:
+        g.set_inval_switch(args.inval_switch)
+        cfg["inval_switch"] = args.inval_switch
     g.sssp_init(W.source)
 
     tree = W.tree_fraction > 0

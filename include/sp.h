@@ -236,6 +236,21 @@ sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns);
 sp_status sp_set_push_delta(sp_graph *g, int32_t delta);
 
 /*
+ * Decremental invalidation strategy (the subtree walk that follows OnDelete,
+ * Section 3.2).  The walk first runs frontier rounds down the
+ * shortest-path tree, one tree level per round.  After `rounds` rounds with
+ * vertices still to visit it switches to pointer jumping over all vertices:
+ * every vertex follows its ancestors, doubling the distance per pass, until
+ * it meets a cut ancestor or the root, so the remaining levels cost
+ * log2(depth) passes instead of one round each.  Both strategies invalidate
+ * exactly the descendants of the cut vertices.  rounds < 0: never switch;
+ * 0 (the default): jump right after OnDelete.  A pass costs about one
+ * frontier round on a graph of a few million vertices, so frontier rounds
+ * pay only for shallow cuts on much larger graphs.
+ */
+sp_status sp_set_inval_switch(sp_graph *g, int32_t rounds);
+
+/*
  * Multi-source form of sp_sssp_init: dist[v] is the shortest distance from
  * the nearest of sources[0..k) (each source has dist 0 and parent -1).  On
  * a graph made of k disjoint components with one source each -- the batched

@@ -176,6 +176,7 @@ void set_limits(sp_graph *g) {
                                              : (u32)std::min<long long>(cap, 0x7fffffffLL);
   g->lim.wait_ns = g->wait_ns_user > 0 ? (u64)g->wait_ns_user : 2000000000ull;
   g->lim.delta = (u32)std::max(0, g->delta_user);
+  g->lim.jump_round = g->jump_round_user;
 }
 
 sp_status status_of_repair(sp_graph *g, const Ctl &c) {
@@ -291,7 +292,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   }
   al.put(g->aent, n * 8);
   al.put(g->ftag, n * 4);
-  al.put(g->xdone, n * 8);
+  al.put(g->jmp, n * 4);
   al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
   al.put(g->ctl, sizeof(Ctl));
@@ -364,10 +365,10 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   bufs_ok = bufs_ok && g->asv;
   g->aent = (int2 *)g->al.get(nn * 8);
   g->ftag = (u32 *)g->al.get(nn * 4);
-  g->xdone = (u64 *)g->al.get(nn * 8);
+  g->jmp = (u32 *)g->al.get(nn * 4);
   g->out_dist = (int *)g->al.get(nn * 4);
   g->out_parent = (int *)g->al.get(nn * 4);
-  if (!g->ctl || !g->s || !g->qflag || !bufs_ok || !g->aent || !g->ftag || !g->xdone ||
+  if (!g->ctl || !g->s || !g->qflag || !bufs_ok || !g->aent || !g->ftag || !g->jmp ||
       !g->out_dist || !g->out_parent) {
     sp_graph_destroy(g);
     return SP_ENOMEM;
@@ -375,7 +376,6 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream);
   cudaMemsetAsync(g->qflag, 0, nn * 4, g->stream);
   cudaMemsetAsync(g->ftag, 0, nn * 4, g->stream);
-  cudaMemsetAsync(g->xdone, 0, nn * 8, g->stream);
   int launches = 0;
   sp::launch_ctl_reset(g, 1, &launches);
 
@@ -431,6 +431,13 @@ sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns) {
 sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
   if (!g || delta < 0) return SP_EINVAL;
   g->delta_user = delta;
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_set_inval_switch(sp_graph *g, int32_t rounds) {
+  if (!g) return SP_EINVAL;
+  g->jump_round_user = rounds < 0 ? -1 : rounds;
   set_limits(g);
   return SP_OK;
 }

@@ -108,7 +108,15 @@ __device__ __forceinline__ u32 *fcnt_ptr(Ctl *c, u32 b) {
 __device__ __forceinline__ u32 *fmin_ptr(Ctl *c, u32 b) {
   return b == 0 ? &c->fmin0 : (b == 1 ? &c->fmin1 : &c->fmin2);
 }
+__device__ __forceinline__ u32 *jcnt_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->jcnt0 : (b == 1 ? &c->jcnt1 : &c->jcnt2);
+}
 __device__ __forceinline__ u32 next3(u32 b) { return b == 2 ? 0u : b + 1u; }
+
+// Pointer-jumping words: an ancestor id (< n), or one of two final states.
+constexpr u32 kJumpCut = 0xFFFFFFFFu;    // a cut vertex lies on the path
+constexpr u32 kJumpRoot = 0xFFFFFFFEu;   // the path reached the root uncut
+constexpr u32 kMaxJumps = 40;            // > log2 of any tree depth
 
 __device__ __forceinline__ u32 sat_add(u32 a, u32 b) {
   const u64 x = (u64)a + b;
@@ -691,6 +699,76 @@ __device__ __forceinline__ void process_small(Op &op, const u32 *sv, u32 n_small
 // rotate the same way: a split round reads pile f, keeps entries in f+1 and
 // zeroes f+2.
 
+// Pointer-jumping tail of the invalidation (block-collective, every block).
+// jmp[v] starts as kJumpCut for a vertex without a distance (cut by
+// OnDelete, reached by the frontier rounds, or unreachable), kJumpRoot for
+// the source, else its parent.  A pass replaces every ancestor word by the
+// ancestor's own word, which doubles the path it covers; a cut anywhere on
+// the path reaches v as kJumpCut.  Passes read words that other threads may
+// have advanced already, which only skips further up the same path.
+__device__ __noinline__ void jump_phase(const LoopArgs &a, u64 *bar, u64 &target, u32 &jumps,
+                                        bool &capped, u64 &n_aff, u32 *scratch, Stage *sa,
+                                        Stage *sas) {
+  Ctl *c = a.ctl;
+  const int lane = threadIdx.x & 31;
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  const u32 n = (u32)a.n;
+  const u32 gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (u32 v = gt; v < n; v += nt) {
+    const u64 sv = ld_cg_u64(a.s + v);
+    const u32 p = parent_of(sv);
+    __stcg(a.jmp + v, dist_of(sv) >= kInf ? kJumpCut : (p == kNoParent ? kJumpRoot : p));
+  }
+  target += gridDim.x;
+  grid_sync(bar, target, c, a.lim);
+  for (;;) {
+    if (ld_cg_i32(&c->timeout)) break;
+    if (jumps > 0 && ld_cg_u32(jcnt_ptr(c, (jumps - 1) % 3)) == 0) break;
+    if (jumps >= kMaxJumps) {
+      capped = true;
+      break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile u32 *)jcnt_ptr(c, (jumps + 1) % 3) = 0u;
+    u32 act = 0;
+    for (u32 v = gt; v < n; v += nt) {
+      const u32 j = __ldcg(a.jmp + v);
+      if (j < kJumpRoot) {
+        const u32 ja = __ldcg(a.jmp + j);
+        __stcg(a.jmp + v, ja);
+        act += ja < kJumpRoot ? 1u : 0u;
+      }
+    }
+    u32 total;
+    block_excl_scan(act, scratch, &total);
+    if (threadIdx.x == 0 && total) atomicAdd(jcnt_ptr(c, jumps % 3), total);
+    ++jumps;
+    target += gridDim.x;
+    grid_sync(bar, target, c, a.lim);
+  }
+  // the vertices cut by a jump lose their distance and join A
+  if (!ld_cg_i32(&c->timeout) && !capped) {
+    const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
+    u64 dummy = 0;
+    for (u32 base = gw * 32; base < n; base += nw * 32) {
+      const u32 i = base + lane;
+      bool hit[K] = {};
+      u32 v[K] = {};
+      v[0] = i;
+      if (i < n && __ldcg(a.jmp + i) == kJumpCut) {
+        const u64 sv = ld_cg_u64(a.s + i);
+        if (dist_of(sv) < kInf) {
+          a.s[i] = kInfPack;
+          hit[0] = true;
+        }
+      }
+      n_aff += hit[0];
+      enqueue(qa, a.rev.row, v, hit, 1, dummy);
+    }
+    flush_queue(qa, scratch);
+  }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
   extern __shared__ u32 dsm[];
@@ -754,8 +832,8 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     const u32 sm = ld_cg_u32(&c->seed_min);
     thresh = sat_add(sm < kInf ? sm : 0u, a.lim.delta);
   }
-  u32 cur = 0, f = 0, round = 0, splits = 0;
-  bool capped = false;
+  u32 cur = 0, f = 0, round = 0, splits = 0, jumps = 0;
+  bool capped = false, jump = false;
   for (;;) {
     if (ld_cg_i32(&c->timeout)) break;
     if (round >= a.lim.max_rounds) {
@@ -769,6 +847,11 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
     bool split = false;
     u32 n_far = 0;
+    if (OP == kOpInval && items > 0 && a.lim.jump_round >= 0 &&
+        round >= (u32)a.lim.jump_round) {
+      jump = true;   // the remaining levels by pointer jumping
+      break;
+    }
     if (items == 0) {
       if (nf) n_far = ld_cg_u32(fcnt_ptr(c, f));
       if (n_far == 0) break;                       // fixed point reached
@@ -861,6 +944,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     target += gridDim.x;
     grid_sync(bar, target, c, a.lim);
   }
+  if (OP == kOpInval && jump) jump_phase(a, bar, target, jumps, capped, n_aff, scratch, &sa, &sas);
   n_edges = warp_sum(n_edges);
   n_imp = warp_sum(n_imp);
   n_enq = warp_sum(n_enq);
@@ -895,7 +979,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
       vc->rounds_push = round;
       vc->splits = splits;
     } else {
-      vc->rounds_inval = round;
+      vc->rounds_inval = round + jumps;
     }
     if (capped) atomicCAS(&c->timeout, 0, 1);
   }
@@ -1092,7 +1176,7 @@ LoopArgs make_args(sp_graph *g) {
   a.aent = g->aent;
   a.aown = g->aown;
   a.ftag = g->ftag;
-  a.xdone = g->xdone;
+  a.jmp = g->jmp;
   a.n = g->n;
   a.del_src = nullptr;
   a.del_dst = nullptr;

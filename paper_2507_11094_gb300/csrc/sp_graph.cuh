@@ -93,7 +93,7 @@ struct LoopArgs {
   u32 *aown;
   u32 *fq[3];            // far piles of the near-far push (rotating)
   u32 *ftag;             // far dedupe tags
-  u64 *xdone;            // call << 32 | distance a vertex was expanded with
+  u32 *jmp;              // pointer-jumping words of the invalidation (flag | ancestor)
   int n;
   // fused OnDelete mark (invalidation loop only)
   const int *del_src, *del_dst;
@@ -122,8 +122,9 @@ struct sp_graph {
   sp::u32 *aown = nullptr;
   sp::u32 *fq[3] = {nullptr, nullptr, nullptr};
   sp::u32 *ftag = nullptr;
-  sp::u64 *xdone = nullptr;
+  sp::u32 *jmp = nullptr;
   int32_t delta_user = 0;
+  int32_t jump_round_user = 0;
   long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device
   sp::Ctl *ctl_host = nullptr;  // pinned

@@ -93,6 +93,10 @@ struct Ctl {
   alignas(128) u32 fmin1;
   alignas(128) u32 fmin2;
   alignas(128) u32 seed_min;       // smallest distance seeded into the push
+  // vertices still jumping after each pointer-jumping pass, triple-buffered
+  alignas(128) u32 jcnt0;
+  alignas(128) u32 jcnt1;
+  alignas(128) u32 jcnt2;
   // batch bookkeeping
   alignas(128) u64 mcnt;           // merge elements: segments << 32 | elements
   alignas(128) u32 bstrips;        // 256-entry strips of big rows
@@ -114,6 +118,8 @@ struct Limits {
   u32 max_rounds;        // per fixedPoint loop
   u64 wait_ns;           // per barrier wait
   u32 delta;             // near-far bucket width of the push loop (0 = off)
+  int jump_round;        // frontier rounds of the invalidation before it
+                         // switches to pointer jumping (< 0: never)
 };
 
 // ---------------------------------------------------------------------------

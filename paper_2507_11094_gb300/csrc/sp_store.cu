@@ -206,6 +206,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->fcnt0 = c->fcnt1 = c->fcnt2 = 0;
   c->fmin0 = c->fmin1 = c->fmin2 = kInf;
   c->seed_min = kInf;
+  c->jcnt0 = c->jcnt1 = c->jcnt2 = 0;
   c->mcnt = 0;
   c->bstrips = 0;
   c->n_seg = 0;

@@ -118,6 +118,7 @@ SIGNATURES = {
     "sp_graph_info_get": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
     "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
     "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
+    "sp_set_inval_switch": (ctypes.c_int, [_P, _I32]),
     "sp_sssp_init_multi": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P]),
     "sp_reserve": (ctypes.c_int, [_P, _I64]),
     "sp_async_result_bytes": (ctypes.c_size_t, []),
@@ -392,6 +393,11 @@ class Graph:
     def set_delta(self, delta: int):
         """Near-far bucket width of the push loop (0 = plain frontier rounds)."""
         _check(load().sp_set_push_delta(self._h, int(delta)), "sp_set_push_delta")
+
+    def set_inval_switch(self, rounds: int):
+        """Frontier rounds of the invalidation before pointer jumping
+        (< 0: never, 0: jump at once)."""
+        _check(load().sp_set_inval_switch(self._h, int(rounds)), "sp_set_inval_switch")
 
     def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
         _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")

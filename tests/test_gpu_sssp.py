@@ -51,9 +51,13 @@ def check_all(g, ref, src, store=True):
     return d
 
 
-def run_workload(W, n_batches, store=True, slack=0.25):
+def run_workload(W, n_batches, store=True, slack=0.25, setup=None):
+    """Every batch against the oracle; returns the stats of each batch."""
     ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    out = []
     with sp.Graph(W.n, W.row_off, W.col, W.w, slack=slack) as g:
+        if setup:
+            setup(g)
         g.sssp_init(W.source)
         d = check_all(g, ref, W.source, store)
         for k in range(n_batches):
@@ -63,6 +67,8 @@ def run_workload(W, n_batches, store=True, slack=0.25):
             assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
                     st.n_add_present) == cnt
             d = check_all(g, ref, W.source, store)
+            out.append(st.as_dict())
+    return out
 
 
 def test_tiny_er_ten_batches():
@@ -424,3 +430,28 @@ def test_near_far_static_equals_plain_and_does_less_work():
         nf = g.sssp_init(W.source, stats=True)
         np.testing.assert_array_equal(g.get_dist(), d_plain)
         assert nf.relaxed_edges < plain.relaxed_edges
+
+
+# ------------------------------------------- invalidation: rounds vs jumping
+
+@pytest.mark.parametrize("make,deep", [
+    (lambda: wl.grid(96, 96, batch_frac=0.01, seed=3), True),
+    (lambda: wl.rmat(scale=13, batch_frac=0.02, seed=4), False),
+    (lambda: wl.tiny_er(seed=5), False),
+], ids=["grid-tree-biased", "rmat13", "er1k"])
+def test_invalidation_switch_same_affected_set(make, deep):
+    """Frontier rounds only, pointer jumping at once, and switches after 1
+    and 3 rounds invalidate the same vertices (the descendants of the cut
+    vertices), and every batch matches the oracle."""
+    runs = {}
+    for sw in (-1, 0, 1, 3):
+        W = make()
+        runs[sw] = run_workload(W, 4, store=False,
+                                setup=lambda g, sw=sw: g.set_inval_switch(sw))
+    base = [st["affected"] for st in runs[-1]]
+    assert sum(base) > 0
+    for sw, sts in runs.items():
+        assert [st["affected"] for st in sts] == base, sw
+    if deep:   # deep subtrees: log2(depth) passes instead of one round per level
+        assert (sum(st["rounds_inval"] for st in runs[0]) <
+                sum(st["rounds_inval"] for st in runs[-1]))
