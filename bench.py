@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--inval-switch", type=int, default=None,
                     help="frontier rounds of the invalidation before pointer jumping "
                          "(-1 never; default: the library's)")
+    ap.add_argument("--local-rounds", type=int, default=None,
+                    help="frontier-edge bound of single-block push rounds (0 = off; "
+                         "default: the library's)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--serving-big-scale", type=int, default=22)
     ap.add_argument("--serving-requests", type=int, default=48)
@@ -276,6 +279,9 @@ def run_gb300(args):
     if args.inval_switch is not None:
         g.set_inval_switch(args.inval_switch)
         cfg["inval_switch"] = args.inval_switch
+    if args.local_rounds is not None:
+        g.set_local_rounds(args.local_rounds)
+        cfg["local_rounds"] = args.local_rounds
     g.sssp_init(W.source)
 
     tree = W.tree_fraction > 0

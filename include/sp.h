@@ -251,6 +251,16 @@ sp_status sp_set_push_delta(sp_graph *g, int32_t delta);
 sp_status sp_set_inval_switch(sp_graph *g, int32_t rounds);
 
 /*
+ * Single-block rounds of the push fixedPoint.  A round whose frontier has at
+ * most max_edges out-edges is run by one thread block with the frontier in
+ * shared memory and a block barrier instead of a grid barrier; the other
+ * blocks wait until the frontier grows past the bound or empties.  On
+ * high-diameter graphs most rounds are this small.  0 turns it off; the
+ * bound is clamped to 4096 (the default).  Results do not depend on it.
+ */
+sp_status sp_set_local_rounds(sp_graph *g, int32_t max_edges);
+
+/*
  * Multi-source form of sp_sssp_init: dist[v] is the shortest distance from
  * the nearest of sources[0..k) (each source has dist 0 and parent -1).  On
  * a graph made of k disjoint components with one source each -- the batched
@@ -388,6 +398,16 @@ sp_status sp_server_drain(sp_server *s);
 sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out);
 /* Current distances of a graph (loads it if needed), host array of n. */
 sp_status sp_server_get_dist(sp_server *s, int32_t graph_id, int32_t *dist);
+
+/*
+ * Loop counters of the last call, for tuning: out[0] push rounds, [1] of
+ * them run by a single block, [2] single-block episodes, [3] near-far
+ * splits, [4] far-pile entries moved back, [5] invalidation rounds, [6] of
+ * them pointer-jumping passes, [7] ns spent in single-block rounds, [8] ns
+ * spent in the push loop.  k (<= 9) entries are written; the figures are
+ * those of the last synchronous call.
+ */
+sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
 
 /* Static name of a status code. */
 const char *sp_status_str(sp_status s);

@@ -177,6 +177,7 @@ void set_limits(sp_graph *g) {
   g->lim.wait_ns = g->wait_ns_user > 0 ? (u64)g->wait_ns_user : 2000000000ull;
   g->lim.delta = (u32)std::max(0, g->delta_user);
   g->lim.jump_round = g->jump_round_user;
+  g->lim.local_edges = (u32)g->local_edges_user;
 }
 
 sp_status status_of_repair(sp_graph *g, const Ctl &c) {
@@ -431,6 +432,23 @@ sp_status sp_set_limits(sp_graph *g, int32_t max_rounds, int64_t wait_ns) {
 sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
   if (!g || delta < 0) return SP_EINVAL;
   g->delta_user = delta;
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k) {
+  if (!g || !out || k < 0 || k > 9) return SP_EINVAL;
+  const Ctl &c = *g->ctl_host;
+  const int64_t v[9] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
+                        (int64_t)c.far_moves, c.rounds_inval, c.jumps,
+                        (int64_t)c.local_ns, (int64_t)c.push_ns};
+  for (int i = 0; i < k; ++i) out[i] = v[i];
+  return SP_OK;
+}
+
+sp_status sp_set_local_rounds(sp_graph *g, int32_t max_edges) {
+  if (!g || max_edges < 0) return SP_EINVAL;
+  g->local_edges_user = std::min<int32_t>(max_edges, (int32_t)sp::kLocalRoundCap);
   set_limits(g);
   return SP_OK;
 }

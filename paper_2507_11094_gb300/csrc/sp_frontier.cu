@@ -34,7 +34,7 @@ namespace {
 constexpr int kOpPush = 0, kOpInval = 1;
 constexpr int K = kEdgesPerLane;
 // block stages of the persistent loops (dynamic shared memory)
-constexpr u32 kStageQ = 4096, kStageQS = 8192, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
+constexpr u32 kStageQ = 4096, kStageQS = 12288, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
 constexpr size_t kLoopSmem =
     (2 * kStageQ + kStageQS + 2 * kStageA + kStageAS + kStageF) * sizeof(u32);
 constexpr u32 kStageK = 1024;    // stages of the one-pass kernels (static)
@@ -77,7 +77,12 @@ __device__ __forceinline__ u64 ld_acquire_u64(const u64 *p) {
   return v;
 }
 
-__device__ __forceinline__ void grid_sync(u64 *bar, u64 target, Ctl *c, const Limits &lim) {
+//
+// Returns whether a timeout has been raised (the same answer in every thread
+// of the block, so that loops leave in step and no __syncthreads is left
+// waiting for threads that have gone).
+__device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Limits &lim) {
+  __shared__ int s_stop;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -95,8 +100,10 @@ __device__ __forceinline__ void grid_sync(u64 *bar, u64 target, Ctl *c, const Li
         if (nap < 256) nap += nap >> 1;
       }
     }
+    s_stop = ld_cg_i32(&c->timeout) != 0;
   }
   __syncthreads();
+  return s_stop != 0;
 }
 
 __device__ __forceinline__ u64 *qcnt_ptr(Ctl *c, u32 b) {
@@ -625,6 +632,14 @@ __device__ __forceinline__ bool repair_enabled(Ctl *c) {
          ld_cg_i32(&c->timeout) == 0 && ld_cg_i32(&c->bad) == 0;
 }
 
+// The same test with one answer for the whole block (kernels with barriers).
+__device__ __forceinline__ bool repair_enabled_block(Ctl *c) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = repair_enabled(c) ? 1 : 0;
+  __syncthreads();
+  return s_ok != 0;
+}
+
 __device__ __forceinline__ Queue make_queue(int2 *ent, u32 *own, u64 *cnt, u32 *sv, u32 *scnt,
                                             Stage *st = nullptr, Stage *sst = nullptr) {
   Queue q;
@@ -706,10 +721,17 @@ __device__ __forceinline__ void process_small(Op &op, const u32 *sv, u32 n_small
 // ancestor's own word, which doubles the path it covers; a cut anywhere on
 // the path reaches v as kJumpCut.  Passes read words that other threads may
 // have advanced already, which only skips further up the same path.
-__device__ __noinline__ void jump_phase(const LoopArgs &a, u64 *bar, u64 &target, u32 &jumps,
-                                        bool &capped, u64 &n_aff, u32 *scratch, Stage *sa,
-                                        Stage *sas) {
+struct JumpState {
+  u64 target, n_aff;
+  u32 jumps, capped;
+};
+
+__device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 target,
+                                             u32 *scratch, Stage *sa, Stage *sas) {
   Ctl *c = a.ctl;
+  u32 jumps = 0;
+  bool capped = false;
+  u64 n_aff = 0;
   const int lane = threadIdx.x & 31;
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
@@ -721,9 +743,9 @@ __device__ __noinline__ void jump_phase(const LoopArgs &a, u64 *bar, u64 &target
     __stcg(a.jmp + v, dist_of(sv) >= kInf ? kJumpCut : (p == kNoParent ? kJumpRoot : p));
   }
   target += gridDim.x;
-  grid_sync(bar, target, c, a.lim);
+  bool stop = grid_sync(bar, target, c, a.lim);
   for (;;) {
-    if (ld_cg_i32(&c->timeout)) break;
+    if (stop) break;
     if (jumps > 0 && ld_cg_u32(jcnt_ptr(c, (jumps - 1) % 3)) == 0) break;
     if (jumps >= kMaxJumps) {
       capped = true;
@@ -744,10 +766,10 @@ __device__ __noinline__ void jump_phase(const LoopArgs &a, u64 *bar, u64 &target
     if (threadIdx.x == 0 && total) atomicAdd(jcnt_ptr(c, jumps % 3), total);
     ++jumps;
     target += gridDim.x;
-    grid_sync(bar, target, c, a.lim);
+    stop = grid_sync(bar, target, c, a.lim);
   }
   // the vertices cut by a jump lose their distance and join A
-  if (!ld_cg_i32(&c->timeout) && !capped) {
+  if (!stop && !capped) {
     const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
     u64 dummy = 0;
     for (u32 base = gw * 32; base < n; base += nw * 32) {
@@ -767,15 +789,291 @@ __device__ __noinline__ void jump_phase(const LoopArgs &a, u64 *bar, u64 &target
     }
     flush_queue(qa, scratch);
   }
+  JumpState out;
+  out.target = target;
+  out.n_aff = n_aff;
+  out.jumps = jumps;
+  out.capped = capped ? 1u : 0u;
+  return out;
+}
+
+// Single-block rounds of the push loop.  While the frontier is small a round
+// is mostly latency (a chain of dependent loads and atomics) plus the grid
+// barrier, and one block can do the work: block 0 keeps the frontier in
+// shared memory, ends each round with __syncthreads, and the other blocks
+// wait.  A frontier entry carries its vertex, the vertex's out-degree and
+// the distance it was improved to, so a round needs no global read before
+// its edges: a block scan of the degrees assigns kLocalUnroll edges to each
+// thread, and every edge's (col, w) load, packed atomicMin and (speculative)
+// read of the target's degree are in flight together.  Entries are not
+// deduplicated: every improvement appends its target with the new distance,
+// so the entry with a vertex's current distance is always present and stale
+// ones only repeat relaxations that cannot win.  The next frontier thus
+// holds at most one entry per edge of this one, and a round runs here only
+// if its frontier has at most lim.local_edges (<= kLocalCap) edges.  On exit
+// the frontier goes to queue slot next3(cur), which is empty, and slot
+// next3(next3(cur)) is cleared for the round after.
+constexpr u32 kLocalCap = kStageQ;
+constexpr int kLocalUnroll = (kLocalRoundCap + kPersistThreads - 1) / kPersistThreads;
+static_assert(kLocalUnroll <= K, "far appends go K at a time");
+static_assert(kLocalRoundCap <= (int)kLocalCap, "single-block frontier lists too small");
+// shared-memory words used: two lists of (vertex, degree, distance) and the
+// edge offsets; the far-pile stage starts after the other stages
+static_assert(7 * kLocalCap <= 2 * kStageQ + kStageQS + 2 * kStageA + kStageAS,
+              "single-block round arrays overlap the far-pile stage");
+
+struct LocalState {      // what an episode hands back to the loop
+  u32 cur, round, capped, stop;
+  u64 n_edges, n_imp, n_enq;
+  int range_err;
+};
+
+// Block 0 only (block-collective).  smem: 7 * kLocalCap words that no other
+// stage of the push loop uses while the episode runs.
+__device__ __noinline__ LocalState local_rounds(const LoopArgs &a, u32 cur, u32 round, u32 thresh,
+                                                u32 f, u32 phase, bool nf, u32 *smem,
+                                                Stage *sf, u32 *scratch) {
+  LocalState out{};
+  Ctl *c = a.ctl;
+  const int lane = threadIdx.x & 31;
+  const u32 tid = threadIdx.x, bs = blockDim.x;
+  u32 *lx[2] = {smem, smem + kLocalCap};
+  u32 *ldeg[2] = {smem + 2 * kLocalCap, smem + 3 * kLocalCap};
+  u32 *ld[2] = {smem + 4 * kLocalCap, smem + 5 * kLocalCap};
+  u32 *soff = smem + 6 * kLocalCap;    // exclusive prefix of the entries' out-degrees
+  __shared__ u32 s_n[2], s_stop;
+  {
+    const u64 q = ld_cg_u64(qcnt_ptr(c, cur));
+    const u32 ne = (u32)(q >> 32), ns = ld_cg_u32(scnt_ptr(c, cur));
+    for (u32 i = tid; i < ne + ns; i += bs) {
+      const u32 v = i < ne ? (u32)__ldcg(&a.qent[cur][i].x) : __ldcg(a.qsv[cur] + (i - ne));
+      lx[0][i] = v;
+      ld[0][i] = dist_of(ld_cg_u64(a.s + v));
+      ldeg[0][i] = (u32)__ldg(&a.fwd.row[v].deg);
+    }
+    if (tid == 0) {
+      s_n[0] = ne + ns;
+      s_n[1] = 0;
+      s_stop = 0;
+    }
+  }
+  __syncthreads();
+  u32 p = 0;
+  for (;;) {
+    const u32 nl = s_n[p];
+    if (nl == 0) break;
+    if (round >= a.lim.max_rounds) {
+      out.capped = 1;
+      break;
+    }
+    const u32 *Lx = lx[p], *Ld = ld[p], *Ldeg = ldeg[p];
+    u32 *Nx = lx[p ^ 1], *Nd = ld[p ^ 1], *Ndeg = ldeg[p ^ 1];
+    // (A) edge offsets: a block scan of the degrees (a contiguous run of
+    // entries per thread)
+    const u32 per = (nl + bs - 1) / bs;
+    const u32 b0 = tid * per < nl ? tid * per : nl;
+    const u32 b1 = b0 + per < nl ? b0 + per : nl;
+    u32 sum = 0;
+    for (u32 i = b0; i < b1; ++i) sum += Ld[i] < kInf ? Ldeg[i] : 0u;
+    u32 total;
+    u32 run = block_excl_scan(sum, scratch, &total);
+    if (total > a.lim.local_edges) break;   // the next frontier might not fit
+    for (u32 i = b0; i < b1; ++i) {
+      soff[i] = run;
+      run += Ld[i] < kInf ? Ldeg[i] : 0u;
+    }
+    __syncthreads();
+    // (B) edges: kLocalUnroll per thread, all in flight together
+    u32 x[kLocalUnroll], nd[kLocalUnroll], vv[kLocalUnroll], dx[kLocalUnroll];
+    u64 cand[kLocalUnroll], old[kLocalUnroll];
+#pragma unroll
+    for (int k = 0; k < kLocalUnroll; ++k) {
+      const u32 e = (u32)k * bs + tid;
+      x[k] = 0;
+      nd[k] = kInf;
+      vv[k] = 0;
+      if (e < total) {
+        u32 lo = 0, hi = nl - 1;   // entry owning edge e: last offset <= e
+        while (lo < hi) {
+          const u32 mid = (lo + hi + 1) >> 1;
+          if (soff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const u32 v = Lx[lo];
+        const long long st = __ldg(&a.fwd.row[v].start);
+        const int2 ed = a.fwd.adj[st + (e - soff[lo])];
+        vv[k] = v;
+        x[k] = (u32)ed.x;
+        nd[k] = Ld[lo] + (u32)ed.y;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kLocalUnroll; ++k) {
+      cand[k] = ~0ull;
+      old[k] = 0ull;
+      dx[k] = 0;
+      if ((u32)k * bs + tid < total) {
+        ++out.n_edges;
+        if (nd[k] >= kInf) {
+          out.range_err = 1;
+        } else {
+          cand[k] = pack(nd[k], vv[k]);
+          old[k] = atomicMin((unsigned long long *)(a.s + x[k]), cand[k]);
+          // speculative: the degree is needed only if the edge improves x
+          dx[k] = (u32)__ldg(&a.fwd.row[x[k]].deg);
+        }
+      }
+    }
+    bool want[kLocalUnroll], far[kLocalUnroll];
+    u32 fmin = 0xFFFFFFFFu, cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kLocalUnroll; ++k) {
+      want[k] = far[k] = false;
+      if (cand[k] < old[k]) {
+        ++out.n_imp;
+        if (nd[k] < thresh) {
+          want[k] = dx[k] > 0;
+          cnt += want[k] ? 1u : 0u;
+        } else {
+          far[k] = atomicExch(a.ftag + x[k], phase) != phase;
+          if (far[k] && nd[k] < fmin) fmin = nd[k];
+        }
+      }
+    }
+    // append the improved targets (warp-aggregated)
+    {
+      const u32 inc = warp_incl_scan(cnt);
+      u32 base = 0;
+      if (lane == 31 && inc) base = atomicAdd(&s_n[p ^ 1], inc);
+      base = __shfl_sync(kFull, base, 31) + inc - cnt;
+#pragma unroll
+      for (int k = 0; k < kLocalUnroll; ++k) {
+        if (want[k]) {
+          Nx[base] = x[k];
+          Nd[base] = nd[k];
+          Ndeg[base] = dx[k];
+          ++base;
+        }
+      }
+      out.n_enq += cnt;
+    }
+    if (nf) {
+      bool fw[K];
+      u32 fx[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        fw[k] = k < kLocalUnroll ? far[k] : false;
+        fx[k] = k < kLocalUnroll ? x[k] : 0u;
+      }
+      far_append(a.fq[f], fcnt_ptr(c, f), fmin_ptr(c, f), sf, fx, fw, K, fmin);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_n[p] = 0;
+      if ((round & 63u) == 0) {   // heartbeat for the waiting blocks
+        *(volatile u64 *)&c->lbeat = globaltimer_ns();
+        s_stop = ld_cg_i32(&c->timeout) != 0 ? 1u : 0u;
+      }
+    }
+    ++round;
+    p ^= 1;
+    __syncthreads();
+    if (s_stop) {
+      out.stop = 1;
+      break;
+    }
+  }
+  // hand the frontier back through the global queue (duplicates are fine:
+  // the distributed rounds read each vertex's distance when they expand it)
+  const u32 nxt = next3(cur);
+  const Queue qn =
+      make_queue(a.qent[nxt], a.qown[nxt], qcnt_ptr(c, nxt), a.qsv[nxt], scnt_ptr(c, nxt));
+  u64 dummy = 0;
+  const u32 nl = s_n[p];
+  const u32 *Lx = lx[p];
+  for (u32 base = (threadIdx.x >> 5) * 32; base < nl; base += bs) {
+    const u32 i = base + lane;
+    bool want[K] = {};
+    u32 xx[K] = {};
+    if (i < nl) {
+      xx[0] = Lx[i];
+      want[0] = true;
+    }
+    enqueue(qn, a.fwd.row, xx, want, 1, dummy);
+  }
+  if (tid == 0) {
+    *(volatile u64 *)qcnt_ptr(c, next3(nxt)) = 0ull;
+    *(volatile u32 *)scnt_ptr(c, next3(nxt)) = 0u;
+  }
+  if (nf) flush_far(sf, a.fq[f], fcnt_ptr(c, f), fmin_ptr(c, f), scratch);
+  __syncthreads();
+  out.cur = nxt;
+  out.round = round;
+  return out;
+}
+
+// One episode of single-block rounds (block-collective, every block): block 0
+// runs them and hands the loop state back through the control block; the
+// others wait for it, bounded by block 0's heartbeat.  Counters in the
+// result are this thread's.
+__device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32 cur, u32 round,
+                                                 u32 thresh, u32 f, u32 phase, bool nf,
+                                                 u32 *smem, Stage *sf, u32 *scratch) {
+  Ctl *c = a.ctl;
+  LocalState out{};
+  if (blockIdx.x == 0) {
+    const u64 t_in = globaltimer_ns();
+    out = local_rounds(a, cur, round, thresh, f, phase, nf, smem, sf, scratch);
+    if (threadIdx.x == 0) {
+      c->local_ns += globaltimer_ns() - t_in;
+      *(volatile u32 *)&c->lcur = out.cur;
+      *(volatile u32 *)&c->lround = out.round;
+      *(volatile u32 *)&c->lcap = out.capped;
+      c->local_episodes += 1;
+      c->local_rounds += out.round - round;
+      __threadfence();
+      st_release_u32(&c->lres, lep);
+      scratch[39] = (out.stop || ld_cg_i32(&c->timeout) != 0) ? 1u : 0u;
+    }
+    __syncthreads();
+    out.stop = scratch[39];
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) {
+      // bounded wait: block 0 refreshes a heartbeat every round
+      const u64 t0 = globaltimer_ns();
+      u32 nap = 32;
+      while (ld_acquire_u32(&c->lres) < lep) {
+        if (ld_cg_i32(&c->timeout) != 0) break;
+        const u64 beat = ld_cg_u64(&c->lbeat), now = globaltimer_ns();
+        if (now - (beat > t0 ? beat : t0) > a.lim.wait_ns) {
+          atomicCAS(&c->timeout, 0, 2);
+          break;
+        }
+        __nanosleep(nap);
+        if (nap < 1024) nap += nap >> 1;
+      }
+      scratch[36] = ld_cg_u32(&c->lcur);
+      scratch[37] = ld_cg_u32(&c->lround);
+      scratch[38] = ld_cg_u32(&c->lcap);
+      scratch[39] = ld_cg_i32(&c->timeout) != 0 ? 1u : 0u;
+    }
+    __syncthreads();
+    out.cur = scratch[36];
+    out.round = scratch[37];
+    out.capped = scratch[38];
+    out.stop = scratch[39];
+    __syncthreads();
+  }
+  return out;
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
+__global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   extern __shared__ u32 dsm[];
   __shared__ Stage sq, sqs, sa, sas, sf;
   __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
-  if (!repair_enabled(c)) return;
+  if (!repair_enabled_block(c)) return;
   if (threadIdx.x == 0) {
     u32 *p = dsm;
     sq.n = 0; sq.cap = kStageQ; sq.vmin = kInf; sq.v = p; sq.d = p + kStageQ; p += 2 * kStageQ;
@@ -786,6 +1084,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  const u64 t_start = globaltimer_ns();
   // warp ids interleaved across blocks, so that a round with few chunks
   // still spreads over every SM
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
@@ -824,7 +1123,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
   const u32 tag0 = ld_cg_u32(&c->epoch);
   const u32 phase0 = ld_cg_u32(&c->phase);
   target += gridDim.x;
-  grid_sync(bar, target, c, a.lim);
+  bool stop = grid_sync(bar, target, c, a.lim);
 
   const bool nf = OP == kOpPush && a.lim.delta > 0;
   u32 thresh = 0xFFFFFFFFu;
@@ -832,10 +1131,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     const u32 sm = ld_cg_u32(&c->seed_min);
     thresh = sat_add(sm < kInf ? sm : 0u, a.lim.delta);
   }
-  u32 cur = 0, f = 0, round = 0, splits = 0, jumps = 0;
+  u32 cur = 0, f = 0, round = 0, splits = 0, jumps = 0, lep = 0;
   bool capped = false, jump = false;
   for (;;) {
-    if (ld_cg_i32(&c->timeout)) break;
+    if (stop) break;
     if (round >= a.lim.max_rounds) {
       capped = true;
       break;
@@ -851,6 +1150,23 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
         round >= (u32)a.lim.jump_round) {
       jump = true;   // the remaining levels by pointer jumping
       break;
+    }
+    if (OP == kOpPush && items > 0 && ne + nsmall <= a.lim.local_edges &&
+        (u64)nedge + (u64)kSmallDeg * nsmall <= a.lim.local_edges) {
+      // small frontier: block 0 runs rounds alone until it grows or empties
+      ++lep;
+      const LocalState ls = local_episode(a, lep, cur, round, thresh, f, phase0 + 1u + splits,
+                                          nf, dsm, &sf, scratch);
+      cur = ls.cur;
+      round = ls.round;
+      capped = ls.capped != 0;
+      stop = ls.stop != 0;
+      n_edges += ls.n_edges;
+      n_imp += ls.n_imp;
+      n_enq += ls.n_enq;
+      range_err |= ls.range_err;
+      if (capped) break;
+      continue;
     }
     if (items == 0) {
       if (nf) n_far = ld_cg_u32(fcnt_ptr(c, f));
@@ -942,9 +1258,15 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     cur = nxt;
     ++round;
     target += gridDim.x;
-    grid_sync(bar, target, c, a.lim);
+    stop = grid_sync(bar, target, c, a.lim);
   }
-  if (OP == kOpInval && jump) jump_phase(a, bar, target, jumps, capped, n_aff, scratch, &sa, &sas);
+  if (OP == kOpInval && jump) {
+    const JumpState js = jump_phase(a, bar, target, scratch, &sa, &sas);
+    target = js.target;
+    jumps = js.jumps;
+    capped = capped || js.capped != 0;
+    n_aff += js.n_aff;
+  }
   n_edges = warp_sum(n_edges);
   n_imp = warp_sum(n_imp);
   n_enq = warp_sum(n_enq);
@@ -978,8 +1300,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_loop(LoopArgs a) {
     if (OP == kOpPush) {
       vc->rounds_push = round;
       vc->splits = splits;
+      vc->push_ns = globaltimer_ns() - t_start;
     } else {
       vc->rounds_inval = round + jumps;
+      vc->jumps = jumps;
     }
     if (capped) atomicCAS(&c->timeout, 0, 1);
   }
@@ -1191,7 +1515,7 @@ int loop_blocks(int which, int num_sms) {
   const void *fn = which == kOpPush ? (const void *)k_loop<kOpPush> : (const void *)k_loop<kOpInval>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmem) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopThreads, kLoopSmem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistThreads, kLoopSmem) !=
           cudaSuccess ||
       per_sm < 1)
     return 0;
@@ -1217,7 +1541,7 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) 
   if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kLoopThreads);
+  cfg.blockDim = dim3(kPersistThreads);
   cfg.dynamicSmemBytes = kLoopSmem;
   cfg.stream = g->stream;
   cudaLaunchAttribute attr[1];

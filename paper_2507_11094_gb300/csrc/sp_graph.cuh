@@ -14,7 +14,9 @@ constexpr int kEdgesPerLane = kChunk / 32;
 // Vertices with at most kSmallDeg edges go to a frontier's small list and
 // are expanded one lane per vertex; larger ones get edge ranges and chunks.
 constexpr int kSmallDeg = 8;
-constexpr int kLoopThreads = 1024;
+constexpr int kLocalRoundCap = 4096;   // frontier edges of a single-block round
+constexpr int kLoopThreads = 1024;      // one-pass frontier kernels (pull, add)
+constexpr int kPersistThreads = 768;    // persistent fixedPoint loops: 80 registers a thread
 
 // Per-block staging area (shared memory) for appends to a queue or a far
 // pile: warps append here with shared-memory atomics and the block publishes
@@ -125,6 +127,7 @@ struct sp_graph {
   sp::u32 *jmp = nullptr;
   int32_t delta_user = 0;
   int32_t jump_round_user = 0;
+  int32_t local_edges_user = 4096;
   long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device
   sp::Ctl *ctl_host = nullptr;  // pinned

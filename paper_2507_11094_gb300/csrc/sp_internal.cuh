@@ -93,6 +93,11 @@ struct Ctl {
   alignas(128) u32 fmin1;
   alignas(128) u32 fmin2;
   alignas(128) u32 seed_min;       // smallest distance seeded into the push
+  // single-block rounds of the push loop: episodes ended by block 0 (the
+  // other blocks wait for it), the loop state it hands back, its heartbeat
+  alignas(128) u32 lres;
+  u32 lcur, lround, lcap;
+  u64 lbeat;
   // vertices still jumping after each pointer-jumping pass, triple-buffered
   alignas(128) u32 jcnt0;
   alignas(128) u32 jcnt1;
@@ -111,6 +116,8 @@ struct Ctl {
   u64 merge_slots;       // old + new slots of all merged rows
   u64 far_moves;         // far-pile entries moved back to near
   u32 rounds_inval, rounds_push, splits;
+  u32 local_episodes, local_rounds, jumps;
+  u64 local_ns, push_ns;   // block 0's time in single-block rounds / in the push loop
 };
 
 // Launch-time limits and knobs.
@@ -118,6 +125,8 @@ struct Limits {
   u32 max_rounds;        // per fixedPoint loop
   u64 wait_ns;           // per barrier wait
   u32 delta;             // near-far bucket width of the push loop (0 = off)
+  u32 local_edges;       // push rounds with at most this many frontier edges
+                         // run in one block (0 = never)
   int jump_round;        // frontier rounds of the invalidation before it
                          // switches to pointer jumping (< 0: never)
 };

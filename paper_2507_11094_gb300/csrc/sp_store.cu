@@ -207,6 +207,8 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->fmin0 = c->fmin1 = c->fmin2 = kInf;
   c->seed_min = kInf;
   c->jcnt0 = c->jcnt1 = c->jcnt2 = 0;
+  c->lres = c->lcur = c->lround = c->lcap = 0;
+  c->lbeat = 0;
   c->mcnt = 0;
   c->bstrips = 0;
   c->n_seg = 0;
@@ -219,6 +221,8 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->merge_slots = 0;
   c->far_moves = 0;
   c->rounds_inval = c->rounds_push = c->splits = 0;
+  c->local_episodes = c->local_rounds = c->jumps = 0;
+  c->local_ns = c->push_ns = 0;
   c->call = c->call + 1;
   if (full) {
     c->epoch = 1;

@@ -119,6 +119,8 @@ SIGNATURES = {
     "sp_set_limits": (ctypes.c_int, [_P, _I32, _I64]),
     "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
     "sp_set_inval_switch": (ctypes.c_int, [_P, _I32]),
+    "sp_set_local_rounds": (ctypes.c_int, [_P, _I32]),
+    "sp_loop_counters": (ctypes.c_int, [_P, _P, _I32]),
     "sp_sssp_init_multi": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P]),
     "sp_reserve": (ctypes.c_int, [_P, _I64]),
     "sp_async_result_bytes": (ctypes.c_size_t, []),
@@ -398,6 +400,19 @@ class Graph:
         """Frontier rounds of the invalidation before pointer jumping
         (< 0: never, 0: jump at once)."""
         _check(load().sp_set_inval_switch(self._h, int(rounds)), "sp_set_inval_switch")
+
+    def loop_counters(self) -> dict:
+        """Loop counters of the last call (tuning aid)."""
+        out = np.zeros(9, dtype=np.int64)
+        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 9),
+               "sp_loop_counters")
+        keys = ("rounds_push", "local_rounds", "local_episodes", "splits", "far_moves",
+                "rounds_inval", "jumps", "local_ns", "push_ns")
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def set_local_rounds(self, max_edges: int):
+        """Frontier-edge bound of single-block push rounds (0 = off)."""
+        _check(load().sp_set_local_rounds(self._h, int(max_edges)), "sp_set_local_rounds")
 
     def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
         _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")

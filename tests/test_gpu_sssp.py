@@ -455,3 +455,19 @@ def test_invalidation_switch_same_affected_set(make, deep):
     if deep:   # deep subtrees: log2(depth) passes instead of one round per level
         assert (sum(st["rounds_inval"] for st in runs[0]) <
                 sum(st["rounds_inval"] for st in runs[-1]))
+
+
+# ------------------------------------------------ single-block push rounds
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.grid(80, 80, batch_frac=0.01, seed=6),
+    lambda: wl.rmat(scale=13, batch_frac=0.01, seed=7),
+], ids=["grid", "rmat13"])
+@pytest.mark.parametrize("bound,delta", [(0, 0), (64, 0), (4096, 0), (4096, 300), (512, 40)])
+def test_local_rounds_any_bound_matches_oracle(make, bound, delta):
+    """Push rounds run by one block (frontier bounds 64 .. 4096 edges, with
+    and without near-far ordering) give the oracle's distances."""
+    def setup(g):
+        g.set_local_rounds(bound)
+        g.set_delta(delta)
+    run_workload(make(), 3, store=False, setup=setup)
