@@ -37,8 +37,8 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                           src, "-o", tmp])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-Wall",
+                           "-shared", "-fPIC", src, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -62,6 +62,11 @@ def _load():
     lib.or_apply_batch.argtypes = [P, i64, P, P, i64, P, P, P, P]
     lib.or_dijkstra.restype = ctypes.c_int
     lib.or_dijkstra.argtypes = [P, i32, P]
+    f32 = ctypes.c_float
+    lib.or_pr_static.restype = ctypes.c_int
+    lib.or_pr_static.argtypes = [P, f32, f32, i32, P, P]
+    lib.or_pr_batch.restype = ctypes.c_int
+    lib.or_pr_batch.argtypes = [P, i64, P, P, i64, P, P, P, f32, f32, i32, P, P]
     _lib = lib
     return lib
 
@@ -138,6 +143,33 @@ class OracleGraph:
         """Apply a ``workloads.Batch``."""
         return self.apply_batch(batch.del_src, batch.del_dst, batch.add_src,
                                 batch.add_dst, batch.add_w)
+
+    # -- PageRank (appendix listing "Dynamic PR": staticPR, DynPR) --------
+    def pagerank(self, damping=0.85, beta=1e-6, max_iter=100):
+        """staticPR: (ranks float32[n], Jacobi steps)."""
+        pr = np.empty(self.n, dtype=np.float32)
+        it = ctypes.c_int32(0)
+        rc = _load().or_pr_static(self._h, float(damping), float(beta), int(max_iter),
+                                  _ptr(pr), ctypes.byref(it))
+        if rc != OK:
+            raise OracleError(rc, "or_pr_static")
+        return pr, int(it.value)
+
+    def pagerank_batch(self, batch, pr, damping=0.85, beta=1e-6, max_iter=100):
+        """One DynPR batch on ranks ``pr`` (float32[n], updated in place).
+        Returns counters: the four batch counters, vertices flagged for the
+        deletions and for the insertions, Jacobi steps of each phase."""
+        a = [np.ascontiguousarray(x, dtype=np.int32)
+             for x in (batch.del_src, batch.del_dst, batch.add_src, batch.add_dst,
+                       batch.add_w)]
+        assert pr.dtype == np.float32 and pr.flags.c_contiguous and pr.size == self.n
+        cnt = np.zeros(8, dtype=np.int64)
+        rc = _load().or_pr_batch(self._h, a[0].size, _ptr(a[0]), _ptr(a[1]), a[2].size,
+                                 _ptr(a[2]), _ptr(a[3]), _ptr(a[4]), float(damping),
+                                 float(beta), int(max_iter), _ptr(pr), _ptr(cnt))
+        if rc != OK:
+            raise OracleError(rc, "or_pr_batch")
+        return tuple(int(x) for x in cnt)
 
     def dijkstra(self, src: int, allow_range_error: bool = False) -> np.ndarray:
         """Distances from src (int32; INF for unreachable)."""

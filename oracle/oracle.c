@@ -34,6 +34,7 @@
  * Graph model: one growable array per row, sorted by destination, with
  * binary search for lookups and memmove for updates.  Slow and obvious.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -315,4 +316,194 @@ int or_dijkstra(const or_graph *g, int32_t src, int32_t *dist_out) {
     }
     free(d); free(done); free(h);
     return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * PageRank (paper, appendix listing "Dynamic PR coded in StarPlat DSL":
+ * staticPR, Incremental, Decremental, DynPR).  Single precision, as the
+ * listing's propNode<float>.
+ *
+ * One Jacobi step over a vertex set S, with N = number of vertices and d
+ * the damping factor:
+ *     pr'[v] = (1 - d) / N + d * sum_{u -> v} pr[u] / outdeg(u)   (v in S)
+ * in-neighbours u in increasing id order, each term pr[u] / outdeg(u)
+ * rounded to float and added to a float sum.  Vertices without out-edges
+ * pass no rank on (the listing divides by count_outNbrs of in-neighbours
+ * only).  Steps repeat until sum_{v in S} |pr'[v] - pr[v]| <= beta or
+ * max_iter steps have run; the listing accumulates the signed difference,
+ * read here as its absolute value (a signed sum can stop on cancellation).
+ *
+ * staticPR: S = all vertices, pr = 1/N at the start.
+ * DynPR, per batch: (1) the destinations of the deletions are flagged and
+ * the flags spread along out-edges to every reachable vertex of the current
+ * graph (propagateNodeFlags, read as forward reachability); (2) the
+ * deletions are applied (updateCSRDel); (3) Jacobi steps over the flagged
+ * vertices from their current ranks (Decremental); then the same three
+ * steps for the insertions (propagateNodeFlags on the graph after the
+ * deletions, updateCSRAdd, Incremental).  Unflagged vertices keep their
+ * ranks.
+ * ---------------------------------------------------------------------- */
+
+/* In-neighbour lists of the current graph, sorted by source id. */
+typedef struct {
+    int64_t *off;
+    int32_t *src;
+    int32_t *outdeg;
+} or_rev;
+
+static void rev_free(or_rev *r) {
+    free(r->off);
+    free(r->src);
+    free(r->outdeg);
+}
+
+static int rev_build(const or_graph *g, or_rev *r) {
+    const int32_t n = g->n;
+    int64_t m = or_num_edges(g);
+    r->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    r->src = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    r->outdeg = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!r->off || !r->src || !r->outdeg) {
+        rev_free(r);
+        return ORACLE_ENOMEM;
+    }
+    for (int32_t u = 0; u < n; ++u) {
+        r->outdeg[u] = g->deg[u];
+        for (int32_t j = 0; j < g->deg[u]; ++j) r->off[g->row[u][j].dst + 1] += 1;
+    }
+    for (int32_t v = 0; v < n; ++v) r->off[v + 1] += r->off[v];
+    int64_t *fill = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!fill) {
+        rev_free(r);
+        return ORACLE_ENOMEM;
+    }
+    for (int32_t v = 0; v < n; ++v) fill[v] = r->off[v];
+    /* sources visited in increasing order, so every list comes out sorted */
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t j = 0; j < g->deg[u]; ++j) r->src[fill[g->row[u][j].dst]++] = u;
+    free(fill);
+    return ORACLE_OK;
+}
+
+/* Jacobi steps over the vertices with flag[v] != 0 (all if flag == NULL). */
+static int pr_iterate(const or_graph *g, const unsigned char *flag, float d, float beta,
+                      int32_t max_iter, float *pr, int32_t *iters) {
+    const int32_t n = g->n;
+    or_rev r;
+    int st = rev_build(g, &r);
+    if (st != ORACLE_OK) return st;
+    float *nxt = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+    if (!nxt) {
+        rev_free(&r);
+        return ORACLE_ENOMEM;
+    }
+    const float base = (1.0f - d) / (float)n;
+    int32_t it = 0;
+    double diff;
+    do {
+        diff = 0.0;
+        for (int32_t v = 0; v < n; ++v) {
+            if (flag && !flag[v]) continue;
+            float sum = 0.0f;
+            for (int64_t e = r.off[v]; e < r.off[v + 1]; ++e) {
+                const int32_t u = r.src[e];
+                const float term = pr[u] / (float)r.outdeg[u];
+                sum = sum + term;
+            }
+            const float prod = d * sum;
+            const float val = base + prod;
+            diff += fabs((double)val - (double)pr[v]);
+            nxt[v] = val;
+        }
+        for (int32_t v = 0; v < n; ++v)
+            if (!flag || flag[v]) pr[v] = nxt[v];
+        ++it;
+    } while (diff > (double)beta && it < max_iter);
+    *iters = it;
+    free(nxt);
+    rev_free(&r);
+    return ORACLE_OK;
+}
+
+/* Flag the given destinations and every vertex reachable from them. */
+static int64_t propagate_flags(const or_graph *g, const int32_t *dst, int64_t k,
+                               unsigned char *flag) {
+    const int32_t n = g->n;
+    int32_t *queue = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!queue) return -1;
+    int64_t head = 0, tail = 0;
+    memset(flag, 0, (size_t)n);
+    for (int64_t i = 0; i < k; ++i) {
+        const int32_t v = dst[i];
+        if (!flag[v]) {
+            flag[v] = 1;
+            queue[tail++] = v;
+        }
+    }
+    while (head < tail) {
+        const int32_t v = queue[head++];
+        for (int32_t j = 0; j < g->deg[v]; ++j) {
+            const int32_t x = g->row[v][j].dst;
+            if (!flag[x]) {
+                flag[x] = 1;
+                queue[tail++] = x;
+            }
+        }
+    }
+    free(queue);
+    return tail;
+}
+
+int or_pr_static(const or_graph *g, float d, float beta, int32_t max_iter, float *pr,
+                 int32_t *iters) {
+    if (!g || !pr || !iters || max_iter < 1 || !(d >= 0.0f && d <= 1.0f) || !(beta >= 0.0f))
+        return ORACLE_EINVAL;
+    for (int32_t v = 0; v < g->n; ++v) pr[v] = 1.0f / (float)g->n;
+    return pr_iterate(g, NULL, d, beta, max_iter, pr, iters);
+}
+
+/* counters: [0..3] as or_apply_batch, [4] flagged for the deletions, [5]
+ * flagged for the insertions, [6] Jacobi steps of Decremental, [7] of
+ * Incremental. */
+int or_pr_batch(or_graph *g, int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                const int32_t *add_w, float d, float beta, int32_t max_iter, float *pr,
+                int64_t *counters) {
+    if (!g || !pr || !counters || n_del < 0 || n_add < 0 || max_iter < 1) return ORACLE_EINVAL;
+    for (int64_t i = 0; i < n_del; ++i)
+        if (del_src[i] < 0 || del_src[i] >= g->n || del_dst[i] < 0 || del_dst[i] >= g->n)
+            return ORACLE_EINVAL;
+    for (int64_t i = 0; i < n_add; ++i)
+        if (add_src[i] < 0 || add_src[i] >= g->n || add_dst[i] < 0 || add_dst[i] >= g->n ||
+            add_w[i] < 1 || add_w[i] > ORACLE_WMAX)
+            return ORACLE_EINVAL;
+    unsigned char *flag = (unsigned char *)malloc((size_t)(g->n > 0 ? g->n : 1));
+    if (!flag) return ORACLE_ENOMEM;
+    int64_t c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
+    int32_t it1 = 0, it2 = 0;
+    int st = ORACLE_OK;
+    /* deletions: OnDelete flags, propagateNodeFlags, updateCSRDel, Decremental */
+    int64_t f1 = propagate_flags(g, del_dst, n_del, flag);
+    if (f1 < 0) st = ORACLE_ENOMEM;
+    if (st == ORACLE_OK) st = or_apply_batch(g, n_del, del_src, del_dst, 0, NULL, NULL, NULL, c1);
+    if (st == ORACLE_OK && f1 > 0) st = pr_iterate(g, flag, d, beta, max_iter, pr, &it1);
+    /* insertions: OnAdd flags, propagateNodeFlags, updateCSRAdd, Incremental */
+    int64_t f2 = 0;
+    if (st == ORACLE_OK) {
+        f2 = propagate_flags(g, add_dst, n_add, flag);
+        if (f2 < 0) st = ORACLE_ENOMEM;
+    }
+    if (st == ORACLE_OK) st = or_apply_batch(g, 0, NULL, NULL, n_add, add_src, add_dst, add_w, c2);
+    if (st == ORACLE_OK && f2 > 0) st = pr_iterate(g, flag, d, beta, max_iter, pr, &it2);
+    free(flag);
+    if (st != ORACLE_OK) return st;
+    counters[0] = c1[0];
+    counters[1] = c1[1];
+    counters[2] = c2[2];
+    counters[3] = c2[3];
+    counters[4] = f1;
+    counters[5] = f2;
+    counters[6] = it1;
+    counters[7] = it2;
+    return ORACLE_OK;
 }
