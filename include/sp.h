@@ -399,6 +399,49 @@ sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out);
 /* Current distances of a graph (loads it if needed), host array of n. */
 sp_status sp_server_get_dist(sp_server *s, int32_t graph_id, int32_t *dist);
 
+/* ------------------------------------------------------------------------
+ * Dynamic PageRank (paper, appendix listing "Dynamic PR coded in StarPlat
+ * DSL": staticPR, DynPR with Decremental / Incremental; Section 7 reports it
+ * beside SSSP).  Single precision, as the listing's propNode<float>.
+ *
+ * A Jacobi step over a vertex set S sets, for every v in S,
+ *     pr[v] = (1 - damping) / n + damping * sum_{u -> v} pr[u] / outdeg(u)
+ * (vertices without out-edges pass no rank on); steps repeat until
+ * sum_{v in S} |pr'[v] - pr[v]| <= beta or max_iter steps have run.
+ * ---------------------------------------------------------------------- */
+
+/* staticPR: all ranks start at 1/n and S is every vertex.  Sets the PageRank
+ * settings used by later batches.  SP_EINVAL for damping outside [0, 1],
+ * beta < 0 or max_iter < 1.  stats (nullable): rounds_push = Jacobi steps,
+ * relaxed_edges = in-edges pulled. */
+sp_status sp_pr_init(sp_graph *g, float damping, float beta, int32_t max_iter,
+                     sp_batch_stats *stats);
+
+/*
+ * DynPR for one batch, same arguments and batch semantics as
+ * sp_apply_batch.  First the deletions: their destinations are flagged, the
+ * flags spread along out-edges to every reachable vertex of the current
+ * graph (propagateNodeFlags), the deletions are merged into both stores,
+ * and Jacobi steps run over the flagged vertices from their current ranks.
+ * Then the same for the insertions on the graph after the deletions.
+ * Unflagged vertices keep their ranks.  The whole batch is validated before
+ * either phase (SP_EINVAL leaves the graph and the ranks unchanged).
+ * Requires sp_pr_init (else SP_ESTATE).  SSSP distances stop being valid
+ * once edges change (sp_sssp_init restores them), and an SSSP batch that
+ * changes edges ends the ranks' validity (sp_pr_init restores them).
+ * stats (nullable): affected = vertices flagged over both phases,
+ * rounds_inval = flag-propagation rounds, rounds_push = Jacobi steps,
+ * relaxed_edges = in-edges pulled; the batch counters as sp_apply_batch.
+ */
+sp_status sp_pr_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                            const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                            const int32_t *add_dst, const int32_t *add_w,
+                            int inputs_on_device, sp_batch_stats *stats);
+
+/* Current ranks (n floats) into host or device memory; SP_ESTATE without
+ * valid ranks. */
+sp_status sp_pr_get(const sp_graph *g, float *pr, int out_on_device);
+
 /*
  * Loop counters of the last call, for tuning: out[0] push rounds, [1] of
  * them run by a single block, [2] single-block episodes, [3] near-far

@@ -6,6 +6,7 @@
 // backend instead copies a `finished` flag to the host every fixedPoint
 // iteration, Section 5.3).
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -296,6 +297,8 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->jmp, n * 4);
   al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
+  al.put(g->pr[0], n * 4); al.put(g->pr[1], n * 4);
+  al.put(g->pracc, n * 4); al.put(g->prflag, n * 4);
   al.put(g->ctl, sizeof(Ctl));
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   for (auto &e : g->ev)
@@ -572,6 +575,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   }
   const Ctl &c = *g->ctl_host;
   g->m += (long long)c.add_applied - (long long)c.del_applied;
+  if (c.add_applied + c.del_applied > 0) g->pr_state = 0;   // ranks no longer hold
   fill_stats(g, c, stats, launches, regrows, ni, timed);
   return status_of_repair(g, c);
 }
@@ -648,6 +652,7 @@ sp_status sp_apply_batch_async(sp_graph *g, int64_t n_del, const int32_t *del_sr
   }
   g->async_ni = ni;
   g->async_launches = launches + 1;
+  g->pr_state = 0;   // the edge set may change: ranks no longer hold
   return SP_OK;
 }
 
@@ -707,6 +712,240 @@ sp_status sp_exec_destroy(sp_exec *x) {
   if (x->exec) cudaGraphExecDestroy(x->exec);
   if (x->graph) cudaGraphDestroy(x->graph);
   delete x;
+  return SP_OK;
+}
+
+// ---- PageRank (appendix listing "Dynamic PR") ------------------------------
+
+namespace {
+
+// One DynPR phase on the device: flags from `dst` spread along out-edges
+// (propagateNodeFlags), the phase's updates merged into both stores
+// (updateCSRDel or updateCSRAdd), then Jacobi steps over the flagged
+// vertices (Decremental or Incremental).  Grows the spare pools and
+// repeats the phase when a merge runs out of room (nothing has changed
+// then).  Adds the phase's counters to acc.
+sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                   const int *ad, const int *aw, long long na, const int *flag_dst,
+                   long long n_flag, Ctl &acc, int *launches, int *regrows) {
+  const long long ni = 2 * (nd + na);
+  if (ni == 0) return SP_OK;
+  sp_status rc = SP_OK;
+  for (int attempt = 0;; ++attempt) {
+    ++g->prtag;
+    sp::launch_ctl_reset(g, 0, launches);
+    cudaError_t e = cudaSuccess;
+    if (n_flag > 0) e = sp::launch_flag(g, flag_dst, n_flag, launches);
+    sp::launch_prep(g, ds, dd, nd, as, ad, aw, na, launches);
+    sp::launch_segments(g, ni, launches);
+    sp::launch_count(g, ni, launches);
+    sp::launch_merge(g, ni, launches);
+    sp::launch_finish(g, launches);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(g->stream);
+      return SP_ECUDA;
+    }
+    rc = read_ctl(g);
+    if (rc != SP_OK) return rc;
+    const Ctl &c = *g->ctl_host;
+    if (c.status != 0) return (sp_status)c.status;
+    if (c.bad) return SP_ECUDA;
+    if (c.timeout) return SP_ETIMEOUT;
+    if (c.need_grow == 0) break;
+    if (attempt >= 6) return SP_ENOMEM;
+    ++*regrows;
+    if (c.need_grow & sp::kGrowPoolFwd) {
+      rc = sp::store_grow_pool(g, &g->fwd, (long long)c.pool_need[0] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    if (c.need_grow & sp::kGrowPoolRev) {
+      rc = sp::store_grow_pool(g, &g->rev, (long long)c.pool_need[1] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    rc = sp::ensure_owner_tables(g);
+    if (rc != SP_OK) return rc;
+  }
+  {
+    const Ctl &c = *g->ctl_host;
+    g->m += (long long)c.add_applied - (long long)c.del_applied;
+    acc.del_applied += c.del_applied;
+    acc.del_absent += c.del_absent;
+    acc.add_applied += c.add_applied;
+    acc.add_present += c.add_present;
+    acc.affected += c.affected;
+    acc.rows_touched += c.rows_touched;
+    acc.rows_relocated += c.rows_relocated;
+    acc.inval_edges += c.inval_edges;
+    acc.merge_slots += c.merge_slots;
+    acc.rounds_inval += c.rounds_inval;
+  }
+  if (n_flag == 0) return SP_OK;   // nothing flagged: every rank stays
+  sp::launch_pr_select(g, 0, launches);
+  cudaError_t e = sp::launch_pr(g, launches);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(g->stream);
+    return SP_ECUDA;
+  }
+  rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  const Ctl &c = *g->ctl_host;
+  acc.pull_edges += c.pull_edges;
+  acc.rounds_push += c.pr_iters;
+  if (c.bad) return SP_ECUDA;
+  if (c.timeout) return SP_ETIMEOUT;
+  return SP_OK;
+}
+
+void pr_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int regrows,
+              float ms) {
+  if (!st) return;
+  std::memset(st, 0, sizeof(*st));
+  st->n_del_applied = (int64_t)c.del_applied;
+  st->n_del_absent = (int64_t)c.del_absent;
+  st->n_add_applied = (int64_t)c.add_applied;
+  st->n_add_present = (int64_t)c.add_present;
+  st->affected = (int64_t)c.affected;          // vertices flagged, both phases
+  st->relaxed_edges = (int64_t)c.pull_edges;   // in-edges pulled, all Jacobi steps
+  st->rows_touched = (int64_t)c.rows_touched;
+  st->rows_relocated = (int64_t)c.rows_relocated;
+  st->rounds_inval = (int32_t)c.rounds_inval;  // flag-propagation rounds
+  st->rounds_push = (int32_t)c.rounds_push;    // Jacobi steps
+  st->n_launches = launches;
+  st->regrows = regrows;
+  // algorithmic bytes: flag propagation (as a frontier walk), the merge, and
+  // per pulled in-edge its source id (4), rank (4) and out-degree (4)
+  st->alg_bytes[SP_PH_INVAL] = (int64_t)(c.affected * 16 + c.inval_edges * 12);
+  st->alg_bytes[SP_PH_MERGE] = (int64_t)(c.merge_slots * 8 + c.rows_touched * 32);
+  st->alg_bytes[SP_PH_PULL] = (int64_t)(c.pull_edges * 12);
+  st->ms_total = ms;
+  (void)g;
+}
+
+}  // namespace
+
+sp_status sp_pr_init(sp_graph *g, float damping, float beta, int32_t max_iter,
+                     sp_batch_stats *stats) {
+  if (!g || !(damping >= 0.f && damping <= 1.f) || !(beta >= 0.f) || max_iter < 1)
+    return SP_EINVAL;
+  const size_t nn = (size_t)g->n;
+  if (!g->pr[0]) {
+    g->pr[0] = (float *)g->al.get(nn * 4);
+    g->pr[1] = (float *)g->al.get(nn * 4);
+    g->pracc = (float *)g->al.get(nn * 4);
+    g->prflag = (u32 *)g->al.get(nn * 4);
+    if (!g->pr[0] || !g->pr[1] || !g->pracc || !g->prflag) return SP_ENOMEM;
+    cudaMemsetAsync(g->prflag, 0, nn * 4, g->stream);
+    g->prtag = 0;
+    if (sp::loop_blocks(2, g->num_sms) <= 0) return SP_ECUDA;
+  }
+  g->pr_damping = damping;
+  g->pr_beta = beta;
+  g->pr_max_iter = max_iter;
+  int launches = 0;
+  rec(g, true, 0);
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_pr_fill(g, 1.0f / (float)g->n, &launches);
+  sp::launch_pr_select(g, 1, &launches);
+  cudaError_t e = sp::launch_pr(g, &launches);
+  rec(g, true, SP_NPHASE);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(g->stream);
+    g->pr_state = 0;
+    return SP_ECUDA;
+  }
+  sp_status rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  const Ctl &c = *g->ctl_host;
+  if (c.bad || c.timeout) {
+    g->pr_state = 0;
+    return c.bad ? SP_ECUDA : SP_ETIMEOUT;
+  }
+  g->pr_state = 1;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, g->ev[0], g->ev[SP_NPHASE]);
+  Ctl acc{};
+  acc.pull_edges = c.pull_edges;
+  acc.rounds_push = c.pr_iters;
+  acc.affected = (u64)g->n;
+  pr_stats(g, acc, stats, launches, 0, ms);
+  return SP_OK;
+}
+
+sp_status sp_pr_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                            const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                            const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
+                            sp_batch_stats *stats) {
+  if (!g) return SP_EINVAL;
+  if (n_del < 0 || n_add < 0) return SP_EINVAL;
+  if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
+    return SP_EINVAL;
+  if (n_del + n_add > (1LL << 30)) return SP_EINVAL;
+  if (g->m + n_add > kMaxEdges) return SP_EINVAL;
+  if (g->pr_state != 1) return SP_ESTATE;
+  const long long nb = n_del + n_add;
+  sp_status rc = ensure_batch_buffers(g, 2 * nb, inputs_on_device ? 0 : std::max(n_del, n_add));
+  if (rc != SP_OK) return rc;
+  auto &b = g->bb;
+  const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
+  rec(g, true, 0);
+  if (!inputs_on_device) {
+    cudaStream_t s = g->stream;
+    if (n_del) {
+      cudaMemcpyAsync(b.in_del_src, del_src, n_del * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_del_dst, del_dst, n_del * 4, cudaMemcpyHostToDevice, s);
+    }
+    if (n_add) {
+      cudaMemcpyAsync(b.in_add_src, add_src, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_dst, add_dst, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_w, add_w, n_add * 4, cudaMemcpyHostToDevice, s);
+    }
+    ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
+  }
+  int launches = 0, regrows = 0;
+  // the whole batch is checked before the first phase changes anything
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_check_batch(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
+  rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  if (g->ctl_host->status != 0) return (sp_status)g->ctl_host->status;
+  Ctl acc{};
+  // deletions: OnDelete flags, propagateNodeFlags, updateCSRDel, Decremental
+  rc = pr_phase(g, ds, dd, n_del, nullptr, nullptr, nullptr, 0, dd, n_del, acc, &launches,
+                &regrows);
+  // insertions: OnAdd flags, propagateNodeFlags, updateCSRAdd, Incremental
+  if (rc == SP_OK)
+    rc = pr_phase(g, nullptr, nullptr, 0, as, ad, aw, n_add, ad, n_add, acc, &launches,
+                  &regrows);
+  rec(g, true, SP_NPHASE);
+  if (acc.del_applied + acc.add_applied > 0) g->state = 0;   // distances no longer hold
+  if (rc != SP_OK) {
+    g->pr_state = 0;
+    return rc;
+  }
+  float ms = 0.f;
+  cudaEventSynchronize(g->ev[SP_NPHASE]);
+  cudaEventElapsedTime(&ms, g->ev[0], g->ev[SP_NPHASE]);
+  pr_stats(g, acc, stats, launches, regrows, ms);
+  return SP_OK;
+}
+
+sp_status sp_pr_get(const sp_graph *g, float *pr, int out_on_device) {
+  if (!g || !pr) return SP_EINVAL;
+  if (g->pr_state != 1) return SP_ESTATE;
+  const cudaError_t e = cudaMemcpyAsync(pr, g->pr[0], (size_t)g->n * 4,
+                                        out_on_device ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyDeviceToHost,
+                                        g->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
   return SP_OK;
 }
 

@@ -31,7 +31,7 @@ namespace sp {
 
 namespace {
 
-constexpr int kOpPush = 0, kOpInval = 1;
+constexpr int kOpPush = 0, kOpInval = 1, kOpFlag = 2;
 constexpr int K = kEdgesPerLane;
 // block stages of the persistent loops (dynamic shared memory)
 constexpr u32 kStageQ = 4096, kStageQS = 12288, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
@@ -448,6 +448,36 @@ struct InvalOp {
     enqueue(next, row, tx, want, K, n_enq);
     u64 dummy = 0;
     enqueue(alist, rrow, tx, want, K, dummy);
+  }
+};
+
+// propagateNodeFlags body (PageRank): every vertex reachable from a flagged
+// one is flagged once (prflag[x] = ptag) and joins the next frontier.
+struct FlagOp {
+  u32 *flag;
+  u32 ptag;
+  Queue next;
+  const RowMeta *row;
+  u64 n_edges = 0, n_enq = 0, n_aff = 0;
+  int range_err = 0;
+
+  __device__ __forceinline__ u32 vdata(u32) { return 0; }
+  __device__ __forceinline__ u64 load(int2 e) { return __ldcg(flag + e.x); }
+  __device__ __forceinline__ void run(const bool *act, const u32 *, const u32 *,
+                                      const int2 *ed, const u64 *sx) {
+    u32 tx[K];
+    bool want[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      tx[k] = (u32)ed[k].x;
+      want[k] = false;
+      if (act[k]) {
+        ++n_edges;
+        if ((u32)sx[k] != ptag) want[k] = atomicExch(flag + ed[k].x, ptag) != ptag;
+        n_aff += want[k];
+      }
+    }
+    enqueue(next, row, tx, want, K, n_enq);
   }
 };
 
@@ -1117,6 +1147,22 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     flush_queue(q0, scratch);
     flush_queue(qa, scratch);
   }
+  if (OP == kOpFlag && a.n_del > 0) {
+    // the phase's destinations are the flags' seeds
+    const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &sq, &sqs);
+    for (long long base = (long long)gw * 32; base < a.n_del; base += (long long)nw * 32) {
+      const long long i = base + lane;
+      bool hit[K] = {};
+      u32 v[K] = {};
+      if (i < a.n_del) {
+        v[0] = (u32)a.del_dst[i];
+        hit[0] = atomicExch(a.prflag + v[0], a.ptag) != a.ptag;
+      }
+      n_aff += hit[0];
+      enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
+    }
+    flush_queue(q0, scratch);
+  }
 
   // state shared by all blocks (read before the first barrier; only block 0
   // writes it back, after the last barrier)
@@ -1233,6 +1279,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
         n_enq += op.n_enq;
         range_err |= op.range_err;
       }
+    } else if (OP == kOpFlag) {
+      FlagOp op{a.prflag, a.ptag, qn, a.fwd.row};
+      for (u32 it = gw; it < items; it += nw) {
+        if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
+        else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
+      }
+      n_edges += op.n_edges;
+      n_enq += op.n_enq;
+      n_aff += op.n_aff;
     } else {
       const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
       InvalOp op{a.s, qn, qa, a.fwd.row, a.rev.row};
@@ -1482,6 +1537,196 @@ __global__ void k_unpack(const u64 *__restrict__ s, int n, int *dist, int *paren
   }
 }
 
+// --- PageRank (appendix listing "Dynamic PR") ---------------------------------
+
+// Select the vertices of a Jacobi phase into the list A (entries over the
+// reverse store): every vertex (staticPR) or those flagged in this phase.
+// Selected vertices without in-edges go to a plain list (zlist, zcnt): their
+// new rank is the constant term.
+__global__ void __launch_bounds__(kLoopThreads) k_pr_select(LoopArgs a, int all) {
+  __shared__ u32 sv[kStageK], sd[kStageK], ssv[kStageK];
+  __shared__ Stage st, sst;
+  __shared__ u32 scratch[40];
+  Ctl *c = a.ctl;
+  if (!repair_enabled(c)) return;
+  if (threadIdx.x == 0) {
+    st.n = 0; st.cap = kStageK; st.vmin = kInf; st.v = sv; st.d = sd;
+    sst.n = 0; sst.cap = kStageK; sst.vmin = kInf; sst.v = ssv; sst.d = nullptr;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &st, &sst);
+  u64 dummy = 0;
+  const u32 n = (u32)a.n;
+  const u32 step = gridDim.x * blockDim.x;
+  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += step) {
+    const u32 v = base + lane;
+    bool want[K] = {};
+    u32 x[K] = {};
+    x[0] = v;
+    if (v < n) want[0] = all || __ldcg(a.prflag + v) == a.ptag;
+    const bool z = want[0] && __ldg(&a.rev.row[v].deg) == 0;
+    const u32 bal = __ballot_sync(kFull, z);
+    if (bal) {
+      u32 zb = 0;
+      if (lane == 0) zb = atomicAdd(&c->zcnt, (u32)__popc(bal));
+      zb = __shfl_sync(kFull, zb, 0);
+      if (z) a.jmp[zb + __popc(bal & lanemask_lt())] = v;
+    }
+    enqueue(qa, a.rev.row, x, want, 1, dummy);
+  }
+  flush_queue(qa, scratch);
+}
+
+__global__ void k_pr_fill(float *p0, float *p1, float *acc, int n, float value) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    p0[v] = value;
+    p1[v] = value;
+    acc[v] = 0.0f;
+  }
+}
+
+// Pull body of a Jacobi step: each lane adds pr[u] / outdeg(u) over its run
+// of in-edges u -> v in slot order and adds the run's sum to acc[v].  A
+// vertex with at most kSmallDeg in-edges is one lane's single run, so its
+// sum is formed in in-neighbour order, as a sequential loop would.
+struct PrOp {
+  const float *pr;
+  float *acc;
+  const RowMeta *frow;
+  u64 n_edges = 0, n_enq = 0;
+  int range_err = 0;
+
+  __device__ __forceinline__ u32 vdata(u32) { return 0; }
+  __device__ __forceinline__ u64 load(int2 e) {
+    const u32 bits = __float_as_uint(__ldcg(pr + e.x));
+    const u32 deg = (u32)__ldg(&frow[e.x].deg);
+    return ((u64)deg << 32) | bits;
+  }
+  __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
+                                      const int2 *, const u64 *sx) {
+    u32 bv = kNoEdge;
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (act[k]) {
+        ++n_edges;
+        if (ov[k] != bv) {
+          if (bv != kNoEdge) atomicAdd(acc + bv, sum);
+          bv = ov[k];
+          sum = 0.0f;
+        }
+        const float term = __fdiv_rn(__uint_as_float((u32)sx[k]), (float)(u32)(sx[k] >> 32));
+        sum = __fadd_rn(sum, term);
+      }
+    }
+    if (bv != kNoEdge) atomicAdd(acc + bv, sum);
+  }
+};
+
+struct PrArgs {
+  LoopArgs la;
+  float *pr[2];
+  float *acc;
+  float base, damping;
+  double beta;
+  int max_iter;
+};
+
+// Jacobi steps over the list A (persistent, cooperative): pass 1 pulls the
+// in-edge sums into acc, pass 2 forms pr' = base + damping * acc, adds
+// |pr' - pr| to the step's difference and clears acc; a step ends when the
+// difference is at most beta or max_iter steps have run.  The result is left
+// in both rank buffers.
+__device__ __forceinline__ double *prd_ptr(Ctl *c, u32 b) {
+  return b == 0 ? &c->prd0 : (b == 1 ? &c->prd1 : &c->prd2);
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 1) k_pr(PrArgs p) {
+  const LoopArgs &a = p.la;
+  Ctl *c = a.ctl;
+  if (!repair_enabled_block(c)) return;
+  __shared__ double s_sum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  const u64 ac = ld_cg_u64(&c->acnt);
+  const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
+  const u32 ns = ld_cg_u32(&c->ascnt);
+  const u32 nz = ld_cg_u32(&c->zcnt);
+  const u32 sgroups = (ns + 31) / 32;
+  const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
+  u64 *bar = &c->bar_push;
+  u64 target = 0;
+  u64 n_edges = 0;
+  u32 it = 0, cur = 0;
+  bool stop = false;
+  for (;;) {
+    // pass 1: in-edge sums
+    PrOp op{p.pr[cur], p.acc, a.fwd.row};
+    for (u32 i = gw; i < items; i += nw) {
+      if (i < sgroups) process_small(op, a.asv, ns, i, a.rev, a.n, c);
+      else process_chunk(op, a.aent, a.aown, ne, nedge, i - sgroups, a.rev, a.n, c);
+    }
+    n_edges += op.n_edges;
+    target += gridDim.x;
+    stop = grid_sync(bar, target, c, a.lim);
+    if (stop) break;
+    // pass 2: new ranks and the step's difference
+    const float *pc = p.pr[cur];
+    float *pn = p.pr[cur ^ 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile double *)prd_ptr(c, (it + 1) % 3) = 0.0;
+    double diff = 0.0;
+    const u32 gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (u32 i = gt; i < ns + ne + nz; i += nt) {
+      const u32 v = i < ns ? __ldcg(a.asv + i)
+                           : (i < ns + ne ? (u32)__ldcg(&a.aent[i - ns].x) : __ldcg(a.jmp + (i - ns - ne)));
+      const float val = __fadd_rn(p.base, __fmul_rn(p.damping, __ldcg(p.acc + v)));
+      diff += fabs((double)val - (double)__ldcg(pc + v));
+      pn[v] = val;
+      p.acc[v] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_xor_sync(kFull, diff, o);
+    if (lane == 0) s_sum[warp] = diff;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
+      if (t != 0.0) atomicAdd(prd_ptr(c, it % 3), t);
+    }
+    target += gridDim.x;
+    stop = grid_sync(bar, target, c, a.lim);
+    if (stop) break;
+    const double d = *(volatile double *)prd_ptr(c, it % 3);
+    ++it;
+    cur ^= 1;
+    if (!(d > p.beta) || it >= (u32)p.max_iter) break;
+  }
+  // leave the result in both buffers
+  if (!stop) {
+    const float *src = p.pr[cur];
+    float *dst = p.pr[cur ^ 1];
+    const u32 gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (u32 i = gt; i < ns + ne + nz; i += nt) {
+      const u32 v = i < ns ? __ldcg(a.asv + i)
+                           : (i < ns + ne ? (u32)__ldcg(&a.aent[i - ns].x) : __ldcg(a.jmp + (i - ns - ne)));
+      dst[v] = __ldcg(src + v);
+    }
+  }
+  n_edges = warp_sum(n_edges);
+  if (lane == 0 && n_edges) atomicAdd(&c->pull_edges, n_edges);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    volatile Ctl *vc = c;
+    vc->pr_iters = it;
+    vc->rounds_push = it;
+    vc->acnt = 0ull;
+    vc->ascnt = 0u;
+    vc->zcnt = 0u;
+  }
+}
+
 LoopArgs make_args(sp_graph *g) {
   LoopArgs a;
   a.ctl = g->ctl;
@@ -1505,6 +1750,8 @@ LoopArgs make_args(sp_graph *g) {
   a.del_src = nullptr;
   a.del_dst = nullptr;
   a.n_del = 0;
+  a.prflag = g->prflag;
+  a.ptag = g->prtag;
   return a;
 }
 
@@ -1512,7 +1759,9 @@ LoopArgs make_args(sp_graph *g) {
 
 int loop_blocks(int which, int num_sms) {
   int per_sm = 0;
-  const void *fn = which == kOpPush ? (const void *)k_loop<kOpPush> : (const void *)k_loop<kOpInval>;
+  const void *fn = which == kOpPush    ? (const void *)k_loop<kOpPush>
+                   : which == kOpInval ? (const void *)k_loop<kOpInval>
+                                       : (const void *)k_loop<kOpFlag>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmem) !=
           cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistThreads, kLoopSmem) !=
@@ -1550,8 +1799,9 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ++*launches;
-  return op == kOpPush ? cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a)
-                       : cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
+  if (op == kOpPush) return cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a);
+  if (op == kOpInval) return cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
+  return cudaLaunchKernelEx(&cfg, k_loop<kOpFlag>, a);
 }
 
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches) {
@@ -1592,6 +1842,51 @@ void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launche
   k_gather_dist<<<(unsigned)std::max(1, std::min(g->num_sms * 4, (k + 255) / 256)), 256, 0,
                   g->stream>>>(g->s, g->n, vs_d, k, out_d, g->ctl);
   ++*launches;
+}
+
+cudaError_t launch_flag(sp_graph *g, const int *dst, long long n, int *launches) {
+  LoopArgs a = make_args(g);
+  a.del_dst = dst;
+  a.n_del = n;
+  return launch_loop(g, kOpFlag, a, launches);
+}
+
+void launch_pr_fill(sp_graph *g, float value, int *launches) {
+  k_pr_fill<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(
+      g->pr[0], g->pr[1], g->pracc, g->n, value);
+  ++*launches;
+}
+
+void launch_pr_select(sp_graph *g, int all, int *launches) {
+  LoopArgs a = make_args(g);
+  k_pr_select<<<(unsigned)std::max(1, g->num_sms), kLoopThreads, 0, g->stream>>>(a, all);
+  ++*launches;
+}
+
+cudaError_t launch_pr(sp_graph *g, int *launches) {
+  PrArgs p;
+  p.la = make_args(g);
+  p.pr[0] = g->pr[0];
+  p.pr[1] = g->pr[1];
+  p.acc = g->pracc;
+  p.base = (1.0f - g->pr_damping) / (float)g->n;
+  p.damping = g->pr_damping;
+  p.beta = (double)g->pr_beta;
+  p.max_iter = g->pr_max_iter;
+  int blocks = g->num_sms;
+  if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kPersistThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = g->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++*launches;
+  return cudaLaunchKernelEx(&cfg, k_pr, p);
 }
 
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches) {

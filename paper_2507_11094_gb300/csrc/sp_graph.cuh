@@ -97,9 +97,13 @@ struct LoopArgs {
   u32 *ftag;             // far dedupe tags
   u32 *jmp;              // pointer-jumping words of the invalidation (flag | ancestor)
   int n;
-  // fused OnDelete mark (invalidation loop only)
+  // fused OnDelete mark (invalidation loop only); the flag loop takes its
+  // seeds from del_dst
   const int *del_src, *del_dst;
   long long n_del;
+  // PageRank flags: prflag[v] == ptag marks v for the current phase
+  u32 *prflag;
+  u32 ptag;
 };
 
 }  // namespace sp
@@ -125,6 +129,15 @@ struct sp_graph {
   sp::u32 *fq[3] = {nullptr, nullptr, nullptr};
   sp::u32 *ftag = nullptr;
   sp::u32 *jmp = nullptr;
+  // PageRank state (allocated by sp_pr_init): ranks in two buffers that
+  // agree between calls, the pull accumulators, phase flags and settings
+  float *pr[2] = {nullptr, nullptr};
+  float *pracc = nullptr;
+  sp::u32 *prflag = nullptr;
+  sp::u32 prtag = 0;
+  int pr_state = 0;            // 0 = no ranks, 1 = valid
+  float pr_damping = 0.85f, pr_beta = 1e-6f;
+  int pr_max_iter = 100;
   int32_t delta_user = 0;
   int32_t jump_round_user = 0;
   int32_t local_edges_user = 4096;
@@ -162,6 +175,8 @@ void launch_segments(sp_graph *g, long long n_items, int *launches);
 void launch_count(sp_graph *g, long long n_items, int *launches);
 void launch_merge(sp_graph *g, long long n_items, int *launches);
 void launch_finish(sp_graph *g, int *launches);
+void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                        const int *ad, const int *aw, long long na, int *launches);
 
 // sp_frontier.cu
 int loop_blocks(int which, int num_sms);
@@ -173,6 +188,11 @@ void launch_pull(sp_graph *g, int *launches);
 void launch_add(sp_graph *g, long long n_items, int *launches);
 cudaError_t launch_push(sp_graph *g, int *launches);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+// PageRank
+cudaError_t launch_flag(sp_graph *g, const int *dst, long long n, int *launches);
+void launch_pr_fill(sp_graph *g, float value, int *launches);
+void launch_pr_select(sp_graph *g, int all, int *launches);
+cudaError_t launch_pr(sp_graph *g, int *launches);
 void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches);
 
 }  // namespace sp

@@ -98,6 +98,12 @@ struct Ctl {
   alignas(128) u32 lres;
   u32 lcur, lround, lcap;
   u64 lbeat;
+  // PageRank: sum |pr' - pr| of each Jacobi step (rotating) and the steps run
+  alignas(128) double prd0;
+  alignas(128) double prd1;
+  alignas(128) double prd2;
+  u32 pr_iters;
+  u32 zcnt;              // selected vertices without in-edges (PageRank)
   // vertices still jumping after each pointer-jumping pass, triple-buffered
   alignas(128) u32 jcnt0;
   alignas(128) u32 jcnt1;

@@ -207,6 +207,9 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->fmin0 = c->fmin1 = c->fmin2 = kInf;
   c->seed_min = kInf;
   c->jcnt0 = c->jcnt1 = c->jcnt2 = 0;
+  c->prd0 = c->prd1 = c->prd2 = 0.0;
+  c->pr_iters = 0;
+  c->zcnt = 0;
   c->lres = c->lcur = c->lround = c->lcap = 0;
   c->lbeat = 0;
   c->mcnt = 0;
@@ -263,6 +266,24 @@ __global__ void k_prep(const int *__restrict__ ds, const int *__restrict__ dd, l
     keys[nb + i] = (1ull << (2 * bits + 1)) | ((u64)v << (bits + 1)) | ((u64)u << 1) | kind;
     vals[i] = (u32)w;
     vals[nb + i] = (u32)w;
+  }
+}
+
+// Validation only (ids and weights), for callers that apply a batch in
+// several steps and must reject it before the first one.
+__global__ void k_check_batch(const int *__restrict__ ds, const int *__restrict__ dd, long long nd,
+                              const int *__restrict__ as, const int *__restrict__ ad,
+                              const int *__restrict__ aw, long long na, int n, Ctl *ctl) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd + na;
+       i += (long long)gridDim.x * blockDim.x) {
+    bool ok;
+    if (i < nd) {
+      ok = ds[i] >= 0 && ds[i] < n && dd[i] >= 0 && dd[i] < n;
+    } else {
+      const long long j = i - nd;
+      ok = as[j] >= 0 && as[j] < n && ad[j] >= 0 && ad[j] < n && aw[j] >= 1 && aw[j] <= SP_WMAX;
+    }
+    if (!ok) set_status(ctl, SP_EINVAL);
   }
 }
 
@@ -1059,6 +1080,14 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   k_merge_big<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
   k_merge_big_items<<<blocks_for(ni, kThreads, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
   *launches += 3;
+}
+
+void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                        const int *ad, const int *aw, long long na, int *launches) {
+  if (nd + na == 0) return;
+  k_check_batch<<<blocks_for(nd + na, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(
+      ds, dd, nd, as, ad, aw, na, g->n, g->ctl);
+  ++*launches;
 }
 
 void launch_finish(sp_graph *g, int *launches) {

@@ -121,6 +121,9 @@ SIGNATURES = {
     "sp_set_inval_switch": (ctypes.c_int, [_P, _I32]),
     "sp_set_local_rounds": (ctypes.c_int, [_P, _I32]),
     "sp_loop_counters": (ctypes.c_int, [_P, _P, _I32]),
+    "sp_pr_init": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, _I32, _P]),
+    "sp_pr_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int, _P]),
+    "sp_pr_get": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "sp_sssp_init_multi": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P]),
     "sp_reserve": (ctypes.c_int, [_P, _I64]),
     "sp_async_result_bytes": (ctypes.c_size_t, []),
@@ -400,6 +403,39 @@ class Graph:
         """Frontier rounds of the invalidation before pointer jumping
         (< 0: never, 0: jump at once)."""
         _check(load().sp_set_inval_switch(self._h, int(rounds)), "sp_set_inval_switch")
+
+    # -- PageRank ------------------------------------------------------------
+    def pr_init(self, damping: float = 0.85, beta: float = 1e-6, max_iter: int = 100,
+                stats: bool = False):
+        """staticPR (single precision); returns BatchStats or None."""
+        st = BatchStats() if stats else None
+        rc = load().sp_pr_init(self._h, float(damping), float(beta), int(max_iter),
+                               ctypes.byref(st) if st else None)
+        _check(rc, "sp_pr_init")
+        return st
+
+    def pr_apply_batch(self, del_src, del_dst, add_src, add_dst, add_w, stats: bool = False):
+        """DynPR for one batch (numpy: host inputs, CUDA tensors: device)."""
+        arr = _Arrays([del_src, del_dst, add_src, add_dst, add_w], [np.int32] * 5)
+        size = (lambda a: int(a.numel())) if arr.on_device else (lambda a: int(a.size))
+        nd, na = size(arr.keep[0]), size(arr.keep[2])
+        if size(arr.keep[1]) != nd or size(arr.keep[3]) != na or size(arr.keep[4]) != na:
+            raise SpError(SP_EINVAL, "batch array sizes")
+        st = BatchStats() if stats else None
+        rc = load().sp_pr_apply_batch(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
+                                      arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
+                                      ctypes.byref(st) if st else None)
+        _check(rc, "sp_pr_apply_batch")
+        return st
+
+    def pr_apply(self, batch, stats: bool = False):
+        return self.pr_apply_batch(batch.del_src, batch.del_dst, batch.add_src, batch.add_dst,
+                                   batch.add_w, stats=stats)
+
+    def pr_get(self):
+        out = np.empty(self.n, dtype=np.float32)
+        _check(load().sp_pr_get(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), "sp_pr_get")
+        return out
 
     def loop_counters(self) -> dict:
         """Loop counters of the last call (tuning aid)."""
