@@ -65,6 +65,8 @@ def _load():
     f32 = ctypes.c_float
     lib.or_pr_static.restype = ctypes.c_int
     lib.or_pr_static.argtypes = [P, f32, f32, i32, P, P]
+    lib.or_tc_static.restype = ctypes.c_int
+    lib.or_tc_static.argtypes = [P, P]
     lib.or_pr_batch.restype = ctypes.c_int
     lib.or_pr_batch.argtypes = [P, i64, P, P, i64, P, P, P, f32, f32, i32, P, P]
     _lib = lib
@@ -143,6 +145,16 @@ class OracleGraph:
         """Apply a ``workloads.Batch``."""
         return self.apply_batch(batch.del_src, batch.del_dst, batch.add_src,
                                 batch.add_dst, batch.add_w)
+
+    # -- triangle count (appendix listing "Dynamic TC": staticTC) ----------
+    def triangles(self) -> int:
+        """staticTC on the current edge set (every triangle once on a
+        symmetric graph)."""
+        c = ctypes.c_int64(0)
+        rc = _load().or_tc_static(self._h, ctypes.byref(c))
+        if rc != OK:
+            raise OracleError(rc, "or_tc_static")
+        return int(c.value)
 
     # -- PageRank (appendix listing "Dynamic PR": staticPR, DynPR) --------
     def pagerank(self, damping=0.85, beta=1e-6, max_iter=100):

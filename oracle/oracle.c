@@ -507,3 +507,32 @@ int or_pr_batch(or_graph *g, int64_t n_del, const int32_t *del_src, const int32_
     counters[7] = it2;
     return ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Triangle count (paper, appendix listing "Dynamic TC coded in StarPlat
+ * DSL", staticTC): for every vertex v, every neighbour u < v and every
+ * neighbour w > v of v such that u -> w is an edge, count one.  On a
+ * symmetric graph (every edge stored in both directions) this counts every
+ * triangle once, at its middle vertex.  The dynamic form of the listing
+ * (Decremental / Incremental corrections) reaches the same number for the
+ * graph after the batch; the oracle recounts from scratch.
+ * ---------------------------------------------------------------------- */
+int or_tc_static(const or_graph *g, int64_t *count) {
+    if (!g || !count) return ORACLE_EINVAL;
+    int64_t c = 0;
+    for (int32_t v = 0; v < g->n; ++v) {
+        const or_edge *r = g->row[v];
+        for (int32_t a = 0; a < g->deg[v]; ++a) {
+            const int32_t u = r[a].dst;
+            if (u >= v) continue;
+            for (int32_t b = 0; b < g->deg[v]; ++b) {
+                const int32_t w = r[b].dst;
+                if (w <= v) continue;
+                const int32_t j = row_lower_bound(g, u, w);
+                if (j < g->deg[u] && g->row[u][j].dst == w) ++c;
+            }
+        }
+    }
+    *count = c;
+    return ORACLE_OK;
+}

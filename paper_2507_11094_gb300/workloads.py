@@ -373,3 +373,115 @@ def grid(rows: int = 4096, cols: int = 4096, batch_frac: float = 0.01,
     b = max(2, int(round(batch_frac * col.size)))
     return Workload(f"grid{rows}x{cols}", n, row_off, col, w, 0, st, b, seed,
                     tree_fraction=tree_fraction)
+
+
+# --------------------------------------------------------------------------
+# symmetric (undirected) graphs for the triangle count
+# --------------------------------------------------------------------------
+
+def symmetrize(n: int, row_off: np.ndarray, col: np.ndarray, w: np.ndarray):
+    """Every edge in both directions; a pair stored twice keeps the weight of
+    its (min, max) orientation, else of the one edge given.  Self-loops are
+    dropped."""
+    u = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_off))
+    v = col.astype(np.int64)
+    keep = u != v
+    u, v, ww = u[keep], v[keep], np.asarray(w)[keep]
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    key = lo * n + hi
+    order = np.lexsort((u > v, key))        # the (min, max) orientation first
+    key, ww = key[order], ww[order]
+    first = np.ones(key.size, bool)
+    first[1:] = key[1:] != key[:-1]
+    key, ww = key[first], ww[first]
+    a, b = key // n, key % n
+    both = np.concatenate([a * n + b, b * n + a])
+    wb = np.concatenate([ww, ww])
+    order = np.argsort(both, kind="stable")
+    return _csr_from_keys(n, both[order], wb[order])
+
+
+class UndirectedStream:
+    """Update batches of a symmetric graph: every deleted or inserted pair
+    {u, v} appears as both u -> v and v -> u, deletions name present pairs,
+    insertions absent ones, and no pair appears twice in a batch."""
+
+    def __init__(self, n, row_off, col, w, wlo, whi, sampler=None):
+        self.n = int(n)
+        keys = csr_keys(self.n, row_off, col)
+        u, v = keys // self.n, keys % self.n
+        sel = u < v
+        self.keys = np.sort(keys[sel])                 # pairs as u * n + v, u < v
+        order = np.argsort(keys[sel], kind="stable")
+        self.wts = np.asarray(w, np.int32)[sel][order]
+        self.wlo, self.whi = int(wlo), int(whi)
+        self.sampler = sampler
+
+    def next(self, n_del: int, n_add: int, seed: int, **_ignored) -> Batch:
+        """n_del / n_add directed updates, i.e. n_del // 2 and n_add // 2
+        pairs."""
+        rng = np.random.default_rng(seed)
+        n = self.n
+        n_del, n_add = n_del // 2, n_add // 2
+        di = rng.choice(self.keys.size, size=n_del, replace=False)
+        dkeys = self.keys[di]
+        chosen = np.empty(0, np.int64)
+        for _ in range(64):
+            if chosen.size >= n_add:
+                break
+            k = int((n_add - chosen.size) * 1.5) + 64
+            if self.sampler is not None:
+                a, b = self.sampler.draw(rng, k)
+            else:
+                a = rng.integers(0, n, size=k, dtype=np.int64)
+                b = rng.integers(0, n, size=k, dtype=np.int64)
+            lo, hi = np.minimum(a, b), np.maximum(a, b)
+            cand = (lo * n + hi)[lo != hi]
+            pos = np.minimum(np.searchsorted(self.keys, cand), max(self.keys.size - 1, 0))
+            cand = cand[~((self.keys.size > 0) & (self.keys[pos] == cand))]
+            cand = cand[~np.isin(cand, dkeys)]
+            chosen = _first_unique_in_order(np.concatenate([chosen, cand]))
+        if chosen.size < n_add:
+            raise RuntimeError("could not draw enough new pairs")
+        akeys = chosen[:n_add]
+        aw = rng.integers(self.wlo, self.whi + 1, size=n_add, dtype=np.int64).astype(np.int32)
+        du, dv = dkeys // n, dkeys % n
+        au, av = akeys // n, akeys % n
+        batch = Batch(
+            del_src=np.concatenate([du, dv]).astype(np.int32),
+            del_dst=np.concatenate([dv, du]).astype(np.int32),
+            add_src=np.concatenate([au, av]).astype(np.int32),
+            add_dst=np.concatenate([av, au]).astype(np.int32),
+            add_w=np.concatenate([aw, aw]),
+        )
+        keep = np.ones(self.keys.size, bool)
+        keep[di] = False
+        keys, wts = self.keys[keep], self.wts[keep]
+        order = np.argsort(akeys, kind="stable")
+        pos = np.searchsorted(keys, akeys[order])
+        self.keys = np.insert(keys, pos, akeys[order])
+        self.wts = np.insert(wts, pos, aw[order])
+        return batch
+
+
+def sym_er(n: int = 1024, pairs: int = 4096, batch_pairs: int = 32, seed: int = 1):
+    """Symmetric ER graph: `pairs` random unordered pairs, both directions,
+    w~U[1,100]; batches of batch_pairs deleted + batch_pairs new pairs."""
+    ro, col, w = er_digraph(n, pairs, 1, 100, seed)
+    ro, col, w = symmetrize(n, ro, col, w)
+    st = UndirectedStream(n, ro, col, w, 1, 100)
+    return Workload(f"sym-er{n}", n, ro, col, w, 0, st, 4 * batch_pairs, seed)
+
+
+def sym_rmat(scale: int = 16, edge_factor: int = 8, batch_frac: float = 0.01, seed: int = 1):
+    """Symmetric R-MAT: edge_factor * n R-MAT edges (a=.57 b=.19 c=.19
+    d=.05) stored in both directions; batches of batch_frac of the pairs
+    deleted and as many new R-MAT pairs inserted, both directions."""
+    n = 1 << scale
+    ro, col, w, sampler = rmat_digraph(scale, edge_factor * n, 1, 100, seed)
+    ro, col, w = symmetrize(n, ro, col, w)
+    st = UndirectedStream(n, ro, col, w, 1, 100, sampler=sampler)
+    pairs = col.size // 2
+    b = max(1, int(round(batch_frac * pairs)))
+    return Workload(f"sym-rmat{scale}-ef{edge_factor}", n, ro, col, w,
+                    max_out_degree_source(ro), st, 4 * b, seed)
