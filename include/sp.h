@@ -372,6 +372,8 @@ typedef struct {
     int64_t resident_bytes, max_resident_bytes;
     int64_t loads, evictions, batches, queries, updates;
     int32_t resident_graphs, registered_graphs;
+    int64_t recoveries;        /* batches whose repair hit a device bound and
+                                  whose distances were recomputed from the source */
 } sp_server_stats;
 
 sp_status sp_server_create(const sp_server_config *cfg, sp_server **out);
@@ -442,13 +444,42 @@ sp_status sp_pr_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
  * valid ranks. */
 sp_status sp_pr_get(const sp_graph *g, float *pr, int out_on_device);
 
+/* ------------------------------------------------------------------------
+ * Dynamic triangle count (paper, appendix listing "Dynamic TC coded in
+ * StarPlat DSL": staticTC, Decremental, Incremental, DynTC).  The graph is
+ * read as undirected and must store every edge in both directions; every
+ * batch must list every updated pair in both directions.
+ * ---------------------------------------------------------------------- */
+
+/* staticTC: for every vertex v, the pairs of neighbours u < v < w with u -> w
+ * an edge (every triangle once).  SP_EINVAL if some edge lacks its reverse
+ * (the count is then not kept). */
+sp_status sp_tc_init(sp_graph *g, int64_t *count);
+
+/*
+ * DynTC for one batch (arguments and batch semantics as sp_apply_batch):
+ * the applied deletions' corrections are counted on the graph before the
+ * merge and subtracted, the applied insertions' on the graph after it and
+ * added; *count receives the triangle count of the new graph.  SP_EINVAL
+ * (nothing changes) if an update's reverse is missing from the batch;
+ * SP_ESTATE without sp_tc_init.  Changing edges ends the validity of SSSP
+ * distances and PageRank ranks, and SSSP or PageRank batches that change
+ * edges end the count's (sp_tc_init restores it).  stats: the batch
+ * counters as sp_apply_batch; affected = triangle sightings counted.
+ */
+sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                            const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                            const int32_t *add_dst, const int32_t *add_w,
+                            int inputs_on_device, int64_t *count, sp_batch_stats *stats);
+
 /*
  * Loop counters of the last call, for tuning: out[0] push rounds, [1] of
  * them run by a single block, [2] single-block episodes, [3] near-far
  * splits, [4] far-pile entries moved back, [5] invalidation rounds, [6] of
  * them pointer-jumping passes, [7] ns spent in single-block rounds, [8] ns
- * spent in the push loop.  k (<= 9) entries are written; the figures are
- * those of the last synchronous call.
+ * spent in the push loop, [9] the bound that ended the last call early (0
+ * none, 1 a round or pass cap, 2 a barrier wait).  k (<= 10) entries are
+ * written; the figures are those of the last synchronous call.
  */
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
 

@@ -298,6 +298,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
   al.put(g->pr[0], n * 4); al.put(g->pr[1], n * 4);
+  al.put(g->prc[0], n * 4); al.put(g->prc[1], n * 4);
   al.put(g->pracc, n * 4); al.put(g->prflag, n * 4);
   al.put(g->ctl, sizeof(Ctl));
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
@@ -440,11 +441,11 @@ sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
 }
 
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k) {
-  if (!g || !out || k < 0 || k > 9) return SP_EINVAL;
+  if (!g || !out || k < 0 || k > 10) return SP_EINVAL;
   const Ctl &c = *g->ctl_host;
-  const int64_t v[9] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
-                        (int64_t)c.far_moves, c.rounds_inval, c.jumps,
-                        (int64_t)c.local_ns, (int64_t)c.push_ns};
+  const int64_t v[10] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
+                         (int64_t)c.far_moves, c.rounds_inval, c.jumps,
+                         (int64_t)c.local_ns, (int64_t)c.push_ns, c.timeout};
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return SP_OK;
 }
@@ -575,7 +576,10 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   }
   const Ctl &c = *g->ctl_host;
   g->m += (long long)c.add_applied - (long long)c.del_applied;
-  if (c.add_applied + c.del_applied > 0) g->pr_state = 0;   // ranks no longer hold
+  if (c.add_applied + c.del_applied > 0) {
+    g->pr_state = 0;   // ranks no longer hold
+    g->tc_state = 0;   // nor does the triangle count
+  }
   fill_stats(g, c, stats, launches, regrows, ni, timed);
   return status_of_repair(g, c);
 }
@@ -652,7 +656,8 @@ sp_status sp_apply_batch_async(sp_graph *g, int64_t n_del, const int32_t *del_sr
   }
   g->async_ni = ni;
   g->async_launches = launches + 1;
-  g->pr_state = 0;   // the edge set may change: ranks no longer hold
+  g->pr_state = 0;   // the edge set may change: ranks and counts no longer hold
+  g->tc_state = 0;
   return SP_OK;
 }
 
@@ -835,9 +840,12 @@ sp_status sp_pr_init(sp_graph *g, float damping, float beta, int32_t max_iter,
   if (!g->pr[0]) {
     g->pr[0] = (float *)g->al.get(nn * 4);
     g->pr[1] = (float *)g->al.get(nn * 4);
+    g->prc[0] = (float *)g->al.get(nn * 4);
+    g->prc[1] = (float *)g->al.get(nn * 4);
     g->pracc = (float *)g->al.get(nn * 4);
     g->prflag = (u32 *)g->al.get(nn * 4);
-    if (!g->pr[0] || !g->pr[1] || !g->pracc || !g->prflag) return SP_ENOMEM;
+    if (!g->pr[0] || !g->pr[1] || !g->prc[0] || !g->prc[1] || !g->pracc || !g->prflag)
+      return SP_ENOMEM;
     cudaMemsetAsync(g->prflag, 0, nn * 4, g->stream);
     g->prtag = 0;
     if (sp::loop_blocks(2, g->num_sms) <= 0) return SP_ECUDA;
@@ -923,7 +931,10 @@ sp_status sp_pr_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
     rc = pr_phase(g, nullptr, nullptr, 0, as, ad, aw, n_add, ad, n_add, acc, &launches,
                   &regrows);
   rec(g, true, SP_NPHASE);
-  if (acc.del_applied + acc.add_applied > 0) g->state = 0;   // distances no longer hold
+  if (acc.del_applied + acc.add_applied > 0) {
+    g->state = 0;      // distances no longer hold
+    g->tc_state = 0;   // nor does the triangle count
+  }
   if (rc != SP_OK) {
     g->pr_state = 0;
     return rc;
@@ -932,6 +943,128 @@ sp_status sp_pr_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   cudaEventSynchronize(g->ev[SP_NPHASE]);
   cudaEventElapsedTime(&ms, g->ev[0], g->ev[SP_NPHASE]);
   pr_stats(g, acc, stats, launches, regrows, ms);
+  return SP_OK;
+}
+
+// ---- triangle count (appendix listing "Dynamic TC") ---------------------------
+
+sp_status sp_tc_init(sp_graph *g, int64_t *count) {
+  if (!g || !count) return SP_EINVAL;
+  int launches = 0;
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_tc_sym_check(g, &launches);
+  sp_status rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  if (g->ctl_host->status != 0) {
+    g->tc_state = 0;
+    return (sp_status)g->ctl_host->status;
+  }
+  sp::launch_tc_static(g, &launches);
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaStreamSynchronize(g->stream);
+    return SP_ECUDA;
+  }
+  rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  g->tc_count = (long long)g->ctl_host->tc_static;
+  g->tc_state = 1;
+  *count = g->tc_count;
+  return SP_OK;
+}
+
+sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                            const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                            const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
+                            int64_t *count, sp_batch_stats *stats) {
+  if (!g || !count) return SP_EINVAL;
+  if (n_del < 0 || n_add < 0) return SP_EINVAL;
+  if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
+    return SP_EINVAL;
+  if (n_del + n_add > (1LL << 30)) return SP_EINVAL;
+  if (g->m + n_add > kMaxEdges) return SP_EINVAL;
+  if (g->tc_state != 1) return SP_ESTATE;
+  const long long nb = n_del + n_add, ni = 2 * nb;
+  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
+  if (rc != SP_OK) return rc;
+  auto &b = g->bb;
+  const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
+  rec(g, true, 0);
+  if (!inputs_on_device) {
+    cudaStream_t s = g->stream;
+    if (n_del) {
+      cudaMemcpyAsync(b.in_del_src, del_src, n_del * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_del_dst, del_dst, n_del * 4, cudaMemcpyHostToDevice, s);
+    }
+    if (n_add) {
+      cudaMemcpyAsync(b.in_add_src, add_src, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_dst, add_dst, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_w, add_w, n_add * 4, cudaMemcpyHostToDevice, s);
+    }
+    ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
+  }
+  int launches = 0, regrows = 0;
+  for (int attempt = 0;; ++attempt) {
+    sp::launch_ctl_reset(g, 0, &launches);
+    sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
+    sp::launch_segments(g, ni, &launches);
+    rec(g, true, 1);
+    sp::launch_count(g, ni, &launches);
+    sp::launch_tc_batch_sym(g, nb, &launches);     // before anything changes
+    rec(g, true, 2);
+    sp::launch_tc_delta(g, nb, 0, &launches);      // Decremental, old graph
+    rec(g, true, 3);
+    sp::launch_merge(g, ni, &launches);            // updateCSRDel + updateCSRAdd
+    rec(g, true, 4);
+    sp::launch_tc_delta(g, nb, 1, &launches);      // Incremental, new graph
+    rec(g, true, 5);
+    sp::launch_finish(g, &launches);
+    for (int i = 6; i <= SP_NPHASE; ++i) rec(g, true, i);
+    if (cudaGetLastError() != cudaSuccess) {
+      cudaStreamSynchronize(g->stream);
+      g->tc_state = 0;
+      return SP_ECUDA;
+    }
+    rc = read_ctl(g);
+    if (rc != SP_OK) return rc;
+    const Ctl &c = *g->ctl_host;
+    if (c.status != 0) return (sp_status)c.status;   // nothing changed
+    if (c.bad) {
+      g->tc_state = 0;
+      return SP_ECUDA;
+    }
+    if (c.need_grow == 0) break;
+    if (attempt >= 6) return SP_ENOMEM;
+    ++regrows;
+    if (c.need_grow & sp::kGrowPoolFwd) {
+      rc = sp::store_grow_pool(g, &g->fwd, (long long)c.pool_need[0] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    if (c.need_grow & sp::kGrowPoolRev) {
+      rc = sp::store_grow_pool(g, &g->rev, (long long)c.pool_need[1] + 1024);
+      if (rc != SP_OK) return rc;
+    }
+    rc = sp::ensure_owner_tables(g);
+    if (rc != SP_OK) return rc;
+  }
+  const Ctl &c = *g->ctl_host;
+  g->m += (long long)c.add_applied - (long long)c.del_applied;
+  if (c.add_applied + c.del_applied > 0) {
+    g->state = 0;      // distances no longer hold
+    g->pr_state = 0;   // nor do ranks
+  }
+  const u64 *d = c.tc_del, *a = c.tc_ins;
+  if (d[0] % 2 || d[1] % 4 || d[2] % 6 || a[0] % 2 || a[1] % 4 || a[2] % 6) {
+    g->tc_state = 0;   // cannot happen on a symmetric graph and batch
+    return SP_ECUDA;
+  }
+  g->tc_count += (long long)(a[0] / 2 + a[1] / 4 + a[2] / 6) -
+                 (long long)(d[0] / 2 + d[1] / 4 + d[2] / 6);
+  *count = g->tc_count;
+  fill_stats(g, c, stats, launches, regrows, ni, true);
+  if (stats) {
+    stats->affected = (int64_t)(d[0] + d[1] + d[2] + a[0] + a[1] + a[2]);   // sightings
+    stats->rounds_inval = stats->rounds_push = 0;
+  }
   return SP_OK;
 }
 

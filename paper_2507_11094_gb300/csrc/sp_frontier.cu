@@ -1587,23 +1587,20 @@ __global__ void k_pr_fill(float *p0, float *p1, float *acc, int n, float value) 
   }
 }
 
-// Pull body of a Jacobi step: each lane adds pr[u] / outdeg(u) over its run
-// of in-edges u -> v in slot order and adds the run's sum to acc[v].  A
-// vertex with at most kSmallDeg in-edges is one lane's single run, so its
-// sum is formed in in-neighbour order, as a sequential loop would.
+// Pull body of a Jacobi step: each lane adds the terms pr[u] / outdeg(u)
+// (kept per vertex in `contrib`, rounded exactly as a division per edge
+// would be) over its run of in-edges u -> v in slot order and adds the run's
+// sum to acc[v].  A vertex with at most kSmallDeg in-edges is one lane's
+// single run, so its sum is formed in in-neighbour order, as a sequential
+// loop would.
 struct PrOp {
-  const float *pr;
+  const float *contrib;
   float *acc;
-  const RowMeta *frow;
   u64 n_edges = 0, n_enq = 0;
   int range_err = 0;
 
   __device__ __forceinline__ u32 vdata(u32) { return 0; }
-  __device__ __forceinline__ u64 load(int2 e) {
-    const u32 bits = __float_as_uint(__ldcg(pr + e.x));
-    const u32 deg = (u32)__ldg(&frow[e.x].deg);
-    return ((u64)deg << 32) | bits;
-  }
+  __device__ __forceinline__ u64 load(int2 e) { return __float_as_uint(__ldcg(contrib + e.x)); }
   __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
                                       const int2 *, const u64 *sx) {
     u32 bv = kNoEdge;
@@ -1617,8 +1614,7 @@ struct PrOp {
           bv = ov[k];
           sum = 0.0f;
         }
-        const float term = __fdiv_rn(__uint_as_float((u32)sx[k]), (float)(u32)(sx[k] >> 32));
-        sum = __fadd_rn(sum, term);
+        sum = __fadd_rn(sum, __uint_as_float((u32)sx[k]));
       }
     }
     if (bv != kNoEdge) atomicAdd(acc + bv, sum);
@@ -1628,6 +1624,7 @@ struct PrOp {
 struct PrArgs {
   LoopArgs la;
   float *pr[2];
+  float *contrib[2];   // pr / outdeg, kept beside each rank buffer
   float *acc;
   float base, damping;
   double beta;
@@ -1662,9 +1659,23 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_pr(PrArgs p) {
   u64 n_edges = 0;
   u32 it = 0, cur = 0;
   bool stop = false;
+  {
+    // the terms of every vertex (out-degrees may have changed since the
+    // last phase); both rank buffers agree here
+    const u32 gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (u32 v = gt; v < (u32)a.n; v += nt) {
+      const int deg = __ldg(&a.fwd.row[v].deg);
+      const float t = deg > 0 ? __fdiv_rn(__ldcg(p.pr[0] + v), (float)deg) : 0.0f;
+      p.contrib[0][v] = t;
+      p.contrib[1][v] = t;
+    }
+    target += gridDim.x;
+    stop = grid_sync(bar, target, c, a.lim);
+  }
   for (;;) {
+    if (stop) break;
     // pass 1: in-edge sums
-    PrOp op{p.pr[cur], p.acc, a.fwd.row};
+    PrOp op{p.contrib[cur], p.acc};
     for (u32 i = gw; i < items; i += nw) {
       if (i < sgroups) process_small(op, a.asv, ns, i, a.rev, a.n, c);
       else process_chunk(op, a.aent, a.aown, ne, nedge, i - sgroups, a.rev, a.n, c);
@@ -1685,6 +1696,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_pr(PrArgs p) {
       const float val = __fadd_rn(p.base, __fmul_rn(p.damping, __ldcg(p.acc + v)));
       diff += fabs((double)val - (double)__ldcg(pc + v));
       pn[v] = val;
+      const int deg = __ldg(&a.fwd.row[v].deg);
+      p.contrib[cur ^ 1][v] = deg > 0 ? __fdiv_rn(val, (float)deg) : 0.0f;
       p.acc[v] = 0.0f;
     }
 #pragma unroll
@@ -1868,6 +1881,8 @@ cudaError_t launch_pr(sp_graph *g, int *launches) {
   p.la = make_args(g);
   p.pr[0] = g->pr[0];
   p.pr[1] = g->pr[1];
+  p.contrib[0] = g->prc[0];
+  p.contrib[1] = g->prc[1];
   p.acc = g->pracc;
   p.base = (1.0f - g->pr_damping) / (float)g->n;
   p.damping = g->pr_damping;

@@ -132,12 +132,16 @@ struct sp_graph {
   // PageRank state (allocated by sp_pr_init): ranks in two buffers that
   // agree between calls, the pull accumulators, phase flags and settings
   float *pr[2] = {nullptr, nullptr};
+  float *prc[2] = {nullptr, nullptr};   // pr / outdeg (Jacobi work buffers)
   float *pracc = nullptr;
   sp::u32 *prflag = nullptr;
   sp::u32 prtag = 0;
   int pr_state = 0;            // 0 = no ranks, 1 = valid
   float pr_damping = 0.85f, pr_beta = 1e-6f;
   int pr_max_iter = 100;
+  // triangle count (sp_tc_init): the current count
+  long long tc_count = 0;
+  int tc_state = 0;            // 0 = no count, 1 = valid
   int32_t delta_user = 0;
   int32_t jump_round_user = 0;
   int32_t local_edges_user = 4096;
@@ -188,6 +192,11 @@ void launch_pull(sp_graph *g, int *launches);
 void launch_add(sp_graph *g, long long n_items, int *launches);
 cudaError_t launch_push(sp_graph *g, int *launches);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+// sp_tc.cu
+void launch_tc_sym_check(sp_graph *g, int *launches);
+void launch_tc_static(sp_graph *g, int *launches);
+void launch_tc_batch_sym(sp_graph *g, long long nb, int *launches);
+void launch_tc_delta(sp_graph *g, long long nb, int kind, int *launches);
 // PageRank
 cudaError_t launch_flag(sp_graph *g, const int *dst, long long n, int *launches);
 void launch_pr_fill(sp_graph *g, float value, int *launches);

@@ -104,6 +104,10 @@ struct Ctl {
   alignas(128) double prd2;
   u32 pr_iters;
   u32 zcnt;              // selected vertices without in-edges (PageRank)
+  // triangle count: staticTC, and the sightings of the deletions' and the
+  // insertions' corrections by number of updated edges (1, 2, 3)
+  alignas(128) u64 tc_static;
+  u64 tc_del[3], tc_ins[3];
   // vertices still jumping after each pointer-jumping pass, triple-buffered
   alignas(128) u32 jcnt0;
   alignas(128) u32 jcnt1;

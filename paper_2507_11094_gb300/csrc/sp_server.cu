@@ -10,6 +10,7 @@
 // its distances recomputed from its source.  Each graph's persistent loops
 // use a share of the SMs so that several can be resident together.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -68,6 +69,7 @@ struct sp_server {
   int64_t next_id = 1, use_counter = 0, inflight = 0, loading = 0;
   int64_t resident = 0, max_resident = 0, loads = 0, evictions = 0;
   int64_t batches = 0, queries = 0, updates = 0;
+  std::atomic<int64_t> recovered{0};
   Clock::time_point t0 = Clock::now();
 
   double now_ms() const {
@@ -211,6 +213,12 @@ void sp_server::worker(int slot) {
         rc = sp_apply_batch(ge->g, (int64_t)r->ds.size(), r->ds.data(), r->dd.data(),
                             (int64_t)r->as.size(), r->as.data(), r->ad.data(), r->aw.data(), 0,
                             nullptr);
+        if (rc == SP_ETIMEOUT) {
+          // a device bound stopped the repair after the edges were merged:
+          // recompute the distances from the source (exact), once
+          rc = sp_sssp_init(ge->g, ge->source, nullptr);
+          if (rc == SP_OK) ++recovered;
+        }
       } else {
         r->qout.assign(r->qv.size(), 0);
         rc = sp_query(ge->g, (int32_t)r->qv.size(), r->qv.data(), r->qout.data(), 0);
@@ -394,6 +402,7 @@ sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out) {
   int32_t res = 0;
   for (auto &g : s->graphs) res += g->g ? 1 : 0;
   out->resident_graphs = res;
+  out->recoveries = s->recovered.load();
   return SP_OK;
 }
 

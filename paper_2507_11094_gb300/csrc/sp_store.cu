@@ -210,6 +210,9 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->prd0 = c->prd1 = c->prd2 = 0.0;
   c->pr_iters = 0;
   c->zcnt = 0;
+  c->tc_static = 0;
+  c->tc_del[0] = c->tc_del[1] = c->tc_del[2] = 0;
+  c->tc_ins[0] = c->tc_ins[1] = c->tc_ins[2] = 0;
   c->lres = c->lcur = c->lround = c->lcap = 0;
   c->lbeat = 0;
   c->mcnt = 0;

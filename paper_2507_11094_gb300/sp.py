@@ -93,7 +93,7 @@ class ServerStats(ctypes.Structure):
                 ("loads", ctypes.c_int64), ("evictions", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("queries", ctypes.c_int64),
                 ("updates", ctypes.c_int64), ("resident_graphs", ctypes.c_int32),
-                ("registered_graphs", ctypes.c_int32)]
+                ("registered_graphs", ctypes.c_int32), ("recoveries", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,6 +124,9 @@ SIGNATURES = {
     "sp_pr_init": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, _I32, _P]),
     "sp_pr_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int, _P]),
     "sp_pr_get": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "sp_tc_init": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "sp_tc_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64), _P]),
     "sp_sssp_init_multi": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P]),
     "sp_reserve": (ctypes.c_int, [_P, _I64]),
     "sp_async_result_bytes": (ctypes.c_size_t, []),
@@ -437,13 +440,39 @@ class Graph:
         _check(load().sp_pr_get(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), "sp_pr_get")
         return out
 
+    # -- triangle count ------------------------------------------------------
+    def tc_init(self) -> int:
+        """staticTC of a symmetric graph."""
+        c = ctypes.c_int64()
+        _check(load().sp_tc_init(self._h, ctypes.byref(c)), "sp_tc_init")
+        return int(c.value)
+
+    def tc_apply_batch(self, del_src, del_dst, add_src, add_dst, add_w, stats: bool = False):
+        """DynTC for one symmetric batch; returns the new count (and stats)."""
+        arr = _Arrays([del_src, del_dst, add_src, add_dst, add_w], [np.int32] * 5)
+        size = (lambda a: int(a.numel())) if arr.on_device else (lambda a: int(a.size))
+        nd, na = size(arr.keep[0]), size(arr.keep[2])
+        if size(arr.keep[1]) != nd or size(arr.keep[3]) != na or size(arr.keep[4]) != na:
+            raise SpError(SP_EINVAL, "batch array sizes")
+        st = BatchStats() if stats else None
+        c = ctypes.c_int64()
+        rc = load().sp_tc_apply_batch(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
+                                      arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
+                                      ctypes.byref(c), ctypes.byref(st) if st else None)
+        _check(rc, "sp_tc_apply_batch")
+        return (int(c.value), st) if stats else int(c.value)
+
+    def tc_apply(self, batch, stats: bool = False):
+        return self.tc_apply_batch(batch.del_src, batch.del_dst, batch.add_src, batch.add_dst,
+                                   batch.add_w, stats=stats)
+
     def loop_counters(self) -> dict:
         """Loop counters of the last call (tuning aid)."""
-        out = np.zeros(9, dtype=np.int64)
-        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 9),
+        out = np.zeros(10, dtype=np.int64)
+        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 10),
                "sp_loop_counters")
         keys = ("rounds_push", "local_rounds", "local_episodes", "splits", "far_moves",
-                "rounds_inval", "jumps", "local_ns", "push_ns")
+                "rounds_inval", "jumps", "local_ns", "push_ns", "timeout")
         return dict(zip(keys, (int(x) for x in out)))
 
     def set_local_rounds(self, max_edges: int):
