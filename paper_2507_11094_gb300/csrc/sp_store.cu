@@ -322,7 +322,6 @@ __global__ void k_seg_emit(const u64 *__restrict__ keys, const u32 *__restrict__
 // batch: count pass (which updates apply, new row sizes, where rows go)
 // --------------------------------------------------------------------------
 
-constexpr int kElemPerLane = kChunk / 32;   // merge elements per lane
 
 // First slot j in [0, deg) of a sorted row with row[j].x >= c.
 __device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) {
@@ -330,15 +329,6 @@ __device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) 
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (__ldg(&row[mid].x) < c) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// First item index in [lo, hi) whose key >= k.
-__device__ __forceinline__ u32 items_lower_bound(const u64 *keys, u32 lo, u32 hi, u64 k) {
-  while (lo < hi) {
-    u32 mid = (lo + hi) >> 1;
-    if (keys[mid] < k) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
@@ -362,7 +352,7 @@ struct CountArgs {
 };
 
 // Rows with at least kBigRow old entries are merged strip by strip
-// (k_merge_big); smaller ones element by element (k_merge).
+// (k_merge_big); smaller ones a warp per row (k_merge).
 constexpr int kBigRow = 256;
 constexpr int kStrip = 256;
 
@@ -443,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
     const u32 si = base + threadIdx.x;
     bool ok = si < nseg;
     Seg sg;
-    u32 tot = 0, nstr = 0;
+    u32 nstr = 0;
     if (ok) {
       sg = a.seg[si];
       if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
@@ -481,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
       }
       a.seg[si] = sg;
       if (rm.deg >= kBigRow) nstr = (u32)((rm.deg + kStrip - 1) / kStrip);
-      else tot = (u32)rm.deg + (sg.end - sg.first);
+
       ++touched;
       slots += (u64)rm.deg + (u64)new_deg;
     }
@@ -494,25 +484,6 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
       const u32 sb = scratch[35] + se;
       __syncthreads();
       for (u32 k = 0; k < nstr; ++k) a.strips[sb + k] = make_int2((int)si, (int)(k * kStrip));
-    }
-    // reserve merge elements of small rows: one packed atomic per block
-    const u32 cnt = (ok && tot > 0) ? 1u : 0u;
-    u32 ctot, ttot;
-    const u32 ce = block_excl_scan_u32(cnt, scratch, &ctot);
-    const u32 te = block_excl_scan_u32(tot, scratch, &ttot);
-    if (threadIdx.x == 0) {
-      const u64 b = ctot ? atomicAdd((unsigned long long *)&c->mcnt, ((u64)ctot << 32) | ttot) : 0;
-      scratch[32] = (u32)(b >> 32);
-      scratch[33] = (u32)b;
-    }
-    __syncthreads();
-    const u32 bhi = scratch[32], blo = scratch[33];
-    __syncthreads();
-    if (cnt) {
-      const u32 slot = bhi + ce, eb = blo + te;
-      a.ment[slot] = make_int2((int)si, (int)eb);
-      const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + tot - 1) / kChunk;
-      for (u32 ch = c0; ch <= c1; ++ch) a.mown[ch] = slot;
     }
   }
   __shared__ u64 sums[3];
@@ -557,152 +528,73 @@ __device__ __forceinline__ bool merge_enabled(Ctl *c) {
 //                               - #applied deletions with col < c
 //                               + #applied insertions before it.
 // Items are sorted by (col, deletion before insertion), so "col < c" is an
-// item index range [first, i).  Elements are independent: the queue spreads
-// them over all warps, kElemPerLane consecutive elements per lane, and each
-// lane walks its run segment by segment.
+// item index range [first, i).  Rows below kBigRow old entries take one warp
+// each: the lanes read 32 consecutive old entries at a time (one coalesced
+// 256-byte load), find their place among the row's items by binary search
+// and write 32 mostly consecutive slots; then the lanes place the applied
+// insertions.  The warp's first lane publishes the row's new metadata.
 __global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
   Ctl *c = a.ctl;
   if (!merge_enabled(c)) return;
   const int lane = threadIdx.x & 31;
-  const u64 pk = ld_cg_u64(&c->mcnt);
-  const u32 ne = (u32)(pk >> 32), nel = (u32)pk;
-  const u32 nch = (nel + kChunk - 1) / kChunk;
+  const u32 nseg = ld_cg_u32(&c->n_seg);
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
   const u64 cmask = (1ull << a.bits) - 1;
-  const u64 kmask = ~((2ull << a.bits) - 1);
   bool bad = false;
-  for (u32 ch = gw; ch < nch; ch += nw) {
-    const u32 e0 = ch * kChunk;
-    const u32 e_end = e0 + kChunk < nel ? e0 + kChunk : nel;
-    const u32 jw = __ldcg(a.mown + ch);
-    // owner of this lane's first element: search a window of 32 queue entries
-    const u32 wj = jw + lane;
-    const u32 web = wj < ne ? (u32)__ldcg(&a.ment[wj].y) : 0xFFFFFFFFu;
-    const u32 ebeg = e0 + (u32)(kElemPerLane * lane);
-    int o = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const u32 ebc = __shfl_sync(kFull, web, (o + step) & 31);
-      if (o + step < 32 && ebc <= ebeg) o += step;
+  for (u32 si = gw; si < nseg; si += nw) {
+    const Seg sg = a.seg[si];
+    if (sg.old_deg >= kBigRow) continue;   // strips
+    const Store &st = a.st[sg.dir];
+    const int2 *old = st.adj + sg.old_start;
+    int2 *dst = st.adj + sg.dest;
+    if (lane == 0) {
+      RowMeta nm;
+      nm.start = sg.dest;
+      nm.deg = sg.new_deg;
+      nm.cap = sg.new_cap;
+      st.row[sg.row] = nm;
+      st.alt[sg.row] = sg.new_alt;
     }
-    if (ebeg >= e_end) continue;
-    // every entry holds >= 1 element and entries after jw start inside this
-    // chunk, so the entry holding any element of the chunk is below jw + 256
-    const u32 slot_hi = (jw + kChunk < ne ? jw + kChunk : ne) - 1;
-    u32 slot_lo = jw + (u32)o;
-    const u32 eL = ebeg + kElemPerLane < e_end ? ebeg + kElemPerLane : e_end;
-    u32 e = ebeg;
-    while (e < eL) {
-      // entry holding e: last slot in [slot_lo, slot_hi] whose first element <= e
-      u32 slot = slot_lo;
-      if (slot < slot_hi && (u32)__ldcg(&a.ment[slot + 1].y) <= e) {
-        u32 lo = slot + 1, hi = slot_hi;
+    for (int j0 = 0; j0 < sg.old_deg; j0 += 32) {
+      const int j = j0 + lane;
+      if (j < sg.old_deg) {
+        const int2 en = old[j];
+        const u64 kc = sg.prefix | ((u64)(unsigned)en.x << 1);
+        u32 lo = sg.first, hi = sg.end;
         while (lo < hi) {
-          const u32 mid = (lo + hi + 1) >> 1;
-          if ((u32)__ldcg(&a.ment[mid].y) <= e) lo = mid; else hi = mid - 1;
+          const u32 mid = (lo + hi) >> 1;
+          if (a.keys[mid] < kc) lo = mid + 1; else hi = mid;
         }
-        slot = lo;
-      }
-      const int2 en0 = __ldcg(a.ment + slot);
-      const Seg sg = a.seg[en0.x];
-      const Store &st = a.st[sg.dir];
-      const int2 *old = st.adj + sg.old_start;
-      int2 *dst = st.adj + sg.dest;
-      const u64 prefix = sg.prefix;
-      const u64 base_pref = sg.base_pref;
-      const u32 eb = (u32)en0.y;
-      const u32 tot = (u32)sg.old_deg + (sg.end - sg.first);
-      const u32 r_end = eL < eb + tot ? eL : eb + tot;
-      if (e == eb) {  // first element of the row publishes the new metadata
-        RowMeta nm;
-        nm.start = sg.dest;
-        nm.deg = sg.new_deg;
-        nm.cap = sg.new_cap;
-        st.row[sg.row] = nm;
-        st.alt[sg.row] = sg.new_alt;
-      }
-      // old entries of the run, loaded together
-      const u32 j0 = e - eb;
-      const u32 jl = r_end - eb < (u32)sg.old_deg ? r_end - eb : (u32)sg.old_deg;
-      int2 en[kElemPerLane];
-#pragma unroll
-      for (int t = 0; t < kElemPerLane; ++t)
-        en[t] = (j0 + t < jl) ? old[j0 + t] : make_int2(0, 0);
-      if (j0 < jl) {
-        // item cursor: first item with col >= the run's first col, then walk
-        u32 ic;
-        {
-          u32 lo = sg.first, hi = sg.end;
-          const u64 k0 = prefix | ((u64)(unsigned)en[0].x << 1);
-          while (lo < hi) {
-            const u32 mid = (lo + hi) >> 1;
-            if (a.keys[mid] < k0) lo = mid + 1; else hi = mid;
-          }
-          ic = lo;
-        }
-        // fast path: no batch item among this run's cols, so every entry
-        // keeps its order and moves by one shift
-        const u32 nl = jl - j0;
-        int lastc = en[0].x;
-#pragma unroll
-        for (int t = 1; t < kElemPerLane; ++t)
-          if (t < (int)nl) lastc = en[t].x;
-        const u64 knext = ic < sg.end ? a.keys[ic] : ~0ull;
-        if ((prefix | ((u64)(unsigned)lastc << 1)) < knext) {
-          const u64 pp = a.item_pref[ic] - base_pref;
-          const int shift = (int)(u32)(pp >> 32) - (int)(u32)pp;
-          const int p0 = (int)j0 + shift;
-          if (p0 >= 0 && p0 + (int)nl <= sg.new_deg) {
-#pragma unroll
-            for (int t = 0; t < kElemPerLane; ++t)
-              if (t < (int)nl) dst[p0 + t] = en[t];
-          } else {
-            bad = true;
-          }
-        } else
-#pragma unroll
-        for (int t = 0; t < kElemPerLane; ++t) {
-          if (j0 + t < jl) {
-            const u64 kc = prefix | ((u64)(unsigned)en[t].x << 1);
-            while (ic < sg.end && a.keys[ic] < kc) ++ic;
-            const bool del = ic < sg.end && a.keys[ic] == kc && (a.flags[ic] & 1);
-            if (!del) {
-              const u64 pp = a.item_pref[ic] - base_pref;
-              const int pos = (int)(j0 + t) - (int)(u32)pp + (int)(u32)(pp >> 32);
-              if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
-              else bad = true;
-            }
-          }
-        }
-      }
-      // batch items of the run: applied insertions
-      const u32 i_lo = (e - eb > (u32)sg.old_deg ? e - eb : (u32)sg.old_deg) - sg.old_deg;
-      const u32 i_hi = r_end - eb > (u32)sg.old_deg ? r_end - eb - sg.old_deg : 0u;
-      for (u32 ii = i_lo; ii < i_hi; ++ii) {
-        const u32 i = sg.first + ii;
-        const u64 key = a.keys[i];
-        if ((key & 1) && (a.flags[i] & 1)) {
-          const int col = (int)((key >> 1) & cmask);
-          int lo = 0, hi = sg.old_deg;   // old entries with col < this col
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (old[mid].x < col) lo = mid + 1; else hi = mid;
-          }
-          u32 l2 = sg.first, h2 = i;     // items with col < this col
-          const u64 k0 = prefix | ((u64)(unsigned)col << 1);
-          while (l2 < h2) {
-            const u32 mid = (l2 + h2) >> 1;
-            if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
-          }
-          const u64 p0 = a.item_pref[l2] - base_pref, pi = a.item_pref[i] - base_pref;
-          const int pos = lo - (int)(u32)p0 + (int)(u32)(pi >> 32);
-          if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
+        const bool del = lo < sg.end && a.keys[lo] == kc && (a.flags[lo] & 1);
+        if (!del) {
+          const u64 pp = a.item_pref[lo] - sg.base_pref;
+          const int pos = j - (int)(u32)pp + (int)(u32)(pp >> 32);
+          if (pos >= 0 && pos < sg.new_deg) dst[pos] = en;
           else bad = true;
         }
       }
-      e = r_end;
-      slot_lo = slot + 1;
+    }
+    for (u32 i = sg.first + lane; i < sg.end; i += 32) {
+      const u64 key = a.keys[i];
+      if ((key & 1) && (a.flags[i] & 1)) {
+        const int col = (int)((key >> 1) & cmask);
+        int lo = 0, hi = sg.old_deg;   // old entries with col < this col
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (old[mid].x < col) lo = mid + 1; else hi = mid;
+        }
+        u32 l2 = sg.first, h2 = i;     // items with col < this col
+        const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
+        while (l2 < h2) {
+          const u32 mid = (l2 + h2) >> 1;
+          if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
+        }
+        const u64 p0 = a.item_pref[l2] - sg.base_pref, pi = a.item_pref[i] - sg.base_pref;
+        const int pos = lo - (int)(u32)p0 + (int)(u32)(pi >> 32);
+        if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
+        else bad = true;
+      }
     }
   }
   if (bad) atomicExch(&c->bad, 1);
