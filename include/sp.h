@@ -473,6 +473,17 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
                             int inputs_on_device, int64_t *count, sp_batch_stats *stats);
 
 /*
+ * sp_apply_batch runs its ~35 kernels as a cached CUDA graph when a batch has
+ * the same shape (deletion and insertion counts, stats or not) as the one
+ * before it: the inputs are copied to internal buffers and one graph launch
+ * replaces the kernel launches.  The graph is rebuilt when a buffer or a
+ * setting changes.  on = 0 turns it off (every call launches kernels one by
+ * one); the default is 1.  Results do not depend on it.  Requires a
+ * non-default stream (graphs are never used on the legacy stream).
+ */
+sp_status sp_set_batch_graphs(sp_graph *g, int32_t on);
+
+/*
  * Loop counters of the last call, for tuning: out[0] push rounds, [1] of
  * them run by a single block, [2] single-block episodes, [3] near-far
  * splits, [4] far-pile entries moved back, [5] invalidation rounds, [6] of
@@ -482,6 +493,10 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
  * written; the figures are those of the last synchronous call.
  */
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
+
+/* Name of the CUDA error behind the handle's last SP_ECUDA from a failed
+ * launch ("cudaSuccess" if none); static storage. */
+const char *sp_last_cuda_error(const sp_graph *g);
 
 /* Static name of a status code. */
 const char *sp_status_str(sp_status s);

@@ -75,6 +75,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
+    ++g->gen;
     if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
         !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.ment || !b.tmp) {
       return SP_ENOMEM;
@@ -90,6 +91,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.in_add_src = (int *)al.get(c * 4); b.in_add_dst = (int *)al.get(c * 4);
     b.in_add_w = (int *)al.get(c * 4);
     b.cap_in = c;
+    ++g->gen;
     if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
       return SP_ENOMEM;
   }
@@ -100,6 +102,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     g->al.put(b.strips, (size_t)b.strips_cap * 8);
     b.strips = (int2 *)g->al.get((size_t)c * 8);
     b.strips_cap = b.strips ? c : 0;
+    ++g->gen;
     if (!b.strips) return SP_ENOMEM;
   }
   // merge chunk-owner table: elements = old entries of touched rows (<= 2m)
@@ -110,6 +113,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     g->al.put(b.mown, (size_t)b.mown_cap * 4);
     b.mown = (u32 *)g->al.get((size_t)c * 4);
     b.mown_cap = b.mown ? c : 0;
+    ++g->gen;
     if (!b.mown) return SP_ENOMEM;
   }
   return SP_OK;
@@ -150,13 +154,41 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
   st->ms_total = 0.f;
   if (timed) {
     for (int i = 0; i < SP_NPHASE; ++i)
-      cudaEventElapsedTime(&st->ms_phase[i], g->ev[i], g->ev[i + 1]);
-    cudaEventElapsedTime(&st->ms_total, g->ev[0], g->ev[SP_NPHASE]);
+      if (cudaEventElapsedTime(&st->ms_phase[i], g->ev[i], g->ev[i + 1]) != cudaSuccess)
+        st->ms_phase[i] = 0.f;
+    if (cudaEventElapsedTime(&st->ms_total, g->ev[0], g->ev[SP_NPHASE]) != cudaSuccess)
+      st->ms_total = 0.f;
+    cudaGetLastError();
   }
 }
 
+// Phase boundary i of a batch: records timing event i, or, while the
+// pipeline is being captured, closes the graph of phase i - 1 and opens the
+// one of phase i.
 void rec(sp_graph *g, bool timed, int i) {
+  if (g->capturing >= 0) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamEndCapture(g->stream, &gr) == cudaSuccess && g->capturing < SP_NPHASE)
+      g->bg_graph[g->capturing] = gr;
+    else if (gr)
+      cudaGraphDestroy(gr);
+    g->capturing = i;
+    if (i < SP_NPHASE && cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) !=
+                             cudaSuccess)
+      g->capturing = -2;   // capture failed: the caller falls back
+    return;
+  }
   if (timed) cudaEventRecord(g->ev[i], g->stream);
+}
+
+void drop_batch_graphs(sp_graph *g) {
+  for (int i = 0; i < SP_NPHASE; ++i) {
+    if (g->bg_exec[i]) cudaGraphExecDestroy(g->bg_exec[i]);
+    if (g->bg_graph[i]) cudaGraphDestroy(g->bg_graph[i]);
+    g->bg_exec[i] = nullptr;
+    g->bg_graph[i] = nullptr;
+  }
+  g->bg_ready = false;
 }
 
 sp_status read_ctl(sp_graph *g) {
@@ -179,6 +211,7 @@ void set_limits(sp_graph *g) {
   g->lim.delta = (u32)std::max(0, g->delta_user);
   g->lim.jump_round = g->jump_round_user;
   g->lim.local_edges = (u32)g->local_edges_user;
+  ++g->gen;
 }
 
 sp_status status_of_repair(sp_graph *g, const Ctl &c) {
@@ -301,6 +334,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->prc[0], n * 4); al.put(g->prc[1], n * 4);
   al.put(g->pracc, n * 4); al.put(g->prflag, n * 4);
   al.put(g->ctl, sizeof(Ctl));
+  drop_batch_graphs(g);
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   for (auto &e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -477,6 +511,7 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats) {
   sp::launch_finish(g, &launches);
   rec(g, timed, SP_NPHASE);
   if (e != cudaSuccess) {
+    g->last_err = (int)e;
     cudaGetLastError();
     cudaStreamSynchronize(g->stream);
     g->state = 2;
@@ -518,21 +553,32 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   if (g->state != 1) return SP_ESTATE;
   const long long nb = n_del + n_add, ni = 2 * nb;
   const bool timed = stats != nullptr;
-  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
+  // the same batch shape twice in a row: the pipeline runs as a cached CUDA
+  // graph (one launch instead of ~35), reading the inputs from the staging
+  // buffers
+  const bool repeat = n_del == g->last_nd && n_add == g->last_na && (int)timed == g->last_timed;
+  g->last_nd = n_del;
+  g->last_na = n_add;
+  g->last_timed = (int)timed;
+  const bool use_graph = g->batch_graphs && g->stream && nb > 0 && repeat;
+  sp_status rc = ensure_batch_buffers(g, ni,
+                                      inputs_on_device && !use_graph ? 0 : std::max(n_del, n_add));
   if (rc != SP_OK) return rc;
   auto &b = g->bb;
   const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
   rec(g, timed, 0);
-  if (!inputs_on_device) {
+  if (!inputs_on_device || use_graph) {
     cudaStream_t s = g->stream;
+    const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice
+                                                 : cudaMemcpyHostToDevice;
     if (n_del) {
-      cudaMemcpyAsync(b.in_del_src, del_src, n_del * 4, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(b.in_del_dst, del_dst, n_del * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_del_src, del_src, n_del * 4, kind, s);
+      cudaMemcpyAsync(b.in_del_dst, del_dst, n_del * 4, kind, s);
     }
     if (n_add) {
-      cudaMemcpyAsync(b.in_add_src, add_src, n_add * 4, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(b.in_add_dst, add_dst, n_add * 4, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(b.in_add_w, add_w, n_add * 4, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(b.in_add_src, add_src, n_add * 4, kind, s);
+      cudaMemcpyAsync(b.in_add_dst, add_dst, n_add * 4, kind, s);
+      cudaMemcpyAsync(b.in_add_w, add_w, n_add * 4, kind, s);
     }
     ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
   }
@@ -540,8 +586,54 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   for (int attempt = 0;; ++attempt) {
     launches = 0;
     if (attempt) rec(g, timed, 0);
-    cudaError_t e = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &launches);
+    cudaError_t e = cudaSuccess;
+    bool replayed = false;
+    if (use_graph && attempt == 0) {
+      if (!(g->bg_ready && g->bg_gen == g->gen && g->bg_nd == n_del && g->bg_na == n_add &&
+            g->bg_timed == (int)timed)) {
+        drop_batch_graphs(g);
+        int cl = 0;
+        if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          g->capturing = 0;   // rec() splits the capture at every phase boundary
+          const cudaError_t ce = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &cl);
+          bool ok = ce == cudaSuccess && g->capturing == SP_NPHASE;
+          if (g->capturing >= 0 && g->capturing < SP_NPHASE) {   // never expected
+            cudaGraph_t gr = nullptr;
+            cudaStreamEndCapture(g->stream, &gr);
+            if (gr) cudaGraphDestroy(gr);
+            ok = false;
+          }
+          g->capturing = -1;
+          for (int i = 0; ok && i < SP_NPHASE; ++i)
+            ok = g->bg_graph[i] &&
+                 cudaGraphInstantiate(&g->bg_exec[i], g->bg_graph[i], 0) == cudaSuccess;
+          if (ok) {
+            g->bg_ready = true;
+            g->bg_gen = g->gen;
+            g->bg_nd = n_del;
+            g->bg_na = n_add;
+            g->bg_timed = (int)timed;
+            g->bg_launches = cl;
+          } else {
+            drop_batch_graphs(g);
+          }
+        }
+        g->capturing = -1;
+        cudaGetLastError();
+      }
+      if (g->bg_ready) {
+        for (int i = 0; i < SP_NPHASE && e == cudaSuccess; ++i) {
+          if (i) rec(g, timed, i);
+          e = cudaGraphLaunch(g->bg_exec[i], g->stream);
+        }
+        rec(g, timed, SP_NPHASE);
+        launches = g->bg_launches;
+        replayed = true;
+      }
+    }
+    if (!replayed) e = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &launches);
     if (e != cudaSuccess) {
+      g->last_err = (int)e;
       cudaGetLastError();
       cudaStreamSynchronize(g->stream);
       g->state = 2;
@@ -613,6 +705,7 @@ sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
   sp_status rc = read_ctl(g);
   g->al.put(src_d, (size_t)k * 4);
   if (e != cudaSuccess) {
+    g->last_err = (int)e;
     cudaGetLastError();
     g->state = 2;
     return SP_ECUDA;
@@ -651,6 +744,7 @@ sp_status sp_apply_batch_async(sp_graph *g, int64_t n_del, const int32_t *del_sr
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(result, g->ctl, sizeof(Ctl), cudaMemcpyDefault, g->stream);
   if (e != cudaSuccess) {
+    g->last_err = (int)e;
     cudaGetLastError();
     return SP_ECUDA;
   }
@@ -748,6 +842,7 @@ sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, cons
     sp::launch_finish(g, launches);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
+      g->last_err = (int)e;
       cudaGetLastError();
       cudaStreamSynchronize(g->stream);
       return SP_ECUDA;
@@ -791,6 +886,7 @@ sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, cons
   cudaError_t e = sp::launch_pr(g, launches);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
+    g->last_err = (int)e;
     cudaGetLastError();
     cudaStreamSynchronize(g->stream);
     return SP_ECUDA;
@@ -862,6 +958,7 @@ sp_status sp_pr_init(sp_graph *g, float damping, float beta, int32_t max_iter,
   rec(g, true, SP_NPHASE);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
+    g->last_err = (int)e;
     cudaGetLastError();
     cudaStreamSynchronize(g->stream);
     g->pr_state = 0;
@@ -1113,6 +1210,18 @@ sp_status sp_query(sp_graph *g, int32_t k, const int32_t *vertices, int32_t *dis
 sp_status sp_set_loop_blocks(sp_graph *g, int32_t blocks) {
   if (!g || blocks < 0) return SP_EINVAL;
   g->loop_blocks_user = blocks;
+  ++g->gen;
+  return SP_OK;
+}
+
+const char *sp_last_cuda_error(const sp_graph *g) {
+  if (!g) return "invalid handle";
+  return cudaGetErrorName((cudaError_t)g->last_err);
+}
+
+sp_status sp_set_batch_graphs(sp_graph *g, int32_t on) {
+  if (!g || on < 0 || on > 1) return SP_EINVAL;
+  g->batch_graphs = on;
   return SP_OK;
 }
 

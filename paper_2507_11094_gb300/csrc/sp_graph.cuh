@@ -144,6 +144,22 @@ struct sp_graph {
   int tc_state = 0;            // 0 = no count, 1 = valid
   int32_t delta_user = 0;
   int32_t jump_round_user = 0;
+  // cached CUDA graph of the batch pipeline (sp_apply_batch): replayed when
+  // the same batch shape repeats; `gen` changes whenever a buffer moves or a
+  // setting changes, which invalidates the cache
+  unsigned long long gen = 1;
+  int last_err = 0;                      // cudaError_t of the last failed launch
+  int batch_graphs = 1;                  // 0 = never capture
+  // one graph per phase, so that timing events can be recorded between them
+  cudaGraph_t bg_graph[SP_NPHASE] = {};
+  cudaGraphExec_t bg_exec[SP_NPHASE] = {};
+  bool bg_ready = false;
+  int capturing = -1;                    // phase being captured (-1: none)
+  unsigned long long bg_gen = 0;
+  long long bg_nd = -1, bg_na = -1;
+  int bg_timed = -1, bg_launches = 0;
+  long long last_nd = -1, last_na = -1;
+  int last_timed = -1;
   int32_t local_edges_user = 4096;
   long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device

@@ -866,6 +866,7 @@ sp_status store_export(sp_graph *g, const Store *st, long long *row_off_d, int *
 }
 
 sp_status store_grow_pool(sp_graph *g, Store *st, long long min_pool_slots) {
+  ++g->gen;
   long long pool = st->slots - st->main_slots;
   long long np = std::max(2 * pool, round_up4(min_pool_slots));
   long long slots = st->main_slots + np;
@@ -892,6 +893,7 @@ sp_status ensure_owner_tables(sp_graph *g) {
     ok = ok && g->qown[b];
   }
   g->aown = (u32 *)g->al.get((size_t)c * 4);
+  ++g->gen;
   g->own_cap = c;
   return (ok && g->aown) ? SP_OK : SP_ENOMEM;
 }

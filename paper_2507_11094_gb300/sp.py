@@ -120,6 +120,7 @@ SIGNATURES = {
     "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
     "sp_set_inval_switch": (ctypes.c_int, [_P, _I32]),
     "sp_set_local_rounds": (ctypes.c_int, [_P, _I32]),
+    "sp_set_batch_graphs": (ctypes.c_int, [_P, _I32]),
     "sp_loop_counters": (ctypes.c_int, [_P, _P, _I32]),
     "sp_pr_init": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, _I32, _P]),
     "sp_pr_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int, _P]),
@@ -151,6 +152,7 @@ SIGNATURES = {
     "sp_server_drain": (ctypes.c_int, [_P]),
     "sp_server_stats_get": (ctypes.c_int, [_P, _P]),
     "sp_server_get_dist": (ctypes.c_int, [_P, _I32, _P]),
+    "sp_last_cuda_error": (ctypes.c_char_p, [_P]),
     "sp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sp_version": (ctypes.c_char_p, []),
 }
@@ -474,6 +476,13 @@ class Graph:
         keys = ("rounds_push", "local_rounds", "local_episodes", "splits", "far_moves",
                 "rounds_inval", "jumps", "local_ns", "push_ns", "timeout")
         return dict(zip(keys, (int(x) for x in out)))
+
+    def last_cuda_error(self) -> str:
+        return load().sp_last_cuda_error(self._h).decode()
+
+    def set_batch_graphs(self, on: bool):
+        """Replay repeated batch shapes as a cached CUDA graph (default on)."""
+        _check(load().sp_set_batch_graphs(self._h, int(bool(on))), "sp_set_batch_graphs")
 
     def set_local_rounds(self, max_edges: int):
         """Frontier-edge bound of single-block push rounds (0 = off)."""

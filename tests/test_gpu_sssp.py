@@ -471,3 +471,41 @@ def test_local_rounds_any_bound_matches_oracle(make, bound, delta):
         g.set_local_rounds(bound)
         g.set_delta(delta)
     run_workload(make(), 3, store=False, setup=setup)
+
+
+# ------------------------------------------------- cached batch CUDA graphs
+
+@pytest.mark.parametrize("make,slack", [
+    (lambda: wl.tiny_er(seed=8), 0.25),
+    (lambda: wl.rmat(scale=13, batch_frac=0.01, seed=9), 0.25),
+    (lambda: wl.rmat(scale=12, batch_frac=0.02, seed=10), 0.0),   # relocations, pool growth
+])
+def test_repeated_batch_shapes_replay_a_cached_graph(make, slack):
+    """On a stream of its own the graph replays repeated batch shapes as a
+    CUDA graph; every batch still matches the oracle, with stats on and off
+    (which changes the shape and forces a new capture), and around a
+    rejected batch."""
+    import torch
+    W = make()
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = sp.Graph(W.n, W.row_off, W.col, W.w, slack=slack, stream=st)
+    try:
+        g.sssp_init(W.source)
+        for k in range(8):
+            b = W.batch(k)
+            if k == 5:    # a rejected batch of the same shape changes nothing
+                bad = wl.Batch(b.del_src, b.del_dst, b.add_src, b.add_dst,
+                               np.zeros_like(b.add_w))
+                rc, _ = g.apply_batch(bad.del_src, bad.del_dst, bad.add_src, bad.add_dst,
+                                      bad.add_w, raise_on_error=False)
+                assert rc == sp.SP_EINVAL
+            st_ = g.apply(b, stats=(k % 3 == 2))
+            cnt = ref.apply(b)
+            if st_ is not None:
+                assert (st_.n_del_applied, st_.n_del_absent, st_.n_add_applied,
+                        st_.n_add_present) == cnt
+            check_all(g, ref, W.source, store=(k % 2 == 0))
+    finally:
+        g.close()
