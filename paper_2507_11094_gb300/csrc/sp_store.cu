@@ -635,21 +635,26 @@ __global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
       const int j = j0 + lane + 32 * t;
       en[t] = j < jl ? old[j] : make_int2(0x7fffffff, 0);
     }
-    // items whose cols lie in [col(j0), col(jl-1)]
-    const u64 klo = sg.prefix | ((u64)(unsigned)old[j0].x << 1);
-    const u64 khi = sg.prefix | ((u64)(unsigned)old[jl - 1].x << 1) | 1ull;
+    // the strip owns the items with cols in [col(j0), col(jl)) (the first
+    // strip from the lowest col, the last one to the highest), so every item
+    // of the row belongs to exactly one strip
+    const bool first_strip = j0 == 0, last_strip = jl == sg.old_deg;
     u32 ilo = sg.first, ihi = sg.end;
-    {
+    if (!first_strip) {
+      const u64 klo = sg.prefix | ((u64)(unsigned)old[j0].x << 1);
       u32 lo = sg.first, hi = sg.end;
       while (lo < hi) {
         const u32 mid = (lo + hi) >> 1;
         if (a.keys[mid] < klo) lo = mid + 1; else hi = mid;
       }
       ilo = lo;
-      hi = sg.end;
+    }
+    if (!last_strip) {
+      const u64 khi = sg.prefix | ((u64)(unsigned)old[jl].x << 1);
+      u32 lo = ilo, hi = sg.end;
       while (lo < hi) {
         const u32 mid = (lo + hi) >> 1;
-        if (a.keys[mid] <= khi) lo = mid + 1; else hi = mid;
+        if (a.keys[mid] < khi) lo = mid + 1; else hi = mid;
       }
       ihi = lo;
     }
@@ -685,42 +690,32 @@ __global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
           }
         }
       }
+      // the strip's applied insertions: old entries before the strip and in
+      // it with a smaller col, applied deletions with a smaller col, applied
+      // insertions before it
+      const u64 cmask = (1ull << a.bits) - 1;
+      for (u32 i = ilo + lane; i < ihi; i += 32) {
+        const u64 key = a.keys[i];
+        if ((key & 1) && (a.flags[i] & 1)) {
+          const int col = (int)((key >> 1) & cmask);
+          int lo = j0, hi = jl;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (old[mid].x < col) lo = mid + 1; else hi = mid;
+          }
+          u32 l2 = ilo, h2 = i;
+          const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
+          while (l2 < h2) {
+            const u32 mid = (l2 + h2) >> 1;
+            if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
+          }
+          const u64 q0 = a.item_pref[l2] - sg.base_pref, qi = a.item_pref[i] - sg.base_pref;
+          const int pos = lo - (int)(u32)q0 + (int)(u32)(qi >> 32);
+          if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
+          else bad = true;
+        }
+      }
     }
-  }
-  if (bad) atomicExch(&c->bad, 1);
-}
-
-// Applied insertions of big rows, one thread per batch item.
-__global__ void __launch_bounds__(kThreads) k_merge_big_items(MergeArgs a) {
-  Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
-  const u64 cmask = (1ull << a.bits) - 1;
-  bool bad = false;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_items;
-       i += gridDim.x * blockDim.x) {
-    const u64 key = a.keys[i];
-    if (!((key & 1) && (a.flags[i] & 1))) continue;
-    const Seg sg = a.seg[a.head_scan[i] + a.head[i] - 1];
-    if (sg.old_deg < kBigRow) continue;
-    const int col = (int)((key >> 1) & cmask);
-    const int2 *old = a.st[sg.dir].adj + sg.old_start;
-    int lo = 0, hi = sg.old_deg;   // old entries with col < this col
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (old[mid].x < col) lo = mid + 1; else hi = mid;
-    }
-    u32 l2 = sg.first, h2 = i;     // items with col < this col
-    const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
-    while (l2 < h2) {
-      const u32 mid = (l2 + h2) >> 1;
-      if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
-    }
-    const u64 q0 = a.item_pref[l2] - sg.base_pref, qi = a.item_pref[i] - sg.base_pref;
-    const int pos = lo - (int)(u32)q0 + (int)(u32)(qi >> 32);
-    if (pos >= 0 && pos < sg.new_deg)
-      a.st[sg.dir].adj[sg.dest + pos] = make_int2(col, (int)a.vals[i]);
-    else
-      bad = true;
   }
   if (bad) atomicExch(&c->bad, 1);
 }
@@ -975,8 +970,7 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.n_items = (u32)ni;
   k_merge<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
   k_merge_big<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  k_merge_big_items<<<blocks_for(ni, kThreads, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  *launches += 3;
+  *launches += 2;
 }
 
 void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
