@@ -4,12 +4,16 @@
 // merged once (updateCSRDel / updateCSRAdd of the DynSSSP driver, done as a
 // sort-merge), and orders graph edges when a store is built.
 //
-// Per 9-bit digit, three launches:
-//   k_hist       per-tile digit counts (count table is digit-major);
+// Per 9-bit digit:
+//   k_hist       per-tile digit counts (count table is digit-major), for the
+//                first digit only;
 //   k_digit_scan one block per digit: prefix of its counts over the tiles,
-//                and the digit's total;
+//                and the digit's total; it also clears the other count table;
 //   k_scatter    digit bases from the totals (block scan), then a stable
-//                in-tile rank with warp match_any + per-warp digit counters.
+//                in-tile rank with warp match_any + per-warp digit counters;
+//                every item it places also counts the next digit for the
+//                output tile it lands in (into the other table), which
+//                replaces the next pass's k_hist.
 #include "sp_internal.cuh"
 
 namespace sp {
@@ -77,11 +81,17 @@ __device__ __forceinline__ u32 block_excl_scan(u32 x, u32 *ws, u32 *total) {
   return r;
 }
 
-// Block d: exclusive prefix of counts[d][0..tiles) in place, total to totals[d].
+// Block d: exclusive prefix of counts[d][0..tiles) in place, total to
+// totals[d]; clears row d of `clear` (the next pass's table) when given.
 __global__ void __launch_bounds__(kThreads)
-k_digit_scan(u32 *__restrict__ counts, u32 tiles, u32 *__restrict__ totals) {
+k_digit_scan(u32 *__restrict__ counts, u32 tiles, u32 *__restrict__ totals,
+             u32 *__restrict__ clear) {
   __shared__ u32 ws[kWarps];
   u32 *row = counts + (long long)blockIdx.x * tiles;
+  if (clear) {
+    u32 *crow = clear + (long long)blockIdx.x * tiles;
+    for (u32 i = threadIdx.x; i < tiles; i += kThreads) crow[i] = 0;
+  }
   const u32 per = (tiles + kThreads - 1) / kThreads;
   const u32 b = threadIdx.x * per < tiles ? threadIdx.x * per : tiles;
   const u32 e = b + per < tiles ? b + per : tiles;
@@ -100,7 +110,8 @@ k_digit_scan(u32 *__restrict__ counts, u32 tiles, u32 *__restrict__ totals) {
 __global__ void __launch_bounds__(kThreads)
 k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long n, int shift,
           const u32 *__restrict__ offs, const u32 *__restrict__ totals, u32 tiles,
-          u64 *__restrict__ keys_out, u32 *__restrict__ vals_out) {
+          u64 *__restrict__ keys_out, u32 *__restrict__ vals_out, u32 *__restrict__ next_counts,
+          int next_shift) {
   __shared__ u32 s_off[kBins];
   __shared__ u32 s_run[kBins];
   __shared__ u32 s_cnt[2][kWarps][kBins];
@@ -170,6 +181,10 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
       u32 pos = s_off[d] + s_cnt[p][warp][d] + rank;
       keys_out[pos] = key;
       vals_out[pos] = val;
+      if (next_counts) {
+        const u32 nd = (u32)((key >> next_shift) & (kBins - 1));
+        atomicAdd(next_counts + (long long)nd * tiles + pos / kTile, 1u);
+      }
     }
   }
 }
@@ -179,7 +194,7 @@ k_scatter(const u64 *__restrict__ keys, const u32 *__restrict__ vals, long long 
 size_t sort_tmp_bytes(long long n) {
   long long tiles = (n + kTile - 1) / kTile;
   long long cnt = tiles * kBins;
-  return (size_t)(cnt + kBins + 64) * sizeof(u32) + 256;
+  return (size_t)(2 * cnt + kBins + 64) * sizeof(u32) + 256;
 }
 
 void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,
@@ -187,17 +202,21 @@ void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,
   if (n <= 1 || key_bits <= 0) return;
   const u32 tiles = (u32)((n + kTile - 1) / kTile);
   const long long cnt = (long long)tiles * kBins;
-  u32 *counts = (u32 *)tmp;
-  u32 *totals = counts + cnt;
+  u32 *counts[2] = {(u32 *)tmp, (u32 *)tmp + cnt};
+  u32 *totals = counts[1] + cnt;
   u64 *kin = keys, *kout = keys_alt;
   u32 *vin = vals, *vout = vals_alt;
   int passes = (key_bits + kBits - 1) / kBits;
+  k_hist<<<tiles, kThreads, 0, st>>>(kin, n, 0, counts[0], tiles);
+  if (launches) *launches += 1;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass * kBits;
-    k_hist<<<tiles, kThreads, 0, st>>>(kin, n, shift, counts, tiles);
-    k_digit_scan<<<kBins, kThreads, 0, st>>>(counts, tiles, totals);
-    k_scatter<<<tiles, kThreads, 0, st>>>(kin, vin, n, shift, counts, totals, tiles, kout, vout);
-    if (launches) *launches += 3;
+    const bool more = pass + 1 < passes;
+    u32 *cur = counts[pass & 1], *nxt = more ? counts[(pass + 1) & 1] : nullptr;
+    k_digit_scan<<<kBins, kThreads, 0, st>>>(cur, tiles, totals, nxt);
+    k_scatter<<<tiles, kThreads, 0, st>>>(kin, vin, n, shift, cur, totals, tiles, kout, vout, nxt,
+                                          shift + kBits);
+    if (launches) *launches += 2;
     u64 *tk = kin; kin = kout; kout = tk;
     u32 *tv = vin; vin = vout; vout = tv;
   }

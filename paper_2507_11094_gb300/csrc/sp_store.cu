@@ -294,27 +294,42 @@ __global__ void k_check_batch(const int *__restrict__ ds, const int *__restrict_
 // batch: segments (one per touched (store, row))
 // --------------------------------------------------------------------------
 
-__global__ void k_seg_heads(const u64 *__restrict__ keys, long long ni, int bits, u32 *head) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ni;
-       i += (long long)gridDim.x * blockDim.x)
-    head[i] = (i == 0 || (keys[i] >> (bits + 1)) != (keys[i - 1] >> (bits + 1))) ? 1u : 0u;
-}
-
-__global__ void k_seg_emit(const u64 *__restrict__ keys, const u32 *__restrict__ head,
-                           const u32 *__restrict__ head_scan, long long ni, int bits, Seg *seg,
-                           Ctl *ctl) {
+// One segment per touched (store, row): an item whose (store, row) differs
+// from its predecessor's starts one.  Segment slots are handed out per block
+// (one atomic per block), so segments are not in item order; a segment's end
+// is found by binary search for the first item of a later row.
+__global__ void __launch_bounds__(kThreads) k_segments(const u64 *__restrict__ keys, long long ni,
+                                                       int bits, Seg *seg, Ctl *ctl) {
+  __shared__ u32 scratch[40];
   const u64 rmask = (1ull << bits) - 1;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ni;
-       i += (long long)gridDim.x * blockDim.x) {
-    const u32 s = head_scan[i] + head[i] - 1;   // segment holding item i
-    if (head[i]) {
-      u64 rk = keys[i] >> (bits + 1);
-      seg[s].first = (u32)i;
-      seg[s].row = (int)(rk & rmask);
-      seg[s].dir = (int)(rk >> bits);
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ni;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    u64 pfx = 0;
+    bool head = false;
+    if (i < ni) {
+      pfx = keys[i] >> (bits + 1);
+      head = i == 0 || (keys[i - 1] >> (bits + 1)) != pfx;
     }
-    if (i == ni - 1 || head[i + 1]) seg[s].end = (u32)(i + 1);
-    if (i == ni - 1) ctl->n_seg = s + 1;
+    u32 total;
+    const u32 rank = block_excl_scan_u32(head ? 1u : 0u, scratch, &total);
+    if (threadIdx.x == 0) scratch[34] = total ? atomicAdd(&ctl->n_seg, total) : 0u;
+    __syncthreads();
+    const u32 sbase = scratch[34];
+    __syncthreads();
+    if (head) {
+      const u64 next = (pfx + 1) << (bits + 1);   // smallest key of a later row
+      long long lo = i + 1, hi = ni;
+      while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (keys[mid] < next) lo = mid + 1; else hi = mid;
+      }
+      Seg &sg = seg[sbase + rank];
+      sg.first = (u32)i;
+      sg.end = (u32)lo;
+      sg.row = (int)(pfx & rmask);
+      sg.dir = (int)(pfx >> bits);
+    }
   }
 }
 
@@ -912,12 +927,9 @@ void launch_segments(sp_graph *g, long long ni, int *launches) {
   BatchBufs &b = g->bb;
   sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, ni, 2 * g->bits + 2, b.tmp, g->stream,
              launches);
-  unsigned gb = blocks_for(ni, kThreads, g->num_sms * 16);
-  k_seg_heads<<<gb, kThreads, 0, g->stream>>>(b.keys, ni, g->bits, b.head);
-  scan_exclusive_u32(b.head, b.head_scan, ni, b.tmp, g->stream, launches);
-  k_seg_emit<<<gb, kThreads, 0, g->stream>>>(b.keys, b.head, b.head_scan, ni, g->bits, b.seg,
-                                             g->ctl);
-  *launches += 2;
+  k_segments<<<blocks_for(ni, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(
+      b.keys, ni, g->bits, b.seg, g->ctl);
+  *launches += 1;
 }
 
 void launch_count(sp_graph *g, long long ni, int *launches) {
