@@ -61,23 +61,21 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     al.put(b.keys, old * 8); al.put(b.keys_alt, old * 8);
     al.put(b.vals, old * 4); al.put(b.vals_alt, old * 4);
     al.put(b.flags, old); al.put(b.itemv, old * 8); al.put(b.item_pref, old * 8);
-    al.put(b.head, old * 4); al.put(b.head_scan, old * 4);
+    al.put(b.opos, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
-    al.put(b.ment, old * 8);
     al.put(b.tmp, b.tmp_bytes);
     b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
     b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
     b.flags = (unsigned char *)al.get(c);
     b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
-    b.head = (u32 *)al.get(c * 4); b.head_scan = (u32 *)al.get(c * 4);
+    b.opos = (u32 *)al.get(c * 4);
     b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
-    b.ment = (int2 *)al.get(c * 8);
     b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
     ++g->gen;
     if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
-        !b.item_pref || !b.head || !b.head_scan || !b.seg || !b.ment || !b.tmp) {
+        !b.item_pref || !b.opos || !b.seg || !b.tmp) {
       return SP_ENOMEM;
     }
   }
@@ -95,7 +93,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
       return SP_ENOMEM;
   }
-  // big-row strips: at most (old entries of touched rows) / 256 + one per row
+  // merge strips: at most (old entries of touched rows) / 256 + one per row
   const long long sneed = (2 * g->m) / 256 + ni + 64;
   if (sneed > b.strips_cap) {
     const long long c = std::max(sneed, 2 * b.strips_cap);
@@ -104,17 +102,6 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.strips_cap = b.strips ? c : 0;
     ++g->gen;
     if (!b.strips) return SP_ENOMEM;
-  }
-  // merge chunk-owner table: elements = old entries of touched rows (<= 2m)
-  // plus batch items
-  const long long mneed = (2 * g->m + ni) / sp::kChunk + 64;
-  if (mneed > b.mown_cap) {
-    const long long c = std::max(mneed, 2 * b.mown_cap);
-    g->al.put(b.mown, (size_t)b.mown_cap * 4);
-    b.mown = (u32 *)g->al.get((size_t)c * 4);
-    b.mown_cap = b.mown ? c : 0;
-    ++g->gen;
-    if (!b.mown) return SP_ENOMEM;
   }
   return SP_OK;
 }
@@ -261,8 +248,7 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
 // Buffers big enough for an asynchronous batch of ni items?
 bool reserved_for(const sp_graph *g, long long ni) {
   const sp::BatchBufs &b = g->bb;
-  return ni + 1 <= b.cap_items && (2 * g->m + ni) / sp::kChunk + 64 <= b.mown_cap &&
-         (2 * g->m) / 256 + ni + 64 <= b.strips_cap;
+  return ni + 1 <= b.cap_items && (2 * g->m) / 256 + ni + 64 <= b.strips_cap;
 }
 
 }  // namespace
@@ -301,10 +287,8 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(b.keys, c * 8); al.put(b.keys_alt, c * 8);
   al.put(b.vals, c * 4); al.put(b.vals_alt, c * 4);
   al.put(b.flags, c); al.put(b.itemv, c * 8); al.put(b.item_pref, c * 8);
-  al.put(b.head, c * 4); al.put(b.head_scan, c * 4);
+  al.put(b.opos, c * 4);
   al.put(b.seg, c * sizeof(sp::Seg));
-  al.put(b.ment, c * 8);
-  al.put(b.mown, (size_t)b.mown_cap * 4);
   al.put(b.strips, (size_t)b.strips_cap * 8);
   al.put(b.tmp, b.tmp_bytes);
   c = b.cap_in;

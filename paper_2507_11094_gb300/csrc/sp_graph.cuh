@@ -66,12 +66,9 @@ struct BatchBufs {
   unsigned char *flags = nullptr;   // per item: bit0 = applied
   u64 *itemv = nullptr;             // per item: applied del (1) | applied add (1<<32)
   u64 *item_pref = nullptr;         // exclusive scan of itemv
-  u32 *head = nullptr, *head_scan = nullptr;
+  u32 *opos = nullptr;              // per item: old entries of its row with a smaller col
   Seg *seg = nullptr;
-  int2 *ment = nullptr;             // merge queue: (segment, first element)
-  u32 *mown = nullptr;              // merge chunk -> queue slot
-  long long mown_cap = 0;
-  int2 *strips = nullptr;           // big-row strips: (segment, first entry)
+  int2 *strips = nullptr;           // merge strips: (segment, first old entry)
   long long strips_cap = 0;
   void *tmp = nullptr;
   size_t tmp_bytes = 0;

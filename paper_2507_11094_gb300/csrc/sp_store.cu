@@ -356,8 +356,7 @@ struct CountArgs {
   unsigned char *flags;
   u64 *itemv;
   const u64 *item_pref;
-  int2 *ment;
-  u32 *mown;
+  u32 *opos;
   int2 *strips;
   Store st[2];
   int bits;
@@ -366,9 +365,7 @@ struct CountArgs {
   int n;
 };
 
-// Rows with at least kBigRow old entries are merged strip by strip
-// (k_merge_big); smaller ones a warp per row (k_merge).
-constexpr int kBigRow = 256;
+// The merge works on strips of kStrip old entries of a row, one warp each.
 constexpr int kStrip = 256;
 
 // One thread per batch item: does this deletion / insertion apply?
@@ -376,10 +373,12 @@ constexpr int kStrip = 256;
 //    deletion of that edge in the batch;
 //  - among the insertions of one edge the smallest weight is the candidate
 //    (first on ties); it applies if the edge is absent after the deletions.
+// Every item also records where its col falls in the old row (opos: the
+// number of old entries with a smaller col) and whether the edge was there
+// (flags bit 1), which is all the merge needs to place it.
 __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
   Ctl *c = a.ctl;
   if (ld_cg_i32(&c->status) != 0) return;
-  const int lane = threadIdx.x & 31;
   const u64 cmask = (1ull << a.bits) - 1;
   u64 del_ok = 0, del_abs = 0, add_ok = 0, add_pres = 0;
   const long long ni = a.n_items;
@@ -396,9 +395,11 @@ __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
       const int2 *old = st.adj + rm.start;
       const int j = row_lower_bound(old, rm.deg, col);
       const bool present = j < rm.deg && __ldg(&old[j].x) == col;
+      const unsigned char pbit = present ? 2 : 0;
+      a.opos[i] = (u32)j;
       if ((key & 1) == 0) {
         const bool applied = present && !(i > 0 && a.keys[i - 1] == key);
-        a.flags[i] = applied ? 1 : 0;
+        a.flags[i] = (applied ? 1 : 0) | pbit;
         a.itemv[i] = applied ? 1ull : 0ull;
         if (dir == 0) { applied ? ++del_ok : ++del_abs; }
       } else if (i == 0 || a.keys[i - 1] != key) {  // first insertion of this edge
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
         const bool applied = !present || del_exists;
         for (long long t = i; t < j2; ++t) {
           const bool on = applied && t == best;
-          a.flags[t] = on ? 1 : 0;
+          a.flags[t] = (on ? 1 : 0) | pbit;
           a.itemv[t] = on ? (1ull << 32) : 0ull;
         }
         if (dir == 0) {
@@ -426,7 +427,6 @@ __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
   __shared__ u64 sums[4];
   if (threadIdx.x < 4) sums[threadIdx.x] = 0;
   __syncthreads();
-  (void)lane;
   block_add(del_ok, &sums[0], &c->del_applied);
   block_add(del_abs, &sums[1], &c->del_absent);
   block_add(add_ok, &sums[2], &c->add_applied);
@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
 
 // One thread per touched row: new size (from the item prefix counts),
 // destination (the row's alternate region, or a fresh pair of regions in the
-// spare pool when the row outgrows its capacity), and a reservation of the
-// row's merge elements (old entries, then batch items) in the merge queue.
+// spare pool when the row outgrows its capacity), and the row's strips of
+// kStrip old entries (one strip for a row with fewer), the merge's units.
 __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
   __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
@@ -485,12 +485,12 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
         sg.new_cap = rm.cap;
       }
       a.seg[si] = sg;
-      if (rm.deg >= kBigRow) nstr = (u32)((rm.deg + kStrip - 1) / kStrip);
+      nstr = rm.deg > kStrip ? (u32)((rm.deg + kStrip - 1) / kStrip) : 1u;
 
       ++touched;
       slots += (u64)rm.deg + (u64)new_deg;
     }
-    // reserve big-row strips: one atomic per block
+    // reserve the strips: one atomic per block
     {
       u32 stot;
       const u32 se = block_excl_scan_u32(nstr, scratch, &stot);
@@ -521,10 +521,8 @@ struct MergeArgs {
   const unsigned char *flags;
   const u64 *item_pref;   // exclusive scan of itemv, n_items + 1 entries
   const Seg *seg;
-  const int2 *ment;
-  const u32 *mown;
+  const u32 *opos;
   const int2 *strips;
-  const u32 *head, *head_scan;   // item -> segment
   Store st[2];
   int bits;
   u32 n_items;
@@ -535,107 +533,86 @@ __device__ __forceinline__ bool merge_enabled(Ctl *c) {
          ld_cg_i32(&c->bad) == 0;
 }
 
+// First index p in [lo, hi) with a[p] >= x (hi if none) in a non-decreasing
+// array.  The whole warp searches together: each step probes 32 evenly
+// spaced entries at once, so a range of R entries takes ceil(log32 R)
+// dependent loads instead of log2 R.  Warp-uniform arguments and result.
+__device__ __forceinline__ u32 warp_lower_bound(const u32 *__restrict__ a, u32 lo, u32 hi,
+                                                u32 x) {
+  const u32 lane = threadIdx.x & 31;
+  while (hi > lo) {
+    const u32 step = (hi - lo + 31) / 32;
+    const u32 q = lo + (lane + 1) * step - 1;
+    const bool less = q < hi && __ldg(a + q) < x;
+    const u32 t = __popc(__ballot_sync(kFull, less));
+    const u32 qt = lo + (t + 1) * step - 1;   // lane t's probe, if it had one
+    const u32 nhi = (t < 32 && qt < hi) ? qt : hi;
+    lo += t * step;
+    hi = nhi;
+  }
+  return lo;
+}
+
 // The merged row holds the kept old entries and the applied insertions in
 // col order, so every element knows its output slot from prefix counts:
-//   old entry j (col c):      j - #applied deletions with col < c
-//                               + #applied insertions with col < c
-//   applied insertion (col c): #old entries with col < c
-//                               - #applied deletions with col < c
-//                               + #applied insertions before it.
-// Items are sorted by (col, deletion before insertion), so "col < c" is an
-// item index range [first, i).  Rows below kBigRow old entries take one warp
-// each: the lanes read 32 consecutive old entries at a time (one coalesced
-// 256-byte load), find their place among the row's items by binary search
-// and write 32 mostly consecutive slots; then the lanes place the applied
-// insertions.  The warp's first lane publishes the row's new metadata.
-__global__ void __launch_bounds__(kThreads) k_merge(MergeArgs a) {
+//   old entry j (col c):   j - #applied deletions with col < c
+//                            + #applied insertions with col < c
+//   applied insertion i:   opos[i] + present[i] - #applied deletions before i
+//                            + #applied insertions before i
+// (opos = old entries with a smaller col; when the edge was present, its
+// deletion is among the deletions before i and its old entry is not).
+// Items are sorted by (col, deletion before insertion) and opos is
+// non-decreasing along a row's items.
+//
+// One warp per strip of kStrip old entries.  The strip owns the items with
+// opos in [j0, jl) (the last strip also those past the end), so every item
+// of the row belongs to exactly one strip, and every item of an earlier
+// strip has a smaller col than every old entry of this one.  The warp loads
+// its old entries (eight coalesced 256-byte loads), finds its item range
+// with two warp-wide searches (none for a row of one strip), stages the
+// items in shared memory, and places both from there: the dependent global
+// loads per strip are the strip record, the row's segment, the searches and
+// one round of item loads.
+constexpr int kStripItems = 128;   // items staged per warp
+struct StripItems {
+  u64 pre[kStripItems];            // applied (ins << 32 | dels) of the row before the item
+  u32 col[kStripItems];
+  u32 w[kStripItems];
+  u32 opos[kStripItems];
+  unsigned char fl[kStripItems];   // bit0 applied, bit1 present, bit2 insertion
+};
+
+__global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
+  __shared__ StripItems sitems[kThreads / 32];
   Ctl *c = a.ctl;
   if (!merge_enabled(c)) return;
   const int lane = threadIdx.x & 31;
-  const u32 nseg = ld_cg_u32(&c->n_seg);
+  StripItems &S = sitems[threadIdx.x >> 5];
+  const u32 nstrips = ld_cg_u32(&c->bstrips);
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
   const u64 cmask = (1ull << a.bits) - 1;
   bool bad = false;
-  for (u32 si = gw; si < nseg; si += nw) {
-    const Seg sg = a.seg[si];
-    if (sg.old_deg >= kBigRow) continue;   // strips
-    const Store &st = a.st[sg.dir];
-    const int2 *old = st.adj + sg.old_start;
-    int2 *dst = st.adj + sg.dest;
-    if (lane == 0) {
-      RowMeta nm;
-      nm.start = sg.dest;
-      nm.deg = sg.new_deg;
-      nm.cap = sg.new_cap;
-      st.row[sg.row] = nm;
-      st.alt[sg.row] = sg.new_alt;
-    }
-    for (int j0 = 0; j0 < sg.old_deg; j0 += 32) {
-      const int j = j0 + lane;
-      if (j < sg.old_deg) {
-        const int2 en = old[j];
-        const u64 kc = sg.prefix | ((u64)(unsigned)en.x << 1);
-        u32 lo = sg.first, hi = sg.end;
-        while (lo < hi) {
-          const u32 mid = (lo + hi) >> 1;
-          if (a.keys[mid] < kc) lo = mid + 1; else hi = mid;
-        }
-        const bool del = lo < sg.end && a.keys[lo] == kc && (a.flags[lo] & 1);
-        if (!del) {
-          const u64 pp = a.item_pref[lo] - sg.base_pref;
-          const int pos = j - (int)(u32)pp + (int)(u32)(pp >> 32);
-          if (pos >= 0 && pos < sg.new_deg) dst[pos] = en;
-          else bad = true;
-        }
-      }
-    }
-    for (u32 i = sg.first + lane; i < sg.end; i += 32) {
-      const u64 key = a.keys[i];
-      if ((key & 1) && (a.flags[i] & 1)) {
-        const int col = (int)((key >> 1) & cmask);
-        int lo = 0, hi = sg.old_deg;   // old entries with col < this col
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (old[mid].x < col) lo = mid + 1; else hi = mid;
-        }
-        u32 l2 = sg.first, h2 = i;     // items with col < this col
-        const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
-        while (l2 < h2) {
-          const u32 mid = (l2 + h2) >> 1;
-          if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
-        }
-        const u64 p0 = a.item_pref[l2] - sg.base_pref, pi = a.item_pref[i] - sg.base_pref;
-        const int pos = lo - (int)(u32)p0 + (int)(u32)(pi >> 32);
-        if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
-        else bad = true;
-      }
-    }
-  }
-  if (bad) atomicExch(&c->bad, 1);
-}
-
-// Big rows: one warp per 256-entry strip of old entries.  The strip's col
-// range bounds the batch items that can fall inside it (two warp-uniform
-// searches); with none, every entry moves by one shift; otherwise each entry
-// finds its own item position inside that short range.  Loads and stores
-// are strided by 32 so a warp touches contiguous bytes.
-__global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
-  Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
-  const int lane = threadIdx.x & 31;
-  const u32 nstrips = ld_cg_u32(&c->bstrips);
-  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
-  const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  bool bad = false;
+  // the next strip's record and segment are loaded while this one is
+  // processed, which takes two dependent loads off every strip's chain
+  int2 sp = gw < nstrips ? __ldcg(a.strips + gw) : make_int2(0, 0);
+  Seg sg;
+  if (gw < nstrips) sg = a.seg[sp.x];
   for (u32 sidx = gw; sidx < nstrips; sidx += nw) {
-    const int2 sp = __ldcg(a.strips + sidx);
-    const Seg sg = a.seg[sp.x];
+    const u32 nx = sidx + nw;
+    const int2 spn = nx < nstrips ? __ldcg(a.strips + nx) : sp;
     const Store &st = a.st[sg.dir];
     const int2 *old = st.adj + sg.old_start;
     int2 *dst = st.adj + sg.dest;
     const int j0 = sp.y;
     const int jl = j0 + kStrip < sg.old_deg ? j0 + kStrip : sg.old_deg;
+    int2 en[kStrip / 32];
+#pragma unroll
+    for (int t = 0; t < kStrip / 32; ++t) {
+      const int j = j0 + lane + 32 * t;
+      en[t] = j < jl ? old[j] : make_int2(0, 0);
+    }
+    const Seg sgn = a.seg[spn.x];
     if (j0 == 0 && lane == 0) {
       RowMeta nm;
       nm.start = sg.dest;
@@ -644,48 +621,53 @@ __global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
       st.row[sg.row] = nm;
       st.alt[sg.row] = sg.new_alt;
     }
-    int2 en[kStrip / 32];
-#pragma unroll
-    for (int t = 0; t < kStrip / 32; ++t) {
-      const int j = j0 + lane + 32 * t;
-      en[t] = j < jl ? old[j] : make_int2(0x7fffffff, 0);
-    }
-    // the strip owns the items with cols in [col(j0), col(jl)) (the first
-    // strip from the lowest col, the last one to the highest), so every item
-    // of the row belongs to exactly one strip
-    const bool first_strip = j0 == 0, last_strip = jl == sg.old_deg;
-    u32 ilo = sg.first, ihi = sg.end;
-    if (!first_strip) {
-      const u64 klo = sg.prefix | ((u64)(unsigned)old[j0].x << 1);
-      u32 lo = sg.first, hi = sg.end;
-      while (lo < hi) {
-        const u32 mid = (lo + hi) >> 1;
-        if (a.keys[mid] < klo) lo = mid + 1; else hi = mid;
+    const u32 ilo = j0 > 0 ? warp_lower_bound(a.opos, sg.first, sg.end, (u32)j0) : sg.first;
+    const u32 ihi = jl < sg.old_deg ? warp_lower_bound(a.opos, ilo, sg.end, (u32)jl) : sg.end;
+    const u32 k = ihi - ilo;
+    const u64 pend = a.item_pref[ihi] - sg.base_pref;
+    if (k <= (u32)kStripItems) {
+      for (u32 q = lane; q < k; q += 32) {
+        const u32 i = ilo + q;
+        const u64 key = a.keys[i];
+        S.pre[q] = a.item_pref[i] - sg.base_pref;
+        S.col[q] = (u32)((key >> 1) & cmask);
+        S.w[q] = a.vals[i];
+        S.opos[q] = a.opos[i];
+        S.fl[q] = (unsigned char)((a.flags[i] & 3) | ((key & 1) ? 4 : 0));
       }
-      ilo = lo;
-    }
-    if (!last_strip) {
-      const u64 khi = sg.prefix | ((u64)(unsigned)old[jl].x << 1);
-      u32 lo = ilo, hi = sg.end;
-      while (lo < hi) {
-        const u32 mid = (lo + hi) >> 1;
-        if (a.keys[mid] < khi) lo = mid + 1; else hi = mid;
-      }
-      ihi = lo;
-    }
-    const u64 p0 = a.item_pref[ilo] - sg.base_pref;
-    if (ilo == ihi) {
-      const int shift = (int)(u32)(p0 >> 32) - (int)(u32)p0;
+      __syncwarp();
 #pragma unroll
       for (int t = 0; t < kStrip / 32; ++t) {
         const int j = j0 + lane + 32 * t;
         if (j < jl) {
-          const int pos = j + shift;
-          if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
+          const u32 cj = (u32)en[t].x;
+          u32 lo = 0, hi = k;   // first staged item with col >= cj
+          while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            if (S.col[mid] < cj) lo = mid + 1; else hi = mid;
+          }
+          const bool del = lo < k && S.col[lo] == cj && (S.fl[lo] & 5) == 1;
+          if (!del) {
+            const u64 pp = lo < k ? S.pre[lo] : pend;
+            const int pos = j - (int)(u32)pp + (int)(u32)(pp >> 32);
+            if (pos >= 0 && pos < sg.new_deg) dst[pos] = en[t];
+            else bad = true;
+          }
+        }
+      }
+      for (u32 q = lane; q < k; q += 32) {
+        if ((S.fl[q] & 5) == 5) {   // applied insertion
+          const u64 pp = S.pre[q];
+          const int pos = (int)S.opos[q] + ((S.fl[q] >> 1) & 1) - (int)(u32)pp +
+                          (int)(u32)(pp >> 32);
+          if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2((int)S.col[q], (int)S.w[q]);
           else bad = true;
         }
       }
+      __syncwarp();
     } else {
+      // more items than the stage holds: the same placement, searching the
+      // batch arrays in global memory
 #pragma unroll
       for (int t = 0; t < kStrip / 32; ++t) {
         const int j = j0 + lane + 32 * t;
@@ -696,7 +678,7 @@ __global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
             const u32 mid = (lo + hi) >> 1;
             if (a.keys[mid] < kc) lo = mid + 1; else hi = mid;
           }
-          const bool del = lo < sg.end && a.keys[lo] == kc && (a.flags[lo] & 1);
+          const bool del = lo < ihi && a.keys[lo] == kc && (a.flags[lo] & 1);
           if (!del) {
             const u64 pp = a.item_pref[lo] - sg.base_pref;
             const int pos = j - (int)(u32)pp + (int)(u32)(pp >> 32);
@@ -705,32 +687,20 @@ __global__ void __launch_bounds__(kThreads) k_merge_big(MergeArgs a) {
           }
         }
       }
-      // the strip's applied insertions: old entries before the strip and in
-      // it with a smaller col, applied deletions with a smaller col, applied
-      // insertions before it
-      const u64 cmask = (1ull << a.bits) - 1;
       for (u32 i = ilo + lane; i < ihi; i += 32) {
         const u64 key = a.keys[i];
-        if ((key & 1) && (a.flags[i] & 1)) {
-          const int col = (int)((key >> 1) & cmask);
-          int lo = j0, hi = jl;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (old[mid].x < col) lo = mid + 1; else hi = mid;
-          }
-          u32 l2 = ilo, h2 = i;
-          const u64 k0 = sg.prefix | ((u64)(unsigned)col << 1);
-          while (l2 < h2) {
-            const u32 mid = (l2 + h2) >> 1;
-            if (a.keys[mid] < k0) l2 = mid + 1; else h2 = mid;
-          }
-          const u64 q0 = a.item_pref[l2] - sg.base_pref, qi = a.item_pref[i] - sg.base_pref;
-          const int pos = lo - (int)(u32)q0 + (int)(u32)(qi >> 32);
-          if (pos >= 0 && pos < sg.new_deg) dst[pos] = make_int2(col, (int)a.vals[i]);
+        const unsigned char f = a.flags[i];
+        if ((key & 1) && (f & 1)) {
+          const u64 pp = a.item_pref[i] - sg.base_pref;
+          const int pos = (int)a.opos[i] + ((f >> 1) & 1) - (int)(u32)pp + (int)(u32)(pp >> 32);
+          if (pos >= 0 && pos < sg.new_deg)
+            dst[pos] = make_int2((int)((key >> 1) & cmask), (int)a.vals[i]);
           else bad = true;
         }
       }
     }
+    sp = spn;
+    sg = sgn;
   }
   if (bad) atomicExch(&c->bad, 1);
 }
@@ -943,8 +913,7 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.flags = b.flags;
   a.itemv = b.itemv;
   a.item_pref = b.item_pref;
-  a.ment = b.ment;
-  a.mown = b.mown;
+  a.opos = b.opos;
   a.strips = b.strips;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
@@ -971,18 +940,22 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.flags = b.flags;
   a.item_pref = b.item_pref;
   a.seg = b.seg;
-  a.ment = b.ment;
-  a.mown = b.mown;
+  a.opos = b.opos;
   a.strips = b.strips;
-  a.head = b.head;
-  a.head_scan = b.head_scan;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
   a.n_items = (u32)ni;
-  k_merge<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  k_merge_big<<<(unsigned)std::max(1, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
-  *launches += 2;
+  // exactly the resident blocks: every warp starts at once and the strips
+  // spread evenly over them
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge, kThreads, 0) !=
+           cudaSuccess ||
+       per_sm < 1))
+    per_sm = 4;
+  k_merge<<<(unsigned)std::max(1, g->num_sms * per_sm), kThreads, 0, g->stream>>>(a);
+  *launches += 1;
 }
 
 void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
