@@ -70,7 +70,8 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
     b.opos = (u32 *)al.get(c * 4);
     b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
-    b.tmp_bytes = std::max(sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c)) + 1024;
+    b.tmp_bytes = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
+                            sp::batch_sort_tmp_bytes(g->sort_blocks)}) + 1024;
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
     ++g->gen;
@@ -223,15 +224,13 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
                           bool timed, int *launches) {
   const long long ni = 2 * (n_del + n_add);
   sp::launch_ctl_reset(g, 0, launches);
-  sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, launches);
-  sp::launch_segments(g, ni, launches);
+  cudaError_t e = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, launches);
   rec(g, timed, 1);
   sp::launch_count(g, ni, launches);
   rec(g, timed, 2);
   sp::launch_merge(g, ni, launches);
   rec(g, timed, 3);
-  cudaError_t e = cudaSuccess;
-  if (n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, launches);
+  if (e == cudaSuccess && n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, launches);
   rec(g, timed, 4);
   if (n_del > 0) sp::launch_pull(g, launches);
   rec(g, timed, 5);
@@ -358,7 +357,8 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   g->loop_blocks_push = sp::loop_blocks(0, g->num_sms);
   g->loop_blocks_inval = sp::loop_blocks(1, g->num_sms);
-  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0) {
+  g->sort_blocks = sp::batch_sort_blocks(g->num_sms);
+  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 || g->sort_blocks <= 0) {
     delete g;
     return SP_ECUDA;
   }
@@ -819,8 +819,8 @@ sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, cons
     sp::launch_ctl_reset(g, 0, launches);
     cudaError_t e = cudaSuccess;
     if (n_flag > 0) e = sp::launch_flag(g, flag_dst, n_flag, launches);
-    sp::launch_prep(g, ds, dd, nd, as, ad, aw, na, launches);
-    sp::launch_segments(g, ni, launches);
+    const cudaError_t es = sp::launch_batch_sort(g, ds, dd, nd, as, ad, aw, na, launches);
+    if (e == cudaSuccess) e = es;
     sp::launch_count(g, ni, launches);
     sp::launch_merge(g, ni, launches);
     sp::launch_finish(g, launches);
@@ -1086,8 +1086,7 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   int launches = 0, regrows = 0;
   for (int attempt = 0;; ++attempt) {
     sp::launch_ctl_reset(g, 0, &launches);
-    sp::launch_prep(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
-    sp::launch_segments(g, ni, &launches);
+    const cudaError_t es = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
     rec(g, true, 1);
     sp::launch_count(g, ni, &launches);
     sp::launch_tc_batch_sym(g, nb, &launches);     // before anything changes
@@ -1100,7 +1099,7 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
     rec(g, true, 5);
     sp::launch_finish(g, &launches);
     for (int i = 6; i <= SP_NPHASE; ++i) rec(g, true, i);
-    if (cudaGetLastError() != cudaSuccess) {
+    if (es != cudaSuccess || cudaGetLastError() != cudaSuccess) {
       cudaStreamSynchronize(g->stream);
       g->tc_state = 0;
       return SP_ECUDA;

@@ -169,6 +169,7 @@ struct sp_graph {
   int32_t max_rounds_user = 0;
   long long wait_ns_user = 0;
   int loop_blocks_push = 0, loop_blocks_inval = 0;
+  int sort_blocks = 0;          // co-resident blocks of the batch sort
   int loop_blocks_user = 0;
   cudaEvent_t ev[SP_NPHASE + 1] = {};
   long long async_ni = 0;       // items of the last enqueued async batch
@@ -186,12 +187,15 @@ sp_status store_export(sp_graph *g, const sp::Store *st, long long *row_off_d,
 sp_status store_grow_pool(sp_graph *g, sp::Store *st, long long min_pool_slots);
 sp_status ensure_owner_tables(sp_graph *g);
 void launch_ctl_reset(sp_graph *g, int full, int *launches);
-void launch_prep(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
-                 const int *ad, const int *aw, long long na, int *launches);
-void launch_segments(sp_graph *g, long long n_items, int *launches);
 void launch_count(sp_graph *g, long long n_items, int *launches);
 void launch_merge(sp_graph *g, long long n_items, int *launches);
 void launch_finish(sp_graph *g, int *launches);
+// sp_sort.cu: items, sort and segments of a batch in one cooperative launch
+int batch_sort_blocks(int num_sms);
+size_t batch_sort_tmp_bytes(int max_blocks);
+cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long long nd,
+                              const int *as, const int *ad, const int *aw, long long na,
+                              int *launches);
 void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
                         const int *ad, const int *aw, long long na, int *launches);
 

@@ -71,6 +71,7 @@ struct Ctl {
   // grid barriers of the two persistent loops (monotone arrival counts)
   alignas(128) u64 bar_inval;
   alignas(128) u64 bar_push;
+  alignas(128) u64 bar_sort;       // the batch sort's grid barrier
   // loop bookkeeping shared across launches
   alignas(128) u32 epoch;          // dedupe tag of the last frontier built
   u32 phase;                       // far dedupe tag of the last phase

@@ -201,6 +201,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->bad = 0;
   c->bar_inval = 0;
   c->bar_push = 0;
+  c->bar_sort = 0;
   c->qcnt0 = c->qcnt1 = c->qcnt2 = c->acnt = 0;
   c->scnt0 = c->scnt1 = c->scnt2 = c->ascnt = 0;
   c->fcnt0 = c->fcnt1 = c->fcnt2 = 0;
@@ -239,39 +240,6 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   }
 }
 
-// Items of the batch: for update i, a forward item (row u, col v) at i and a
-// reverse item (row v, col u) at nb + i; the low key bit is 0 for a deletion
-// and 1 for an insertion, so a deletion sorts before an insertion of the
-// same edge (deletions first, DynSSSP driver).
-__global__ void k_prep(const int *__restrict__ ds, const int *__restrict__ dd, long long nd,
-                       const int *__restrict__ as, const int *__restrict__ ad,
-                       const int *__restrict__ aw, long long na, int n, int bits, u64 *keys,
-                       u32 *vals, Ctl *ctl) {
-  const long long nb = nd + na;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
-       i += (long long)gridDim.x * blockDim.x) {
-    int u, v, w = 0;
-    u64 kind;
-    bool ok;
-    if (i < nd) {
-      u = ds[i]; v = dd[i]; kind = 0;
-      ok = u >= 0 && u < n && v >= 0 && v < n;
-    } else {
-      long long j = i - nd;
-      u = as[j]; v = ad[j]; w = aw[j]; kind = 1;
-      ok = u >= 0 && u < n && v >= 0 && v < n && w >= 1 && w <= SP_WMAX;
-    }
-    if (!ok) {
-      set_status(ctl, SP_EINVAL);
-      u = 0; v = 0;
-    }
-    keys[i] = ((u64)u << (bits + 1)) | ((u64)v << 1) | kind;
-    keys[nb + i] = (1ull << (2 * bits + 1)) | ((u64)v << (bits + 1)) | ((u64)u << 1) | kind;
-    vals[i] = (u32)w;
-    vals[nb + i] = (u32)w;
-  }
-}
-
 // Validation only (ids and weights), for callers that apply a batch in
 // several steps and must reject it before the first one.
 __global__ void k_check_batch(const int *__restrict__ ds, const int *__restrict__ dd, long long nd,
@@ -287,49 +255,6 @@ __global__ void k_check_batch(const int *__restrict__ ds, const int *__restrict_
       ok = as[j] >= 0 && as[j] < n && ad[j] >= 0 && ad[j] < n && aw[j] >= 1 && aw[j] <= SP_WMAX;
     }
     if (!ok) set_status(ctl, SP_EINVAL);
-  }
-}
-
-// --------------------------------------------------------------------------
-// batch: segments (one per touched (store, row))
-// --------------------------------------------------------------------------
-
-// One segment per touched (store, row): an item whose (store, row) differs
-// from its predecessor's starts one.  Segment slots are handed out per block
-// (one atomic per block), so segments are not in item order; a segment's end
-// is found by binary search for the first item of a later row.
-__global__ void __launch_bounds__(kThreads) k_segments(const u64 *__restrict__ keys, long long ni,
-                                                       int bits, Seg *seg, Ctl *ctl) {
-  __shared__ u32 scratch[40];
-  const u64 rmask = (1ull << bits) - 1;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < ni;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long i = base + threadIdx.x;
-    u64 pfx = 0;
-    bool head = false;
-    if (i < ni) {
-      pfx = keys[i] >> (bits + 1);
-      head = i == 0 || (keys[i - 1] >> (bits + 1)) != pfx;
-    }
-    u32 total;
-    const u32 rank = block_excl_scan_u32(head ? 1u : 0u, scratch, &total);
-    if (threadIdx.x == 0) scratch[34] = total ? atomicAdd(&ctl->n_seg, total) : 0u;
-    __syncthreads();
-    const u32 sbase = scratch[34];
-    __syncthreads();
-    if (head) {
-      const u64 next = (pfx + 1) << (bits + 1);   // smallest key of a later row
-      long long lo = i + 1, hi = ni;
-      while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (keys[mid] < next) lo = mid + 1; else hi = mid;
-      }
-      Seg &sg = seg[sbase + rank];
-      sg.first = (u32)i;
-      sg.end = (u32)lo;
-      sg.row = (int)(pfx & rmask);
-      sg.dir = (int)(pfx >> bits);
-    }
   }
 }
 
@@ -881,25 +806,6 @@ sp_status ensure_owner_tables(sp_graph *g) {
 void launch_ctl_reset(sp_graph *g, int full, int *launches) {
   k_ctl_reset<<<1, 1, 0, g->stream>>>(g->ctl, full);
   ++*launches;
-}
-
-void launch_prep(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
-                 const int *ad, const int *aw, long long na, int *launches) {
-  long long nb = nd + na;
-  if (nb == 0) return;
-  k_prep<<<blocks_for(nb, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(
-      ds, dd, nd, as, ad, aw, na, g->n, g->bits, g->bb.keys, g->bb.vals, g->ctl);
-  ++*launches;
-}
-
-void launch_segments(sp_graph *g, long long ni, int *launches) {
-  if (ni == 0) return;
-  BatchBufs &b = g->bb;
-  sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, ni, 2 * g->bits + 2, b.tmp, g->stream,
-             launches);
-  k_segments<<<blocks_for(ni, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(
-      b.keys, ni, g->bits, b.seg, g->ctl);
-  *launches += 1;
 }
 
 void launch_count(sp_graph *g, long long ni, int *launches) {
