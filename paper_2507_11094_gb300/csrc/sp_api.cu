@@ -150,32 +150,22 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
   }
 }
 
-// Phase boundary i of a batch: records timing event i, or, while the
-// pipeline is being captured, closes the graph of phase i - 1 and opens the
-// one of phase i.
+// Phase boundary i of a batch: records timing event i.  While the pipeline
+// is being captured the record becomes a node of the graph, so a replay
+// times its phases too.
 void rec(sp_graph *g, bool timed, int i) {
-  if (g->capturing >= 0) {
-    cudaGraph_t gr = nullptr;
-    if (cudaStreamEndCapture(g->stream, &gr) == cudaSuccess && g->capturing < SP_NPHASE)
-      g->bg_graph[g->capturing] = gr;
-    else if (gr)
-      cudaGraphDestroy(gr);
-    g->capturing = i;
-    if (i < SP_NPHASE && cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) !=
-                             cudaSuccess)
-      g->capturing = -2;   // capture failed: the caller falls back
-    return;
-  }
-  if (timed) cudaEventRecord(g->ev[i], g->stream);
+  if (!timed) return;
+  if (g->capturing >= 0)
+    cudaEventRecordWithFlags(g->ev[i], g->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(g->ev[i], g->stream);
 }
 
 void drop_batch_graphs(sp_graph *g) {
-  for (int i = 0; i < SP_NPHASE; ++i) {
-    if (g->bg_exec[i]) cudaGraphExecDestroy(g->bg_exec[i]);
-    if (g->bg_graph[i]) cudaGraphDestroy(g->bg_graph[i]);
-    g->bg_exec[i] = nullptr;
-    g->bg_graph[i] = nullptr;
-  }
+  if (g->bg_exec) cudaGraphExecDestroy(g->bg_exec);
+  if (g->bg_graph) cudaGraphDestroy(g->bg_graph);
+  g->bg_exec = nullptr;
+  g->bg_graph = nullptr;
   g->bg_ready = false;
 }
 
@@ -578,19 +568,13 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
         drop_batch_graphs(g);
         int cl = 0;
         if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-          g->capturing = 0;   // rec() splits the capture at every phase boundary
+          g->capturing = 0;
           const cudaError_t ce = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &cl);
-          bool ok = ce == cudaSuccess && g->capturing == SP_NPHASE;
-          if (g->capturing >= 0 && g->capturing < SP_NPHASE) {   // never expected
-            cudaGraph_t gr = nullptr;
-            cudaStreamEndCapture(g->stream, &gr);
-            if (gr) cudaGraphDestroy(gr);
-            ok = false;
-          }
           g->capturing = -1;
-          for (int i = 0; ok && i < SP_NPHASE; ++i)
-            ok = g->bg_graph[i] &&
-                 cudaGraphInstantiate(&g->bg_exec[i], g->bg_graph[i], 0) == cudaSuccess;
+          cudaGraph_t gr = nullptr;
+          bool ok = cudaStreamEndCapture(g->stream, &gr) == cudaSuccess && ce == cudaSuccess && gr;
+          g->bg_graph = gr;
+          ok = ok && cudaGraphInstantiate(&g->bg_exec, g->bg_graph, 0) == cudaSuccess;
           if (ok) {
             g->bg_ready = true;
             g->bg_gen = g->gen;
@@ -606,11 +590,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
         cudaGetLastError();
       }
       if (g->bg_ready) {
-        for (int i = 0; i < SP_NPHASE && e == cudaSuccess; ++i) {
-          if (i) rec(g, timed, i);
-          e = cudaGraphLaunch(g->bg_exec[i], g->stream);
-        }
-        rec(g, timed, SP_NPHASE);
+        e = cudaGraphLaunch(g->bg_exec, g->stream);
         launches = g->bg_launches;
         replayed = true;
       }

@@ -147,11 +147,11 @@ struct sp_graph {
   unsigned long long gen = 1;
   int last_err = 0;                      // cudaError_t of the last failed launch
   int batch_graphs = 1;                  // 0 = never capture
-  // one graph per phase, so that timing events can be recorded between them
-  cudaGraph_t bg_graph[SP_NPHASE] = {};
-  cudaGraphExec_t bg_exec[SP_NPHASE] = {};
+  // one graph per batch shape; the phase timing events are nodes inside it
+  cudaGraph_t bg_graph = nullptr;
+  cudaGraphExec_t bg_exec = nullptr;
   bool bg_ready = false;
-  int capturing = -1;                    // phase being captured (-1: none)
+  int capturing = -1;                    // >= 0 while the pipeline is captured
   unsigned long long bg_gen = 0;
   long long bg_nd = -1, bg_na = -1;
   int bg_timed = -1, bg_launches = 0;
