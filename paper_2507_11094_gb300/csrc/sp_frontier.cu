@@ -382,38 +382,42 @@ struct PushOp {
   __device__ __forceinline__ u64 load(int2 e) { return ld_cg_u64(s + e.x); }
   __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *od,
                                       const int2 *ed, const u64 *sx) {
-    u32 tx[K];
-    bool want[K], far[K];
+    // every atomicMin of the lane is issued before any result is used, then
+    // every dedupe exchange: two round trips per lane instead of up to 2K
+    u32 tx[K], nd[K];
+    u64 cand[K], old[K];
+    bool want[K], far[K], tried[K];
     u32 fmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       want[k] = false;
       far[k] = false;
       tx[k] = (u32)ed[k].x;
+      nd[k] = od[k] + (u32)ed[k].y;
+      cand[k] = pack(nd[k], ov[k]);
+      tried[k] = false;
       if (act[k]) {
         ++n_edges;
         if (od[k] < kInf) {
-          const u32 nd = od[k] + (u32)ed[k].y;
-          if (nd >= kInf) {
-            range_err = 1;
-          } else {
-            const u64 cand = pack(nd, ov[k]);
-            if (cand < sx[k]) {
-              const u64 old = atomicMin((unsigned long long *)(s + ed[k].x), cand);
-              if (cand < old) {
-                ++n_imp;
-                if (nd < thresh) {
-                  want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
-                } else {
-                  far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
-                  if (far[k] && nd < fmin) fmin = nd;
-                }
-              }
-            }
-          }
+          if (nd[k] >= kInf) range_err = 1;
+          else tried[k] = cand[k] < sx[k];
         }
       }
     }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      old[k] = tried[k] ? atomicMin((unsigned long long *)(s + ed[k].x), cand[k]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (tried[k] && cand[k] < old[k]) {
+        ++n_imp;
+        if (nd[k] < thresh) want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
+        else far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (far[k] && nd[k] < fmin) fmin = nd[k];
     enqueue(next, row, tx, want, K, n_enq);
     if (pile) far_append(pile, pcnt, far_min, fst, tx, far, K, fmin);
   }
@@ -465,17 +469,18 @@ struct FlagOp {
   __device__ __forceinline__ u64 load(int2 e) { return __ldcg(flag + e.x); }
   __device__ __forceinline__ void run(const bool *act, const u32 *, const u32 *,
                                       const int2 *ed, const u64 *sx) {
-    u32 tx[K];
+    u32 tx[K], prev[K];
     bool want[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k) {   // every exchange in flight before any is read
       tx[k] = (u32)ed[k].x;
-      want[k] = false;
-      if (act[k]) {
-        ++n_edges;
-        if ((u32)sx[k] != ptag) want[k] = atomicExch(flag + ed[k].x, ptag) != ptag;
-        n_aff += want[k];
-      }
+      n_edges += act[k];
+      prev[k] = act[k] && (u32)sx[k] != ptag ? atomicExch(flag + ed[k].x, ptag) : ptag;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      want[k] = prev[k] != ptag;
+      n_aff += want[k];
     }
     enqueue(next, row, tx, want, K, n_enq);
   }
@@ -767,13 +772,27 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
   const u32 n = (u32)a.n;
   const u32 gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-  for (u32 v = gt; v < n; v += nt) {
-    const u64 sv = ld_cg_u64(a.s + v);
-    const u32 p = parent_of(sv);
-    __stcg(a.jmp + v, dist_of(sv) >= kInf ? kJumpCut : (p == kNoParent ? kJumpRoot : p));
+  // every sweep below takes K vertices per thread at a time and issues all
+  // their loads before it stores anything, so their latencies overlap
+  for (u32 v0 = gt; v0 < n; v0 += nt * K) {
+    u64 sv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const u32 v = v0 + (u32)k * nt;
+      sv[k] = v < n ? ld_cg_u64(a.s + v) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const u32 v = v0 + (u32)k * nt;
+      const u32 p = parent_of(sv[k]);
+      if (v < n)
+        __stcg(a.jmp + v, dist_of(sv[k]) >= kInf ? kJumpCut : (p == kNoParent ? kJumpRoot : p));
+    }
   }
   target += gridDim.x;
   bool stop = grid_sync(bar, target, c, a.lim);
+  const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
+  u64 dummy = 0;
   for (;;) {
     if (stop) break;
     if (jumps > 0 && ld_cg_u32(jcnt_ptr(c, (jumps - 1) % 3)) == 0) break;
@@ -782,14 +801,34 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
       break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile u32 *)jcnt_ptr(c, (jumps + 1) % 3) = 0u;
+    // a vertex whose word turns into kJumpCut in this pass had a distance
+    // (its word was an ancestor) and a cut lies on its tree path: it loses
+    // the distance and joins A here, exactly once
     u32 act = 0;
-    for (u32 v = gt; v < n; v += nt) {
-      const u32 j = __ldcg(a.jmp + v);
-      if (j < kJumpRoot) {
-        const u32 ja = __ldcg(a.jmp + j);
-        __stcg(a.jmp + v, ja);
-        act += ja < kJumpRoot ? 1u : 0u;
+    for (u32 w0 = gw * 32 * K; w0 < n; w0 += nw * 32 * K) {
+      u32 v[K], j[K], ja[K];
+      bool hit[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        v[k] = w0 + lane + 32 * k;
+        j[k] = v[k] < n ? __ldcg(a.jmp + v[k]) : kJumpRoot;
       }
+#pragma unroll
+      for (int k = 0; k < K; ++k) ja[k] = j[k] < kJumpRoot ? __ldcg(a.jmp + j[k]) : j[k];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        hit[k] = false;
+        if (j[k] < kJumpRoot) {
+          __stcg(a.jmp + v[k], ja[k]);
+          act += ja[k] < kJumpRoot ? 1u : 0u;
+          if (ja[k] == kJumpCut) {
+            a.s[v[k]] = kInfPack;
+            hit[k] = true;
+            ++n_aff;
+          }
+        }
+      }
+      enqueue(qa, a.rev.row, v, hit, K, dummy);
     }
     u32 total;
     block_excl_scan(act, scratch, &total);
@@ -798,27 +837,7 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
     target += gridDim.x;
     stop = grid_sync(bar, target, c, a.lim);
   }
-  // the vertices cut by a jump lose their distance and join A
-  if (!stop && !capped) {
-    const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
-    u64 dummy = 0;
-    for (u32 base = gw * 32; base < n; base += nw * 32) {
-      const u32 i = base + lane;
-      bool hit[K] = {};
-      u32 v[K] = {};
-      v[0] = i;
-      if (i < n && __ldcg(a.jmp + i) == kJumpCut) {
-        const u64 sv = ld_cg_u64(a.s + i);
-        if (dist_of(sv) < kInf) {
-          a.s[i] = kInfPack;
-          hit[0] = true;
-        }
-      }
-      n_aff += hit[0];
-      enqueue(qa, a.rev.row, v, hit, 1, dummy);
-    }
-    flush_queue(qa, scratch);
-  }
+  flush_queue(qa, scratch);
   JumpState out;
   out.target = target;
   out.n_aff = n_aff;
@@ -1433,24 +1452,30 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   int range_err = 0;
   u64 n_enq = 0;
-  for (long long base = gw * 32; base < a.n_items; base += nw * 32) {
+  // the forward-store items are the first half of the sorted batch (the
+  // store bit is the key's top bit)
+  const long long nfw = a.n_items / 2;
+  for (long long base = gw * 32; base < nfw; base += nw * 32) {
     const long long i = base + lane;
     bool want[K] = {};
     u32 v[K] = {};
-    if (i < a.n_items) {
+    if (i < nfw) {
       const u64 key = a.keys[i];
+      const unsigned char fl = a.flags[i];
+      const u32 w = a.vals[i];
+      const u32 u = (u32)((key >> (a.bits + 1)) & cmask);
+      v[0] = (u32)((key >> 1) & cmask);
       // forward-store insertion that the merge applied
-      if ((key >> (2 * a.bits + 1)) == 0 && (key & 1) && (a.flags[i] & 1)) {
-        const u32 u = (u32)((key >> (a.bits + 1)) & cmask);
-        v[0] = (u32)((key >> 1) & cmask);
-        const u32 du = dist_of(ld_cg_u64(a.la.s + u));
+      if ((key & 1) && (fl & 1)) {
+        const u64 su = ld_cg_u64(a.la.s + u), sv = ld_cg_u64(a.la.s + v[0]);
+        const u32 du = dist_of(su);
         if (du < kInf) {
-          const u32 nd = du + a.vals[i];
+          const u32 nd = du + w;
           if (nd >= kInf) {
             range_err = 1;
           } else {
             const u64 cand = pack(nd, u);
-            if (cand < ld_cg_u64(a.la.s + v[0])) {
+            if (cand < sv) {
               const u64 old = atomicMin((unsigned long long *)(a.la.s + v[0]), cand);
               if (cand < old) {
                 atomicMin(&c->seed_min, nd);
