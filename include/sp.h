@@ -489,8 +489,11 @@ sp_status sp_set_batch_graphs(sp_graph *g, int32_t on);
  * splits, [4] far-pile entries moved back, [5] invalidation rounds, [6] of
  * them pointer-jumping passes, [7] ns spent in single-block rounds, [8] ns
  * spent in the push loop, [9] the bound that ended the last call early (0
- * none, 1 a round or pass cap, 2 a barrier wait).  k (<= 10) entries are
- * written; the figures are those of the last synchronous call.
+ * none, 1 a round or pass cap, 2 a barrier wait), [10] where it was hit (1
+ * a loop's round cap, 2 a loop's grid barrier, 3 the wait for a
+ * single-block episode, 4 the batch sort's grid barrier), [11] the round,
+ * barrier index or episode there.  k (<= 12) entries are written; the
+ * figures are those of the last synchronous call.
  */
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
 

@@ -166,7 +166,36 @@ void drop_batch_graphs(sp_graph *g) {
   if (g->bg_graph) cudaGraphDestroy(g->bg_graph);
   g->bg_exec = nullptr;
   g->bg_graph = nullptr;
+  g->bg_sort = g->bg_inval = nullptr;
   g->bg_ready = false;
+}
+
+// The kernel nodes of the captured batch graph that read the batch inputs:
+// the batch sort (every input array) and the invalidation loop (the
+// deletions).  Every other kernel reads the sorted items.
+bool find_input_nodes(sp_graph *g) {
+  g->bg_sort = g->bg_inval = nullptr;
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g->bg_graph, nullptr, &nn) != cudaSuccess) return false;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && cudaGraphGetNodes(g->bg_graph, nodes.data(), &nn) != cudaSuccess) return false;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams p = {};
+    if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess) return false;
+    if (p.func == sp::batch_sort_fn()) g->bg_sort = nd;
+    else if (p.func == sp::inval_fn()) g->bg_inval = nd;
+  }
+  return g->bg_sort != nullptr;
+}
+
+cudaError_t retarget_input_nodes(sp_graph *g, const int *ds, const int *dd, long long nd,
+                                 const int *as, const int *ad, const int *aw, long long na) {
+  cudaError_t e = sp::retarget_batch_sort(g, g->bg_exec, g->bg_sort, ds, dd, nd, as, ad, aw, na);
+  if (e == cudaSuccess && g->bg_inval)
+    e = sp::retarget_inval(g, g->bg_exec, g->bg_inval, ds, dd, nd);
+  return e;
 }
 
 sp_status read_ctl(sp_graph *g) {
@@ -449,11 +478,12 @@ sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
 }
 
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k) {
-  if (!g || !out || k < 0 || k > 10) return SP_EINVAL;
+  if (!g || !out || k < 0 || k > 12) return SP_EINVAL;
   const Ctl &c = *g->ctl_host;
-  const int64_t v[10] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
+  const int64_t v[12] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
                          (int64_t)c.far_moves, c.rounds_inval, c.jumps,
-                         (int64_t)c.local_ns, (int64_t)c.push_ns, c.timeout};
+                         (int64_t)c.local_ns, (int64_t)c.push_ns, c.timeout,
+                         c.to_site, c.to_info};
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return SP_OK;
 }
@@ -535,13 +565,12 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   g->last_na = n_add;
   g->last_timed = (int)timed;
   const bool use_graph = g->batch_graphs && g->stream && nb > 0 && repeat;
-  sp_status rc = ensure_batch_buffers(g, ni,
-                                      inputs_on_device && !use_graph ? 0 : std::max(n_del, n_add));
+  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
   if (rc != SP_OK) return rc;
   auto &b = g->bb;
   const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
   rec(g, timed, 0);
-  if (!inputs_on_device || use_graph) {
+  if (!inputs_on_device) {
     cudaStream_t s = g->stream;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice
                                                  : cudaMemcpyHostToDevice;
@@ -575,6 +604,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
           bool ok = cudaStreamEndCapture(g->stream, &gr) == cudaSuccess && ce == cudaSuccess && gr;
           g->bg_graph = gr;
           ok = ok && cudaGraphInstantiate(&g->bg_exec, g->bg_graph, 0) == cudaSuccess;
+          ok = ok && find_input_nodes(g);
           if (ok) {
             g->bg_ready = true;
             g->bg_gen = g->gen;
@@ -588,6 +618,12 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
         }
         g->capturing = -1;
         cudaGetLastError();
+      }
+      // a replay reads this call's inputs: the two nodes that read them are
+      // pointed at them (no copy of the batch)
+      if (g->bg_ready && retarget_input_nodes(g, ds, dd, n_del, as, ad, aw, n_add) != cudaSuccess) {
+        cudaGetLastError();
+        drop_batch_graphs(g);
       }
       if (g->bg_ready) {
         e = cudaGraphLaunch(g->bg_exec, g->stream);

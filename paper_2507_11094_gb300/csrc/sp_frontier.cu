@@ -93,7 +93,7 @@ __device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Li
       while (ld_acquire_u64(bar) < target) {
         if (ld_cg_i32(&c->timeout) != 0) break;
         if (globaltimer_ns() - t0 > lim.wait_ns) {
-          atomicCAS(&c->timeout, 0, 2);
+          raise_timeout(c, 2, 2, (u32)(target / gridDim.x));
           break;
         }
         __nanosleep(nap);
@@ -1095,7 +1095,7 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
         if (ld_cg_i32(&c->timeout) != 0) break;
         const u64 beat = ld_cg_u64(&c->lbeat), now = globaltimer_ns();
         if (now - (beat > t0 ? beat : t0) > a.lim.wait_ns) {
-          atomicCAS(&c->timeout, 0, 2);
+          raise_timeout(c, 2, 3, lep);
           break;
         }
         __nanosleep(nap);
@@ -1379,7 +1379,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       vc->rounds_inval = round + jumps;
       vc->jumps = jumps;
     }
-    if (capped) atomicCAS(&c->timeout, 0, 1);
+    if (capped) raise_timeout(c, 1, 1, round + jumps);
   }
 }
 
@@ -1840,6 +1840,26 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) 
   if (op == kOpPush) return cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a);
   if (op == kOpInval) return cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
   return cudaLaunchKernelEx(&cfg, k_loop<kOpFlag>, a);
+}
+
+const void *inval_fn() { return (const void *)k_loop<kOpInval>; }
+
+cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node, const int *ds,
+                           const int *dd, long long nd) {
+  LoopArgs a = make_args(g);
+  a.del_src = ds;
+  a.del_dst = dd;
+  a.n_del = nd;
+  int blocks = g->loop_blocks_inval;
+  if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
+  void *args[1] = {&a};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)k_loop<kOpInval>;
+  p.gridDim = dim3((unsigned)blocks);
+  p.blockDim = dim3(kPersistThreads);
+  p.sharedMemBytes = (unsigned)kLoopSmem;
+  p.kernelParams = args;
+  return cudaGraphExecKernelNodeSetParams(ex, node, &p);
 }
 
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches) {

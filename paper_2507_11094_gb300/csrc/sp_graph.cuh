@@ -150,6 +150,7 @@ struct sp_graph {
   // one graph per batch shape; the phase timing events are nodes inside it
   cudaGraph_t bg_graph = nullptr;
   cudaGraphExec_t bg_exec = nullptr;
+  cudaGraphNode_t bg_sort = nullptr, bg_inval = nullptr;   // nodes that read the inputs
   bool bg_ready = false;
   int capturing = -1;                    // >= 0 while the pipeline is captured
   unsigned long long bg_gen = 0;
@@ -196,6 +197,15 @@ size_t batch_sort_tmp_bytes(int max_blocks);
 cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long long nd,
                               const int *as, const int *ad, const int *aw, long long na,
                               int *launches);
+// the captured batch-sort / invalidation node of an instantiated graph,
+// pointed at another batch of the same shape
+const void *batch_sort_fn();
+cudaError_t retarget_batch_sort(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node,
+                                const int *ds, const int *dd, long long nd, const int *as,
+                                const int *ad, const int *aw, long long na);
+const void *inval_fn();
+cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node, const int *ds,
+                           const int *dd, long long nd);
 void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
                         const int *ad, const int *aw, long long na, int *launches);
 

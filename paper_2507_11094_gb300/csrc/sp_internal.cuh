@@ -68,6 +68,9 @@ struct Ctl {
   int range_err;         // a candidate distance reached SP_INF
   int timeout;           // 1 = round cap, 2 = barrier wait bound
   int bad;               // an internal bounds check failed (write skipped)
+  u32 to_site;           // the wait that raised timeout: 1 round cap, 2 loop barrier,
+                         // 3 single-block episode, 4 batch-sort barrier
+  u32 to_info;           // its round, barrier index or episode
   // grid barriers of the two persistent loops (monotone arrival counts)
   alignas(128) u64 bar_inval;
   alignas(128) u64 bar_push;
@@ -159,6 +162,15 @@ __device__ __forceinline__ u32 ld_acquire_u32(const u32 *p) {
 __device__ __forceinline__ void st_release_u32(u32 *p, u32 v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Raise the call's timeout (kind 1 = a cap, 2 = a wait bound) and, for
+// the first raiser only, record where it happened.
+__device__ __forceinline__ void raise_timeout(Ctl *c, int kind, u32 site, u32 info) {
+  if (atomicCAS(&c->timeout, 0, kind) == 0) {
+    c->to_site = site;
+    c->to_info = info;
+  }
+}
+
 __device__ __forceinline__ u64 globaltimer_ns() {
   u64 t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -278,7 +278,7 @@ __device__ __forceinline__ bool sort_sync(unsigned long long *bar, unsigned long
       while (ld_acq_u64(bar) < target) {
         if (ld_cg_i32(&c->timeout) != 0) break;
         if (globaltimer_ns() - t0 > wait_ns) {
-          atomicCAS(&c->timeout, 0, 2);
+          raise_timeout(c, 2, 4, (u32)(target / gridDim.x));
           break;
         }
         __nanosleep(nap);
@@ -651,16 +651,16 @@ size_t batch_sort_tmp_bytes(int max_blocks) {
   return (size_t)kBins * std::max(max_blocks, 1) * sizeof(u32) + 256;
 }
 
-cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long long nd,
-                              const int *as, const int *ad, const int *aw, long long na,
-                              int *launches) {
+namespace {
+
+// Arguments and grid of the batch sort for these inputs.
+int batch_sort_args(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                    const int *ad, const int *aw, long long na, BatchSortArgs &a) {
   const long long ni = 2 * (nd + na);
-  if (ni == 0) return cudaSuccess;
   BatchBufs &bb = g->bb;
   int G = (int)std::min<long long>((ni + kBTile - 1) / kBTile, g->sort_blocks);
   if (g->loop_blocks_user > 0 && g->loop_blocks_user < G) G = g->loop_blocks_user;
   if (G < 1) G = 1;
-  BatchSortArgs a;
   a.ds = ds; a.dd = dd; a.as = as; a.ad = ad; a.aw = aw;
   a.nd = nd; a.na = na;
   a.n = g->n;
@@ -679,6 +679,19 @@ cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long lo
   a.wait_ns = g->lim.wait_ns;
   a.n_items = (u32)ni;
   a.chunk = (u32)((ni + G - 1) / G);
+  return G;
+}
+
+}  // namespace
+
+const void *batch_sort_fn() { return (const void *)k_batch_sort; }
+
+cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long long nd,
+                              const int *as, const int *ad, const int *aw, long long na,
+                              int *launches) {
+  if (nd + na == 0) return cudaSuccess;
+  BatchSortArgs a;
+  const int G = batch_sort_args(g, ds, dd, nd, as, ad, aw, na, a);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kBT);
@@ -691,6 +704,21 @@ cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long lo
   cfg.numAttrs = 1;
   ++*launches;
   return cudaLaunchKernelEx(&cfg, k_batch_sort, a);
+}
+
+cudaError_t retarget_batch_sort(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node,
+                                const int *ds, const int *dd, long long nd, const int *as,
+                                const int *ad, const int *aw, long long na) {
+  BatchSortArgs a;
+  const int G = batch_sort_args(g, ds, dd, nd, as, ad, aw, na, a);
+  void *args[1] = {&a};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)k_batch_sort;
+  p.gridDim = dim3((unsigned)G);
+  p.blockDim = dim3(kBT);
+  p.sharedMemBytes = (unsigned)kBSmem;
+  p.kernelParams = args;
+  return cudaGraphExecKernelNodeSetParams(ex, node, &p);
 }
 
 void sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, long long n,

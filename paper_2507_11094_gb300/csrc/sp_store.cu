@@ -198,6 +198,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->need_grow = 0;
   c->range_err = 0;
   c->timeout = 0;
+  c->to_site = c->to_info = 0;
   c->bad = 0;
   c->bar_inval = 0;
   c->bar_push = 0;

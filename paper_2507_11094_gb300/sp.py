@@ -184,8 +184,15 @@ def load(build_if_missing: bool = False):
     return lib
 
 
-def _check(rc: int, what: str):
+def _check(rc: int, what: str, h=None):
     if rc != SP_OK:
+        if rc == SP_ETIMEOUT and h is not None:
+            # say which device bound ended the call (loop counters 9..11)
+            out = np.zeros(12, dtype=np.int64)
+            if load().sp_loop_counters(h, out.ctypes.data_as(ctypes.c_void_p), 12) == SP_OK:
+                what = (f"{what} (bound {int(out[9])} at site {int(out[10])}, "
+                        f"index {int(out[11])}; push rounds {int(out[0])}, "
+                        f"single-block {int(out[1])}, invalidation rounds {int(out[5])})")
         raise SpError(rc, what)
 
 
@@ -286,7 +293,7 @@ class Graph:
     def sssp_init(self, source: int, stats: bool = False):
         st = BatchStats() if stats else None
         rc = load().sp_sssp_init(self._h, int(source), ctypes.byref(st) if st else None)
-        _check(rc, "sp_sssp_init")
+        _check(rc, "sp_sssp_init", self._h)
         return st
 
     def apply_batch(self, del_src, del_dst, add_src, add_dst, add_w, stats: bool = False,
@@ -303,7 +310,7 @@ class Graph:
                                    arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
                                    ctypes.byref(st) if st else None)
         if raise_on_error:
-            _check(rc, "sp_apply_batch")
+            _check(rc, "sp_apply_batch", self._h)
             return st
         return rc, st
 
@@ -319,7 +326,7 @@ class Graph:
         st = BatchStats() if stats else None
         rc = load().sp_sssp_init_multi(self._h, arr.ptrs[0], k, int(arr.on_device),
                                        ctypes.byref(st) if st else None)
-        _check(rc, "sp_sssp_init_multi")
+        _check(rc, "sp_sssp_init_multi", self._h)
         return st
 
     def reserve(self, max_updates: int):
@@ -416,7 +423,7 @@ class Graph:
         st = BatchStats() if stats else None
         rc = load().sp_pr_init(self._h, float(damping), float(beta), int(max_iter),
                                ctypes.byref(st) if st else None)
-        _check(rc, "sp_pr_init")
+        _check(rc, "sp_pr_init", self._h)
         return st
 
     def pr_apply_batch(self, del_src, del_dst, add_src, add_dst, add_w, stats: bool = False):
@@ -430,7 +437,7 @@ class Graph:
         rc = load().sp_pr_apply_batch(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
                                       arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
                                       ctypes.byref(st) if st else None)
-        _check(rc, "sp_pr_apply_batch")
+        _check(rc, "sp_pr_apply_batch", self._h)
         return st
 
     def pr_apply(self, batch, stats: bool = False):
@@ -461,7 +468,7 @@ class Graph:
         rc = load().sp_tc_apply_batch(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
                                       arr.ptrs[3], arr.ptrs[4], int(arr.on_device),
                                       ctypes.byref(c), ctypes.byref(st) if st else None)
-        _check(rc, "sp_tc_apply_batch")
+        _check(rc, "sp_tc_apply_batch", self._h)
         return (int(c.value), st) if stats else int(c.value)
 
     def tc_apply(self, batch, stats: bool = False):
@@ -470,11 +477,12 @@ class Graph:
 
     def loop_counters(self) -> dict:
         """Loop counters of the last call (tuning aid)."""
-        out = np.zeros(10, dtype=np.int64)
-        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 10),
+        out = np.zeros(12, dtype=np.int64)
+        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 12),
                "sp_loop_counters")
         keys = ("rounds_push", "local_rounds", "local_episodes", "splits", "far_moves",
-                "rounds_inval", "jumps", "local_ns", "push_ns", "timeout")
+                "rounds_inval", "jumps", "local_ns", "push_ns", "timeout", "timeout_site",
+                "timeout_index")
         return dict(zip(keys, (int(x) for x in out)))
 
     def last_cuda_error(self) -> str:
@@ -523,7 +531,7 @@ class Exec:
         rc = load().sp_apply_batch_finish(self.g._h, ctypes.c_void_p(self.result.data_ptr()),
                                           ctypes.byref(st) if st else None)
         if raise_on_error:
-            _check(rc, "sp_apply_batch_finish")
+            _check(rc, "sp_apply_batch_finish", self.g._h)
             return st
         return rc, st
 

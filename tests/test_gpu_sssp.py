@@ -278,6 +278,9 @@ def test_round_cap_returns_timeout_and_reinit_recovers():
         with pytest.raises(sp.SpError) as e:
             g.sssp_init(0)
         assert e.value.code == sp.SP_ETIMEOUT
+        lc = g.loop_counters()   # the bound says where it was hit: a round cap
+        assert lc["timeout"] == 1 and lc["timeout_site"] == 1 and lc["timeout_index"] == 5
+        assert "site 1" in str(e.value)
         z = np.zeros(0, np.int32)
         rc, _ = g.apply_batch(z, z, z, z, z, raise_on_error=False)
         assert rc == sp.SP_ESTATE
