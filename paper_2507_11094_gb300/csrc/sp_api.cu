@@ -132,11 +132,15 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
   st->alg_bytes[SP_PH_MERGE] = (int64_t)(c.merge_slots * 8 + c.rows_touched * 32 + ni * 21);
   st->alg_bytes[SP_PH_INVAL] =
       (int64_t)(c.affected * (16 + 8 + 8 + 4) + c.inval_edges * 16);
-  st->alg_bytes[SP_PH_PULL] = (int64_t)(c.affected * 16 + c.pull_edges * 16 + c.seeds * 20);
-  st->alg_bytes[SP_PH_ADD] = (int64_t)(c.add_applied * (12 + 16));
+  // the pull and OnAdd run inside the push loop's launch (its first stage),
+  // so their bytes count with the push phase
+  st->alg_bytes[SP_PH_PULL] = 0;
+  st->alg_bytes[SP_PH_ADD] = 0;
   st->alg_bytes[SP_PH_PUSH] =
       (int64_t)(c.push_vertices * (4 + 16 + 8) + c.relaxed * 16 + c.improved * 8 +
-                c.enqueued * (4 + 4 + 4));
+                c.enqueued * (4 + 4 + 4)) +
+      (int64_t)(c.affected * 16 + c.pull_edges * 16 + c.seeds * 20) +
+      (int64_t)(c.add_applied * (12 + 16));
   st->alg_bytes[SP_PH_FINISH] = (int64_t)sizeof(Ctl);
   for (int i = 0; i < SP_NPHASE; ++i) st->ms_phase[i] = 0.f;
   st->ms_total = 0.f;
@@ -251,11 +255,10 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
   rec(g, timed, 3);
   if (e == cudaSuccess && n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, launches);
   rec(g, timed, 4);
-  if (n_del > 0) sp::launch_pull(g, launches);
+  // the pull and OnAdd run as the first stage of the push loop's launch
   rec(g, timed, 5);
-  sp::launch_add(g, ni, launches);
   rec(g, timed, 6);
-  if (e == cudaSuccess) e = sp::launch_push(g, launches);
+  if (e == cudaSuccess) e = sp::launch_push(g, launches, n_del > 0 ? 1 : 0, ni);
   rec(g, timed, 7);
   sp::launch_finish(g, launches);
   rec(g, timed, 8);

@@ -1116,6 +1116,9 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
   return out;
 }
 
+__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
+__device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
+
 template <int OP>
 __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   extern __shared__ u32 dsm[];
@@ -1181,6 +1184,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
     }
     flush_queue(q0, scratch);
+  }
+
+  if (OP == kOpPush) {   // a batch's seeds: the pull over A, then OnAdd
+    if (a.seed_pull) pull_stage(a, &sq, &sqs, scratch);
+    if (a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
   }
 
   // state shared by all blocks (read before the first barrier; only block 0
@@ -1385,17 +1393,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
 
 // --- pull (one pass over A) -----------------------------------------------
 
-__global__ void __launch_bounds__(kLoopThreads) k_pull(LoopArgs a) {
-  __shared__ u32 sv[kStageK], sd[kStageK], ssv[kStageK];
-  __shared__ Stage st, sst;
-  __shared__ u32 scratch[40];
+// Pull stage (block-collective): every vertex of A takes the minimum over
+// its in-edges; the improved ones form the push loop's first frontier
+// (queue slot 0).
+__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
   Ctl *c = a.ctl;
-  if (!repair_enabled(c)) return;
-  if (threadIdx.x == 0) {
-    st.n = 0; st.cap = kStageK; st.vmin = kInf; st.v = sv; st.d = sd;
-    sst.n = 0; sst.cap = kStageK; sst.vmin = kInf; sst.v = ssv; sst.d = nullptr;
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const u64 ac = ld_cg_u64(&c->acnt);
   const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
@@ -1403,7 +1405,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_pull(LoopArgs a) {
   const u32 sgroups = (nsmall + 31) / 32;
   const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
   const u32 tag = ld_cg_u32(&c->epoch);
-  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &st, &sst);
+  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst);
   PullOp op{a.s, a.qflag, tag, q0, a.fwd.row, &c->seed_min};
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
@@ -1423,30 +1425,13 @@ __global__ void __launch_bounds__(kLoopThreads) k_pull(LoopArgs a) {
 
 // --- OnAdd: relax every applied insertion ---------------------------------
 
-struct AddArgs {
-  LoopArgs la;
-  const u64 *keys;
-  const u32 *vals;
-  const unsigned char *flags;
-  long long n_items;
-  int bits;
-};
-
-__global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
-  __shared__ u32 sv[kStageK], sd[kStageK], ssv[kStageK];
-  __shared__ Stage st, sst;
-  __shared__ u32 scratch[40];
-  Ctl *c = a.la.ctl;
-  if (!repair_enabled(c)) return;
-  if (threadIdx.x == 0) {
-    st.n = 0; st.cap = kStageK; st.vmin = kInf; st.v = sv; st.d = sd;
-    sst.n = 0; sst.cap = kStageK; sst.vmin = kInf; sst.v = ssv; sst.d = nullptr;
-  }
-  __syncthreads();
+// OnAdd stage (block-collective): every applied insertion (u, v, w) is
+// relaxed; an improved v joins the push loop's first frontier (slot 0).
+__device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
+  Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   const u32 tag = ld_cg_u32(&c->epoch);
-  const Queue q0 =
-      make_queue(a.la.qent[0], a.la.qown[0], &c->qcnt0, a.la.qsv[0], &c->scnt0, &st, &sst);
+  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst);
   const u64 cmask = (1ull << a.bits) - 1;
   const long long gw = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1467,7 +1452,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
       v[0] = (u32)((key >> 1) & cmask);
       // forward-store insertion that the merge applied
       if ((key & 1) && (fl & 1)) {
-        const u64 su = ld_cg_u64(a.la.s + u), sv = ld_cg_u64(a.la.s + v[0]);
+        const u64 su = ld_cg_u64(a.s + u), sv = ld_cg_u64(a.s + v[0]);
         const u32 du = dist_of(su);
         if (du < kInf) {
           const u32 nd = du + w;
@@ -1476,17 +1461,17 @@ __global__ void __launch_bounds__(kLoopThreads) k_add(AddArgs a) {
           } else {
             const u64 cand = pack(nd, u);
             if (cand < sv) {
-              const u64 old = atomicMin((unsigned long long *)(a.la.s + v[0]), cand);
+              const u64 old = atomicMin((unsigned long long *)(a.s + v[0]), cand);
               if (cand < old) {
                 atomicMin(&c->seed_min, nd);
-                want[0] = atomicExch(a.la.qflag + v[0], tag) != tag;
+                want[0] = atomicExch(a.qflag + v[0], tag) != tag;
               }
             }
           }
         }
       }
     }
-    enqueue(q0, a.la.fwd.row, v, want, 1, n_enq);
+    enqueue(q0, a.fwd.row, v, want, 1, n_enq);
   }
   flush_queue(q0, scratch);
   u64 q = warp_sum(n_enq);
@@ -1790,6 +1775,12 @@ LoopArgs make_args(sp_graph *g) {
   a.n_del = 0;
   a.prflag = g->prflag;
   a.ptag = g->prtag;
+  a.seed_pull = 0;
+  a.keys = g->bb.keys;
+  a.vals = g->bb.vals;
+  a.flags = g->bb.flags;
+  a.n_items = 0;
+  a.bits = g->bits;
   return a;
 }
 
@@ -1870,29 +1861,10 @@ cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd
   return launch_loop(g, kOpInval, a, launches);
 }
 
-void launch_pull(sp_graph *g, int *launches) {
+cudaError_t launch_push(sp_graph *g, int *launches, int pull, long long n_items) {
   LoopArgs a = make_args(g);
-  k_pull<<<(unsigned)std::max(1, g->num_sms), kLoopThreads, 0, g->stream>>>(a);   // one wave
-  ++*launches;
-}
-
-void launch_add(sp_graph *g, long long n_items, int *launches) {
-  if (n_items == 0) return;
-  AddArgs a;
-  a.la = make_args(g);
-  a.keys = g->bb.keys;
-  a.vals = g->bb.vals;
-  a.flags = g->bb.flags;
+  a.seed_pull = pull;
   a.n_items = n_items;
-  a.bits = g->bits;
-  long long blocks = (n_items + kLoopThreads - 1) / kLoopThreads;
-  blocks = std::min<long long>(std::max<long long>(blocks, 1), g->num_sms);   // one wave
-  k_add<<<(unsigned)blocks, kLoopThreads, 0, g->stream>>>(a);
-  ++*launches;
-}
-
-cudaError_t launch_push(sp_graph *g, int *launches) {
-  LoopArgs a = make_args(g);
   return launch_loop(g, kOpPush, a, launches);
 }
 

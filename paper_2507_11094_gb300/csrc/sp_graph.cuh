@@ -101,6 +101,14 @@ struct LoopArgs {
   // PageRank flags: prflag[v] == ptag marks v for the current phase
   u32 *prflag;
   u32 ptag;
+  // first stage of the push loop of a batch (before its first barrier): the
+  // pull over the affected list A, and OnAdd over the sorted batch items
+  int seed_pull;
+  const u64 *keys;
+  const u32 *vals;
+  const unsigned char *flags;
+  long long n_items;
+  int bits;
 };
 
 }  // namespace sp
@@ -215,9 +223,9 @@ void launch_init(sp_graph *g, int source, int *launches);
 void launch_init_multi(sp_graph *g, const int *src_d, int k, int *launches);
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd,
                          int *launches);
-void launch_pull(sp_graph *g, int *launches);
-void launch_add(sp_graph *g, long long n_items, int *launches);
-cudaError_t launch_push(sp_graph *g, int *launches);
+// push fixedPoint; for a batch (pull != 0 or n_items > 0) its first stage
+// pulls over A and relaxes the applied insertions
+cudaError_t launch_push(sp_graph *g, int *launches, int pull = 0, long long n_items = 0);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
 // sp_tc.cu
 void launch_tc_sym_check(sp_graph *g, int *launches);
