@@ -196,11 +196,18 @@ def _check(rc: int, what: str, h=None):
         raise SpError(rc, what)
 
 
+_TORCH = None
+
+
 def _torch():
-    import torch
-    if not torch.cuda.is_available():
-        raise RuntimeError("CUDA is not available: libsp has no CPU path")
-    return torch
+    """torch, once CUDA is known to be there (checked on the first call)."""
+    global _TORCH
+    if _TORCH is None:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: libsp has no CPU path")
+        _TORCH = torch
+    return _TORCH
 
 
 def _is_cuda_tensor(x) -> bool:
@@ -224,8 +231,11 @@ class _Arrays:
                 continue
             if self.on_device:
                 t = _torch()
-                tdt = {np.int32: t.int32, np.int64: t.int64}[dt]
-                a = a.to(tdt).contiguous()
+                tdt = t.int32 if dt is np.int32 else t.int64
+                if a.dtype != tdt:   # converted only when needed (each call costs µs)
+                    a = a.to(tdt)
+                if not a.is_contiguous():
+                    a = a.contiguous()
                 self.keep.append(a)
                 self.ptrs.append(ctypes.c_void_p(a.data_ptr()))
             else:
