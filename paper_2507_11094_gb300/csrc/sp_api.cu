@@ -60,14 +60,14 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     long long old = b.cap_items;
     al.put(b.keys, old * 8); al.put(b.keys_alt, old * 8);
     al.put(b.vals, old * 4); al.put(b.vals_alt, old * 4);
-    al.put(b.flags, old); al.put(b.itemv, old * 8); al.put(b.item_pref, old * 8);
+    al.put(b.flags, old); al.put(b.item_pref, old * 8);
     al.put(b.opos, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
     al.put(b.tmp, b.tmp_bytes);
     b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
     b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
     b.flags = (unsigned char *)al.get(c);
-    b.itemv = (u64 *)al.get(c * 8); b.item_pref = (u64 *)al.get(c * 8);
+    b.item_pref = (u64 *)al.get(c * 8);
     b.opos = (u32 *)al.get(c * 4);
     b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
     b.tmp_bytes = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
@@ -75,7 +75,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.tmp = al.get(b.tmp_bytes);
     b.cap_items = c;
     ++g->gen;
-    if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags || !b.itemv ||
+    if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags ||
         !b.item_pref || !b.opos || !b.seg || !b.tmp) {
       return SP_ENOMEM;
     }
@@ -307,7 +307,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   long long c = b.cap_items;
   al.put(b.keys, c * 8); al.put(b.keys_alt, c * 8);
   al.put(b.vals, c * 4); al.put(b.vals_alt, c * 4);
-  al.put(b.flags, c); al.put(b.itemv, c * 8); al.put(b.item_pref, c * 8);
+  al.put(b.flags, c); al.put(b.item_pref, c * 8);
   al.put(b.opos, c * 4);
   al.put(b.seg, c * sizeof(sp::Seg));
   al.put(b.strips, (size_t)b.strips_cap * 8);
@@ -380,7 +380,9 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   g->loop_blocks_push = sp::loop_blocks(0, g->num_sms);
   g->loop_blocks_inval = sp::loop_blocks(1, g->num_sms);
   g->sort_blocks = sp::batch_sort_blocks(g->num_sms);
-  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 || g->sort_blocks <= 0) {
+  g->count_blocks = sp::count_blocks(g->num_sms);
+  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 || g->sort_blocks <= 0 ||
+      g->count_blocks <= 0) {
     delete g;
     return SP_ECUDA;
   }

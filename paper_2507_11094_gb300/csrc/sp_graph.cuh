@@ -63,9 +63,8 @@ struct BatchBufs {
   long long cap_items = 0;
   u64 *keys = nullptr, *keys_alt = nullptr;
   u32 *vals = nullptr, *vals_alt = nullptr;
-  unsigned char *flags = nullptr;   // per item: bit0 = applied
-  u64 *itemv = nullptr;             // per item: applied del (1) | applied add (1<<32)
-  u64 *item_pref = nullptr;         // exclusive scan of itemv
+  unsigned char *flags = nullptr;   // per item: bit0 = applied, bit1 = edge was present
+  u64 *item_pref = nullptr;         // exclusive prefix of the applied updates per item
   u32 *opos = nullptr;              // per item: old entries of its row with a smaller col
   Seg *seg = nullptr;
   int2 *strips = nullptr;           // merge strips: (segment, first old entry)
@@ -179,6 +178,7 @@ struct sp_graph {
   long long wait_ns_user = 0;
   int loop_blocks_push = 0, loop_blocks_inval = 0;
   int sort_blocks = 0;          // co-resident blocks of the batch sort
+  int count_blocks = 0;         // co-resident blocks of the count pass
   int loop_blocks_user = 0;
   cudaEvent_t ev[SP_NPHASE + 1] = {};
   long long async_ni = 0;       // items of the last enqueued async batch
@@ -196,6 +196,7 @@ sp_status store_export(sp_graph *g, const sp::Store *st, long long *row_off_d,
 sp_status store_grow_pool(sp_graph *g, sp::Store *st, long long min_pool_slots);
 sp_status ensure_owner_tables(sp_graph *g);
 void launch_ctl_reset(sp_graph *g, int full, int *launches);
+int count_blocks(int num_sms);
 void launch_count(sp_graph *g, long long n_items, int *launches);
 void launch_merge(sp_graph *g, long long n_items, int *launches);
 void launch_finish(sp_graph *g, int *launches);

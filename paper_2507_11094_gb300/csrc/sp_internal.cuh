@@ -75,6 +75,7 @@ struct Ctl {
   alignas(128) u64 bar_inval;
   alignas(128) u64 bar_push;
   alignas(128) u64 bar_sort;       // the batch sort's grid barrier
+  alignas(128) u64 bar_count;      // the count pass's grid barrier
   // loop bookkeeping shared across launches
   alignas(128) u32 epoch;          // dedupe tag of the last frontier built
   u32 phase;                       // far dedupe tag of the last phase
@@ -176,6 +177,46 @@ __device__ __forceinline__ u64 globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ u64 ld_acquire_u64_(const u64 *p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of a cooperative launch on a monotone arrival count (zeroed
+// when the call starts): barrier k waits for k * gridDim.x arrivals.  A wait
+// is bounded by wait_ns; one that runs out raises the call's timeout (kind
+// 2, at `site`) and SP_ETIMEOUT status, and every later wait returns at
+// once.  Returns whether a timeout was raised, the same in every thread.
+// Callers use it before anything has changed, so the status leaves the
+// graph as it was.
+__device__ __forceinline__ bool coop_barrier(u64 *bar, u64 target, Ctl *c, u64 wait_ns,
+                                             u32 site) {
+  __shared__ int s_stop;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd((unsigned long long *)bar, 1ull);
+    if (ld_acquire_u64_(bar) < target) {
+      const u64 t0 = globaltimer_ns();
+      u32 nap = 32;
+      while (ld_acquire_u64_(bar) < target) {
+        if (ld_cg_i32(&c->timeout) != 0) break;
+        if (globaltimer_ns() - t0 > wait_ns) {
+          raise_timeout(c, 2, site, (u32)(target / gridDim.x));
+          break;
+        }
+        __nanosleep(nap);
+        if (nap < 256) nap += nap >> 1;
+      }
+    }
+    s_stop = ld_cg_i32(&c->timeout) != 0;
+    if (s_stop) atomicCAS(&c->status, 0, SP_ETIMEOUT);
+  }
+  __syncthreads();
+  return s_stop != 0;
+}
+
 __device__ __forceinline__ u32 lanemask_lt() {
   u32 m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

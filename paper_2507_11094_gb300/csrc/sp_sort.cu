@@ -256,42 +256,6 @@ __device__ __forceinline__ u32 bscan512(u32 x, u32 *ws, u32 *total) {
   return r;
 }
 
-__device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid barrier on a monotone arrival count (zeroed when the call starts).
-// A wait is bounded by wait_ns; one that runs out raises ctl->timeout and
-// every later wait returns at once.  Same answer in every thread.
-__device__ __forceinline__ bool sort_sync(unsigned long long *bar, unsigned long long target,
-                                          Ctl *c, unsigned long long wait_ns) {
-  __shared__ int s_stop;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1ull);
-    if (ld_acq_u64(bar) < target) {
-      const unsigned long long t0 = globaltimer_ns();
-      u32 nap = 32;
-      while (ld_acq_u64(bar) < target) {
-        if (ld_cg_i32(&c->timeout) != 0) break;
-        if (globaltimer_ns() - t0 > wait_ns) {
-          raise_timeout(c, 2, 4, (u32)(target / gridDim.x));
-          break;
-        }
-        __nanosleep(nap);
-        if (nap < 256) nap += nap >> 1;
-      }
-    }
-    s_stop = ld_cg_i32(&c->timeout) != 0;
-    if (s_stop) atomicCAS(&c->status, 0, SP_ETIMEOUT);   // nothing has changed yet
-  }
-  __syncthreads();
-  return s_stop != 0;
-}
-
 // Lanes of the warp whose valid item has the same 9-bit digit (the answer of
 // a match_any, built from one ballot per digit bit).
 __device__ __forceinline__ u32 digit_peers(u32 d, bool valid) {
@@ -331,8 +295,8 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
   const u32 G = gridDim.x, b = blockIdx.x;
   const u32 cb = min(b * a.chunk, a.n_items), ce = min(cb + a.chunk, a.n_items);
   const bool one = ce - cb <= (u32)kBTile;           // the chunk is one sub-tile
-  unsigned long long *bar = (unsigned long long *)&c->bar_sort;
-  unsigned long long nbar = 0;
+  u64 *bar = &c->bar_sort;
+  u64 nbar = 0;
   const long long nb = a.nd + a.na;
   const int bits = a.bits;
   const u32 lt = lanemask_lt();
@@ -395,7 +359,7 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
   a.tab[(size_t)b * kBins + t] = s_hist[t];
 
   for (int p = 0; p < a.passes; ++p) {
-    if (sort_sync(bar, ++nbar * G, c, a.wait_ns)) return;
+    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4)) return;
     const int shift = p * kBits;
     // digit bases of this chunk: thread t sums digits 4*(t % 128) .. +3 over
     // the rows q = t / 128 (mod 4) with 16-byte loads; the four partial sums
@@ -509,7 +473,7 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
       s_off[t] += s_hist[t];
       __syncthreads();
     }
-    if (sort_sync(bar, ++nbar * G, c, a.wait_ns)) return;
+    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4)) return;
     if (p + 1 < a.passes) {   // the next digit's counts over this chunk
       const int nshift = shift + kBits;
       s_hist[t] = 0;

@@ -203,6 +203,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->bar_inval = 0;
   c->bar_push = 0;
   c->bar_sort = 0;
+  c->bar_count = 0;
   c->qcnt0 = c->qcnt1 = c->qcnt2 = c->acnt = 0;
   c->scnt0 = c->scnt1 = c->scnt2 = c->ascnt = 0;
   c->fcnt0 = c->fcnt1 = c->fcnt2 = 0;
@@ -280,98 +281,201 @@ struct CountArgs {
   const u32 *vals;
   Seg *seg;
   unsigned char *flags;
-  u64 *itemv;
-  const u64 *item_pref;
+  u64 *item_pref;      // exclusive prefix of the applied (ins << 32 | dels), n_items + 1
   u32 *opos;
   int2 *strips;
+  u64 *tab;            // per-block totals of the prefix
   Store st[2];
   int bits;
   float slack;
   u32 n_items;
+  u32 chunk;           // items per block
   int n;
+  u64 wait_ns;
 };
 
 // The merge works on strips of kStrip old entries of a row, one warp each.
 constexpr int kStrip = 256;
 
-// One thread per batch item: does this deletion / insertion apply?
-//  - a deletion applies if the edge is in the row and it is the first
-//    deletion of that edge in the batch;
-//  - among the insertions of one edge the smallest weight is the candidate
-//    (first on ties); it applies if the edge is absent after the deletions.
-// Every item also records where its col falls in the old row (opos: the
-// number of old entries with a smaller col) and whether the edge was there
-// (flags bit 1), which is all the merge needs to place it.
-__global__ void __launch_bounds__(kThreads) k_count_items(CountArgs a) {
+constexpr int kCT = 256;              // threads per block of the count pass
+constexpr int kCI = 4;                // items per thread per sub-tile
+constexpr int kCTile = kCT * kCI;
+
+__device__ __forceinline__ u64 warp_incl_scan_u64(u64 x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 lo = __shfl_up_sync(kFull, (u32)x, o), hi = __shfl_up_sync(kFull, (u32)(x >> 32), o);
+    if (lane >= o) x += ((u64)hi << 32) | lo;
+  }
+  return x;
+}
+
+// Block-wide exclusive prefix of one u64 per thread; the block total goes to
+// *total.  ws holds one word per warp.
+__device__ __forceinline__ u64 block_excl_scan_u64(u64 x, u64 *ws, u64 *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const u64 incl = warp_incl_scan_u64(x);
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    u64 v = lane < nwarps ? ws[lane] : 0ull;
+    v = warp_incl_scan_u64(v);
+    if (lane < nwarps) ws[lane] = v;
+  }
+  __syncthreads();
+  const u64 r = (warp ? ws[warp - 1] : 0ull) + incl - x;
+  *total = ws[nwarps - 1];
+  __syncthreads();
+  return r;
+}
+
+// The count pass in one cooperative launch; block b owns items
+// [b*chunk, (b+1)*chunk).
+//  1. Items.  A deletion applies if the edge is in the row and it is the
+//     first deletion of that edge in the batch; among the insertions of one
+//     edge the smallest weight is the candidate (first on ties), and it
+//     applies if the edge is absent after the deletions.  Every item also
+//     records where its col falls in the old row (opos: the old entries with
+//     a smaller col) and whether the edge was there (flags bit 1), which is
+//     all the merge needs to place it.  Each thread advances the binary
+//     searches of kCI items in lockstep, so their loads overlap.
+//  2. The exclusive prefix of the applied (ins << 32 | dels) over all items
+//     (block scans, then the block bases after a grid barrier).
+//  3. One thread per touched row (after a second barrier): new size,
+//     destination (the row's alternate region, or a fresh pair of regions in
+//     the spare pool when the row outgrows its capacity), and the row's
+//     strips of kStrip old entries (one strip for a row with fewer), the
+//     merge's units.
+__global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
+  __shared__ u32 scratch[40];
+  __shared__ u64 ws64[kCT / 32];
+  __shared__ u64 s_run;
+  __shared__ u64 sums[7];
   Ctl *c = a.ctl;
-  if (ld_cg_i32(&c->status) != 0) return;
+  if (ld_cg_i32(&c->status) != 0) return;   // the same answer in every block
+  const u32 G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const u32 ni = a.n_items;
+  const u32 cb = min(b * a.chunk, ni), ce = min(cb + a.chunk, ni);
   const u64 cmask = (1ull << a.bits) - 1;
+  u64 *bar = &c->bar_count;
   u64 del_ok = 0, del_abs = 0, add_ok = 0, add_pres = 0;
-  const long long ni = a.n_items;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < ni;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long i = base + threadIdx.x;
-    if (i < ni) {
-      const u64 key = a.keys[i];
-      const int dir = (int)(key >> (2 * a.bits + 1));
-      const int row = (int)((key >> (a.bits + 1)) & cmask);
-      const int col = (int)((key >> 1) & cmask);
-      const Store &st = a.st[dir];
-      const RowMeta rm = st.row[row];
-      const int2 *old = st.adj + rm.start;
-      const int j = row_lower_bound(old, rm.deg, col);
-      const bool present = j < rm.deg && __ldg(&old[j].x) == col;
+  if (t == 0) s_run = 0;
+  if (t < 7) sums[t] = 0;
+  __syncthreads();
+
+  for (u32 tb = cb; tb < ce; tb += kCTile) {
+    u64 key[kCI], pk[kCI], nk[kCI];
+    int col[kCI], lo[kCI], hi[kCI], deg[kCI], dir[kCI];
+    const int2 *old[kCI];
+    bool val[kCI];
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {
+      const u32 i = tb + k * kCT + t;
+      val[k] = i < ce;
+      key[k] = val[k] ? a.keys[i] : 0ull;
+      pk[k] = val[k] && i > 0 ? a.keys[i - 1] : ~0ull;
+      nk[k] = val[k] && i + 1 < ni ? a.keys[i + 1] : ~0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {
+      dir[k] = (int)(key[k] >> (2 * a.bits + 1));
+      const int row = (int)((key[k] >> (a.bits + 1)) & cmask);
+      col[k] = (int)((key[k] >> 1) & cmask);
+      const Store &st = a.st[dir[k] & 1];
+      RowMeta rm;
+      rm.start = 0;
+      rm.deg = 0;
+      if (val[k]) rm = st.row[row];
+      old[k] = st.adj + rm.start;
+      lo[k] = 0;
+      hi[k] = deg[k] = rm.deg;
+    }
+    for (;;) {   // binary searches in lockstep: every load of a step in flight together
+      bool act = false;
+      int mid[kCI], x[kCI];
+#pragma unroll
+      for (int k = 0; k < kCI; ++k) {
+        act |= lo[k] < hi[k];
+        mid[k] = (lo[k] + hi[k]) >> 1;
+        x[k] = lo[k] < hi[k] ? __ldg(&old[k][mid[k]].x) : 0;
+      }
+      if (!act) break;
+#pragma unroll
+      for (int k = 0; k < kCI; ++k)
+        if (lo[k] < hi[k]) {
+          if (x[k] < col[k]) lo[k] = mid[k] + 1; else hi[k] = mid[k];
+        }
+    }
+    u64 iv[kCI];
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {
+      const int cl = lo[k] < deg[k] ? __ldg(&old[k][lo[k]].x) : -1;
+      iv[k] = 0;
+      if (!val[k]) continue;
+      const u32 i = tb + k * kCT + t;
+      const bool present = cl == col[k];
       const unsigned char pbit = present ? 2 : 0;
-      a.opos[i] = (u32)j;
-      if ((key & 1) == 0) {
-        const bool applied = present && !(i > 0 && a.keys[i - 1] == key);
+      a.opos[i] = (u32)lo[k];
+      if ((key[k] & 1) == 0) {
+        const bool applied = present && pk[k] != key[k];
         a.flags[i] = (applied ? 1 : 0) | pbit;
-        a.itemv[i] = applied ? 1ull : 0ull;
-        if (dir == 0) { applied ? ++del_ok : ++del_abs; }
-      } else if (i == 0 || a.keys[i - 1] != key) {  // first insertion of this edge
-        long long j2 = i + 1, best = i;
-        u32 bw = a.vals[i];
-        while (j2 < ni && a.keys[j2] == key) {
-          const u32 w2 = a.vals[j2];
-          if (w2 < bw) { bw = w2; best = j2; }
-          ++j2;
+        iv[k] = applied ? 1ull : 0ull;
+        if (dir[k] == 0) { applied ? ++del_ok : ++del_abs; }
+      } else {
+        // the run of insertions of this edge (almost always this item alone)
+        u32 first = i, last = i;
+        bool best = true;
+        if (pk[k] == key[k] || nk[k] == key[k]) {
+          while (first > 0 && a.keys[first - 1] == key[k]) --first;
+          while (last + 1 < ni && a.keys[last + 1] == key[k]) ++last;
+          u32 bi = first, bw = a.vals[first];
+          for (u32 q = first + 1; q <= last; ++q) {
+            const u32 w2 = a.vals[q];
+            if (w2 < bw) { bw = w2; bi = q; }
+          }
+          best = bi == i;
         }
-        const bool del_exists = i > 0 && a.keys[i - 1] == (key ^ 1ull);
-        const bool applied = !present || del_exists;
-        for (long long t = i; t < j2; ++t) {
-          const bool on = applied && t == best;
-          a.flags[t] = (on ? 1 : 0) | pbit;
-          a.itemv[t] = on ? (1ull << 32) : 0ull;
-        }
-        if (dir == 0) {
-          add_ok += applied;
-          add_pres += (u64)(j2 - i) - (applied ? 1 : 0);
+        const u64 before = first == i ? pk[k] : (first > 0 ? a.keys[first - 1] : ~0ull);
+        const bool del_exists = first > 0 && before == (key[k] ^ 1ull);
+        const bool run_applies = !present || del_exists;
+        const bool applied = best && run_applies;
+        a.flags[i] = (applied ? 1 : 0) | pbit;
+        iv[k] = applied ? (1ull << 32) : 0ull;
+        if (dir[k] == 0 && i == first) {
+          add_ok += run_applies;
+          add_pres += (u64)(last - first + 1) - (run_applies ? 1 : 0);
         }
       }
     }
+    // prefix of the applied over this block's items so far
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {
+      u64 tot;
+      const u64 ex = block_excl_scan_u64(iv[k], ws64, &tot);
+      const u32 i = tb + k * kCT + t;
+      if (i < ce) a.item_pref[i] = s_run + ex;
+      __syncthreads();
+      if (t == 0) s_run += tot;
+      __syncthreads();
+    }
   }
-  __shared__ u64 sums[4];
-  if (threadIdx.x < 4) sums[threadIdx.x] = 0;
-  __syncthreads();
-  block_add(del_ok, &sums[0], &c->del_applied);
-  block_add(del_abs, &sums[1], &c->del_absent);
-  block_add(add_ok, &sums[2], &c->add_applied);
-  block_add(add_pres, &sums[3], &c->add_present);
-}
+  if (t == 0) __stcg(a.tab + b, s_run);
+  if (coop_barrier(bar, (u64)G, c, a.wait_ns, 5)) return;
+  {   // this block's base: the totals of the blocks before it
+    u64 part = 0;
+    for (u32 q = t; q < b; q += kCT) part += __ldcg(a.tab + q);
+    u64 all;
+    block_excl_scan_u64(part, ws64, &all);
+    for (u32 i = cb + t; i < ce; i += kCT) a.item_pref[i] += all;
+    if (b == G - 1 && t == 0) a.item_pref[ni] = all + s_run;
+  }
+  if (coop_barrier(bar, 2ull * G, c, a.wait_ns, 5)) return;
 
-// One thread per touched row: new size (from the item prefix counts),
-// destination (the row's alternate region, or a fresh pair of regions in the
-// spare pool when the row outgrows its capacity), and the row's strips of
-// kStrip old entries (one strip for a row with fewer), the merge's units.
-__global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
-  __shared__ u32 scratch[40];
-  Ctl *c = a.ctl;
-  if (ld_cg_i32(&c->status) != 0) return;
-  const int lane = threadIdx.x & 31;
   const u32 nseg = ld_cg_u32(&c->n_seg);
   u64 touched = 0, relocated = 0, slots = 0;
-  for (u32 base = blockIdx.x * blockDim.x; base < nseg; base += gridDim.x * blockDim.x) {
-    const u32 si = base + threadIdx.x;
+  for (u32 base = b * kCT; base < nseg; base += G * kCT) {
+    const u32 si = base + t;
     bool ok = si < nseg;
     Seg sg;
     u32 nstr = 0;
@@ -386,14 +490,15 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
     if (ok) {
       const Store &st = a.st[sg.dir];
       const RowMeta rm = st.row[sg.row];
-      const u64 p = a.item_pref[sg.end] - a.item_pref[sg.first];
+      const u64 pf = __ldcg(a.item_pref + sg.first);
+      const u64 p = __ldcg(a.item_pref + sg.end) - pf;
       const int new_deg = rm.deg - (int)(u32)p + (int)(u32)(p >> 32);
       sg.old_start = rm.start;
       sg.old_deg = rm.deg;
       sg.new_deg = new_deg;
       sg.pad = 0;
       sg.prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
-      sg.base_pref = a.item_pref[sg.first];
+      sg.base_pref = pf;
       if (new_deg > rm.cap) {
         long long nc = row_capacity(new_deg, a.slack);
         const long long dbl = round_up4(2LL * rm.cap);
@@ -412,28 +517,26 @@ __global__ void __launch_bounds__(kThreads) k_count_segs(CountArgs a) {
       }
       a.seg[si] = sg;
       nstr = rm.deg > kStrip ? (u32)((rm.deg + kStrip - 1) / kStrip) : 1u;
-
       ++touched;
       slots += (u64)rm.deg + (u64)new_deg;
     }
-    // reserve the strips: one atomic per block
-    {
+    {   // reserve the strips: one atomic per block
       u32 stot;
       const u32 se = block_excl_scan_u32(nstr, scratch, &stot);
-      if (threadIdx.x == 0) scratch[35] = stot ? atomicAdd(&c->bstrips, stot) : 0u;
+      if (t == 0) scratch[35] = stot ? atomicAdd(&c->bstrips, stot) : 0u;
       __syncthreads();
       const u32 sb = scratch[35] + se;
       __syncthreads();
       for (u32 k = 0; k < nstr; ++k) a.strips[sb + k] = make_int2((int)si, (int)(k * kStrip));
     }
   }
-  __shared__ u64 sums[3];
-  if (threadIdx.x < 3) sums[threadIdx.x] = 0;
-  __syncthreads();
-  (void)lane;
-  block_add(touched, &sums[0], &c->rows_touched);
-  block_add(relocated, &sums[1], &c->rows_relocated);
-  block_add(slots, &sums[2], &c->merge_slots);
+  block_add(del_ok, &sums[0], &c->del_applied);
+  block_add(del_abs, &sums[1], &c->del_absent);
+  block_add(add_ok, &sums[2], &c->add_applied);
+  block_add(add_pres, &sums[3], &c->add_present);
+  block_add(touched, &sums[4], &c->rows_touched);
+  block_add(relocated, &sums[5], &c->rows_relocated);
+  block_add(slots, &sums[6], &c->merge_slots);
 }
 
 // --------------------------------------------------------------------------
@@ -445,7 +548,7 @@ struct MergeArgs {
   const u64 *keys;
   const u32 *vals;
   const unsigned char *flags;
-  const u64 *item_pref;   // exclusive scan of itemv, n_items + 1 entries
+  const u64 *item_pref;   // exclusive prefix of the applied updates, n_items + 1 entries
   const Seg *seg;
   const u32 *opos;
   const int2 *strips;
@@ -809,6 +912,14 @@ void launch_ctl_reset(sp_graph *g, int full, int *launches) {
   ++*launches;
 }
 
+int count_blocks(int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count, kCT, 0) != cudaSuccess ||
+      per_sm < 1)
+    return 0;
+  return per_sm * num_sms;
+}
+
 void launch_count(sp_graph *g, long long ni, int *launches) {
   if (ni == 0) return;
   BatchBufs &b = g->bb;
@@ -818,23 +929,33 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.vals = b.vals;
   a.seg = b.seg;
   a.flags = b.flags;
-  a.itemv = b.itemv;
   a.item_pref = b.item_pref;
   a.opos = b.opos;
   a.strips = b.strips;
+  a.tab = (u64 *)b.tmp;   // the batch sort's table is free again
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
   a.slack = g->slack;
   a.n_items = (u32)ni;
   a.n = g->n;
-  const unsigned grid = blocks_for(ni, kThreads, g->num_sms * 16);
-  k_count_items<<<grid, kThreads, 0, g->stream>>>(a);
-  // item prefix counts (n_items + 1 entries; itemv[ni] is 0)
-  cudaMemsetAsync(b.itemv + ni, 0, sizeof(u64), g->stream);
-  scan_exclusive_u64(b.itemv, b.item_pref, ni + 1, b.tmp, g->stream, launches);
-  k_count_segs<<<grid, kThreads, 0, g->stream>>>(a);
-  *launches += 2;
+  a.wait_ns = g->lim.wait_ns;
+  int G = (int)std::min<long long>((ni + kCTile - 1) / kCTile, g->count_blocks);
+  if (g->loop_blocks_user > 0 && g->loop_blocks_user * 4 < G) G = g->loop_blocks_user * 4;
+  if (G < 1) G = 1;
+  a.chunk = (u32)((ni + G - 1) / G);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = g->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_count, a);
+  *launches += 1;
 }
 
 void launch_merge(sp_graph *g, long long ni, int *launches) {
