@@ -148,6 +148,12 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
     for (int i = 0; i < SP_NPHASE; ++i)
       if (cudaEventElapsedTime(&st->ms_phase[i], g->ev[i], g->ev[i + 1]) != cudaSuccess)
         st->ms_phase[i] = 0.f;
+    // an invalidation beside the store update: its own duration (it overlaps
+    // the count and merge phases, so the phases add up to more than the total)
+    if (g->last_beside &&
+        cudaEventElapsedTime(&st->ms_phase[SP_PH_INVAL], g->ev_inval[0], g->ev_inval[1]) !=
+            cudaSuccess)
+      st->ms_phase[SP_PH_INVAL] = 0.f;
     if (cudaEventElapsedTime(&st->ms_total, g->ev[0], g->ev[SP_NPHASE]) != cudaSuccess)
       st->ms_total = 0.f;
     cudaGetLastError();
@@ -174,6 +180,11 @@ void drop_batch_graphs(sp_graph *g) {
   g->bg_ready = false;
 }
 
+// Pointer jumping reads only the parents in s, so the invalidation can run
+// beside the store update; frontier rounds walk the forward store and wait
+// for the merge.
+bool inval_beside(const sp_graph *g) { return g->side && g->lim.jump_round == 0; }
+
 // The kernel nodes of the captured batch graph that read the batch inputs:
 // the batch sort (every input array) and the invalidation loop (the
 // deletions).  Every other kernel reads the sorted items.
@@ -198,7 +209,7 @@ cudaError_t retarget_input_nodes(sp_graph *g, const int *ds, const int *dd, long
                                  const int *as, const int *ad, const int *aw, long long na) {
   cudaError_t e = sp::retarget_batch_sort(g, g->bg_exec, g->bg_sort, ds, dd, nd, as, ad, aw, na);
   if (e == cudaSuccess && g->bg_inval)
-    e = sp::retarget_inval(g, g->bg_exec, g->bg_inval, ds, dd, nd);
+    e = sp::retarget_inval(g, g->bg_exec, g->bg_inval, ds, dd, nd, inval_beside(g) ? 1 : 0);
   return e;
 }
 
@@ -241,19 +252,48 @@ sp_status status_of_repair(sp_graph *g, const Ctl &c) {
   return SP_OK;
 }
 
+// Timing event i (0 start, 1 end) of an invalidation on the side stream.
+void rec_side(sp_graph *g, bool timed, int i) {
+  if (!timed) return;
+  if (g->capturing >= 0)
+    cudaEventRecordWithFlags(g->ev_inval[i], g->side, cudaEventRecordExternal);
+  else
+    cudaEventRecord(g->ev_inval[i], g->side);
+}
+
+// How a batch's invalidation runs.
+enum InvalMode {
+  kInvalAfter = 0,    // after the merge, on the graph's stream
+  kInvalBeside = 1,   // on the side stream, beside the count and the merge
+  kInvalKept = 2,     // a rerun after a pool grow: the first attempt's stands
+};
+
 // The kernel sequence of one batch (no host synchronisation).
 cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n_del,
                           const int *as, const int *ad, const int *aw, long long n_add,
-                          bool timed, int *launches) {
+                          bool timed, int *launches, int mode = kInvalAfter) {
   const long long ni = 2 * (n_del + n_add);
-  sp::launch_ctl_reset(g, 0, launches);
+  sp::launch_ctl_reset(g, mode == kInvalKept ? 2 : 0, launches);
   cudaError_t e = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, launches);
   rec(g, timed, 1);
+  const bool beside = mode == kInvalBeside && n_del > 0;
+  g->last_beside = beside && timed;
+  if (beside) {   // fork: the side stream starts once the batch is validated
+    cudaEventRecord(g->fork_ev, g->stream);
+    cudaStreamWaitEvent(g->side, g->fork_ev, 0);
+    rec_side(g, timed, 0);
+    const cudaError_t ei = sp::launch_inval(g, ds, dd, n_del, launches, 1, g->side);
+    if (e == cudaSuccess) e = ei;
+    rec_side(g, timed, 1);
+    cudaEventRecord(g->join_ev, g->side);
+  }
   sp::launch_count(g, ni, launches);
   rec(g, timed, 2);
   sp::launch_merge(g, ni, launches);
   rec(g, timed, 3);
-  if (e == cudaSuccess && n_del > 0) e = sp::launch_inval(g, ds, dd, n_del, launches);
+  if (beside) cudaStreamWaitEvent(g->stream, g->join_ev, 0);   // join
+  else if (mode == kInvalAfter && e == cudaSuccess && n_del > 0)
+    e = sp::launch_inval(g, ds, dd, n_del, launches);
   rec(g, timed, 4);
   // the pull and OnAdd run as the first stage of the push loop's launch
   rec(g, timed, 5);
@@ -300,6 +340,7 @@ const char *sp_version(void) { return "0.1.0"; }
 
 sp_status sp_graph_destroy(sp_graph *g) {
   if (!g) return SP_OK;
+  if (g->side) cudaStreamSynchronize(g->side);
   cudaStreamSynchronize(g->stream);
   auto &al = g->al;
   auto &b = g->bb;
@@ -333,6 +374,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->aent, n * 8);
   al.put(g->ftag, n * 4);
   al.put(g->jmp, n * 4);
+  al.put(g->cut, n * 4);
   al.put(g->aown, (size_t)g->own_cap * 4);
   al.put(g->out_dist, n * 4); al.put(g->out_parent, n * 4);
   al.put(g->pr[0], n * 4); al.put(g->pr[1], n * 4);
@@ -343,6 +385,11 @@ sp_status sp_graph_destroy(sp_graph *g) {
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   for (auto &e : g->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : g->ev_inval)
+    if (e) cudaEventDestroy(e);
+  if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+  if (g->join_ev) cudaEventDestroy(g->join_ev);
+  if (g->side) cudaStreamDestroy(g->side);
   cudaStreamSynchronize(g->stream);
   delete g;
   return SP_OK;
@@ -391,6 +438,21 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
       sp_graph_destroy(g);
       return SP_ECUDA;
     }
+  for (auto &e : g->ev_inval)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      sp_graph_destroy(g);
+      return SP_ECUDA;
+    }
+  // the side stream of the invalidation; without it (or on the legacy
+  // default stream) the invalidation runs after the merge
+  if (g->stream &&
+      (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    sp_graph_destroy(g);
+    return SP_ECUDA;
+  }
   if (cudaMallocHost(&g->ctl_host, sizeof(Ctl)) != cudaSuccess) {
     cudaGetLastError();
     g->ctl_host = nullptr;
@@ -413,9 +475,10 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   g->aent = (int2 *)g->al.get(nn * 8);
   g->ftag = (u32 *)g->al.get(nn * 4);
   g->jmp = (u32 *)g->al.get(nn * 4);
+  g->cut = (u32 *)g->al.get(nn * 4);
   g->out_dist = (int *)g->al.get(nn * 4);
   g->out_parent = (int *)g->al.get(nn * 4);
-  if (!g->ctl || !g->s || !g->qflag || !bufs_ok || !g->aent || !g->ftag || !g->jmp ||
+  if (!g->ctl || !g->s || !g->qflag || !bufs_ok || !g->aent || !g->ftag || !g->jmp || !g->cut ||
       !g->out_dist || !g->out_parent) {
     sp_graph_destroy(g);
     return SP_ENOMEM;
@@ -591,6 +654,9 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
     ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
   }
   int launches = 0, regrows = 0;
+  // the first attempt runs the invalidation beside the store update; a rerun
+  // after a pool grow keeps what it found (it already changed the distances)
+  const int mode0 = inval_beside(g) ? kInvalBeside : kInvalAfter;
   for (int attempt = 0;; ++attempt) {
     launches = 0;
     if (attempt) rec(g, timed, 0);
@@ -603,7 +669,8 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
         int cl = 0;
         if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
           g->capturing = 0;
-          const cudaError_t ce = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &cl);
+          const cudaError_t ce = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &cl,
+                                               mode0);
           g->capturing = -1;
           cudaGraph_t gr = nullptr;
           bool ok = cudaStreamEndCapture(g->stream, &gr) == cudaSuccess && ce == cudaSuccess && gr;
@@ -636,7 +703,9 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
         replayed = true;
       }
     }
-    if (!replayed) e = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &launches);
+    if (!replayed)
+      e = enqueue_batch(g, ds, dd, n_del, as, ad, aw, n_add, timed, &launches,
+                        attempt == 0 ? mode0 : (mode0 == kInvalBeside ? kInvalKept : kInvalAfter));
     if (e != cudaSuccess) {
       g->last_err = (int)e;
       cudaGetLastError();

@@ -425,11 +425,13 @@ struct PushOp {
 
 // Decremental first loop body: a child x of v (parent[x] == v) loses its
 // distance and parent, joins the next frontier (its out-edges) and the
-// affected list A (its in-edges, for the pull).
+// cut list (its in-edges are pulled later).
 struct InvalOp {
   u64 *s;
-  Queue next, alist;
-  const RowMeta *row, *rrow;
+  Queue next;
+  const RowMeta *row;
+  u32 *cut, *ccnt, *cmin;   // cut-vertex list and its block stage
+  Stage *cst;
   u64 n_edges = 0, n_enq = 0, n_aff = 0;
   int range_err = 0;
 
@@ -450,8 +452,7 @@ struct InvalOp {
       }
     }
     enqueue(next, row, tx, want, K, n_enq);
-    u64 dummy = 0;
-    enqueue(alist, rrow, tx, want, K, dummy);
+    far_append(cut, ccnt, cmin, cst, tx, want, K, 0u);
   }
 };
 
@@ -667,6 +668,14 @@ __device__ __forceinline__ bool repair_enabled(Ctl *c) {
          ld_cg_i32(&c->timeout) == 0 && ld_cg_i32(&c->bad) == 0;
 }
 
+// The batch passed validation (one answer for the whole block).
+__device__ __forceinline__ bool batch_valid_block(Ctl *c) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = ld_cg_i32(&c->status) == 0 ? 1 : 0;
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // The same test with one answer for the whole block (kernels with barriers).
 __device__ __forceinline__ bool repair_enabled_block(Ctl *c) {
   __shared__ int s_ok;
@@ -762,7 +771,7 @@ struct JumpState {
 };
 
 __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 target,
-                                             u32 *scratch, Stage *sa, Stage *sas) {
+                                             u32 *scratch, Stage *cst) {
   Ctl *c = a.ctl;
   u32 jumps = 0;
   bool capped = false;
@@ -791,8 +800,6 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
   }
   target += gridDim.x;
   bool stop = grid_sync(bar, target, c, a.lim);
-  const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
-  u64 dummy = 0;
   for (;;) {
     if (stop) break;
     if (jumps > 0 && ld_cg_u32(jcnt_ptr(c, (jumps - 1) % 3)) == 0) break;
@@ -803,7 +810,7 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
     if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile u32 *)jcnt_ptr(c, (jumps + 1) % 3) = 0u;
     // a vertex whose word turns into kJumpCut in this pass had a distance
     // (its word was an ancestor) and a cut lies on its tree path: it loses
-    // the distance and joins A here, exactly once
+    // the distance and joins the cut list here, exactly once
     u32 act = 0;
     for (u32 w0 = gw * 32 * K; w0 < n; w0 += nw * 32 * K) {
       u32 v[K], j[K], ja[K];
@@ -828,7 +835,7 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
           }
         }
       }
-      enqueue(qa, a.rev.row, v, hit, K, dummy);
+      far_append(a.cut, &c->ccnt, &c->cmin, cst, v, hit, K, 0u);
     }
     u32 total;
     block_excl_scan(act, scratch, &total);
@@ -837,7 +844,7 @@ __device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 ta
     target += gridDim.x;
     stop = grid_sync(bar, target, c, a.lim);
   }
-  flush_queue(qa, scratch);
+  flush_far(cst, a.cut, &c->ccnt, &c->cmin, scratch);
   JumpState out;
   out.target = target;
   out.n_aff = n_aff;
@@ -875,6 +882,11 @@ struct LocalState {      // what an episode hands back to the loop
   u32 cur, round, capped, stop;
   u64 n_edges, n_imp, n_enq;
   int range_err;
+  // the counters the loop decides on next (frontier slot cur, far pile f),
+  // as block 0 left them: every block takes the same decision even though
+  // block 0 may already be changing them in its next episode
+  u64 q;
+  u32 nsmall, n_far, fmin;
 };
 
 // Block 0 only (block-collective).  smem: 7 * kLocalCap words that no other
@@ -1069,22 +1081,40 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
                                                  u32 *smem, Stage *sf, u32 *scratch) {
   Ctl *c = a.ctl;
   LocalState out{};
+  __shared__ u64 s_q;
+  __shared__ u32 s_sn, s_fn, s_fm;
   if (blockIdx.x == 0) {
     const u64 t_in = globaltimer_ns();
     out = local_rounds(a, cur, round, thresh, f, phase, nf, smem, sf, scratch);
     if (threadIdx.x == 0) {
       c->local_ns += globaltimer_ns() - t_in;
+      const u64 q = ld_cg_u64(qcnt_ptr(c, out.cur));
+      const u32 sn = ld_cg_u32(scnt_ptr(c, out.cur));
+      const u32 fn = nf ? ld_cg_u32(fcnt_ptr(c, f)) : 0u;
+      const u32 fm = nf ? ld_cg_u32(fmin_ptr(c, f)) : kInf;
       *(volatile u32 *)&c->lcur = out.cur;
       *(volatile u32 *)&c->lround = out.round;
       *(volatile u32 *)&c->lcap = out.capped;
+      *(volatile u64 *)&c->lq = q;
+      *(volatile u32 *)&c->lsn = sn;
+      *(volatile u32 *)&c->lfn = fn;
+      *(volatile u32 *)&c->lfm = fm;
       c->local_episodes += 1;
       c->local_rounds += out.round - round;
       __threadfence();
       st_release_u32(&c->lres, lep);
       scratch[39] = (out.stop || ld_cg_i32(&c->timeout) != 0) ? 1u : 0u;
+      s_q = q;
+      s_sn = sn;
+      s_fn = fn;
+      s_fm = fm;
     }
     __syncthreads();
     out.stop = scratch[39];
+    out.q = s_q;
+    out.nsmall = s_sn;
+    out.n_far = s_fn;
+    out.fmin = s_fm;
     __syncthreads();
   } else {
     if (threadIdx.x == 0) {
@@ -1093,8 +1123,11 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
       u32 nap = 32;
       while (ld_acquire_u32(&c->lres) < lep) {
         if (ld_cg_i32(&c->timeout) != 0) break;
+        // the heartbeat is block 0's clock, read after this block's: it can
+        // be the later of the two, and then nothing has run out yet
         const u64 beat = ld_cg_u64(&c->lbeat), now = globaltimer_ns();
-        if (now - (beat > t0 ? beat : t0) > a.lim.wait_ns) {
+        const u64 since = beat > t0 ? beat : t0;
+        if (now > since && now - since > a.lim.wait_ns) {
           raise_timeout(c, 2, 3, lep);
           break;
         }
@@ -1105,18 +1138,27 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
       scratch[37] = ld_cg_u32(&c->lround);
       scratch[38] = ld_cg_u32(&c->lcap);
       scratch[39] = ld_cg_i32(&c->timeout) != 0 ? 1u : 0u;
+      s_q = ld_cg_u64(&c->lq);
+      s_sn = ld_cg_u32(&c->lsn);
+      s_fn = ld_cg_u32(&c->lfn);
+      s_fm = ld_cg_u32(&c->lfm);
     }
     __syncthreads();
     out.cur = scratch[36];
     out.round = scratch[37];
     out.capped = scratch[38];
     out.stop = scratch[39];
+    out.q = s_q;
+    out.nsmall = s_sn;
+    out.n_far = s_fn;
+    out.fmin = s_fm;
     __syncthreads();
   }
   return out;
 }
 
-__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
+__device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst, Stage *sa,
+                                        Stage *sas, u32 *scratch, u64 *bar, u64 &target);
 __device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 
 template <int OP>
@@ -1125,7 +1167,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   __shared__ Stage sq, sqs, sa, sas, sf;
   __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
-  if (!repair_enabled_block(c)) return;
+  // beside the store update the invalidation starts once the batch is
+  // validated and does not wait for the merge's pool check: a rerun after a
+  // pool grow keeps what it found
+  if (OP == kOpInval && a.concurrent) {
+    if (!batch_valid_block(c)) return;
+  } else if (!repair_enabled_block(c)) {
+    return;
+  }
   if (threadIdx.x == 0) {
     u32 *p = dsm;
     sq.n = 0; sq.cap = kStageQ; sq.vmin = kInf; sq.v = p; sq.d = p + kStageQ; p += 2 * kStageQ;
@@ -1147,9 +1196,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   u64 target = 0;
 
   if (OP == kOpInval && a.n_del > 0) {
-    // OnDelete: a deleted edge u -> v that is v's parent edge invalidates v.
+    // OnDelete: a deleted edge u -> v that is v's parent edge invalidates v;
+    // v joins the cut list and, for frontier rounds, the first frontier
+    // (beside the store update there are none: the tree walk is jumping)
     const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &sq, &sqs);
-    const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
     for (long long base = (long long)gw * 32; base < a.n_del; base += (long long)nw * 32) {
       const long long i = base + lane;
       bool hit[K] = {};
@@ -1162,12 +1212,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
           hit[0] = atomicCAS((unsigned long long *)(a.s + v[0]), sv, kInfPack) == sv;
       }
       n_aff += hit[0];
-      enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
-      u64 dummy = 0;
-      enqueue(qa, a.rev.row, v, hit, 1, dummy);
+      if (!a.concurrent) enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
+      far_append(a.cut, &c->ccnt, &c->cmin, &sf, v, hit, 1, 0u);
     }
-    flush_queue(q0, scratch);
-    flush_queue(qa, scratch);
+    if (!a.concurrent) flush_queue(q0, scratch);
+    flush_far(&sf, a.cut, &c->ccnt, &c->cmin, scratch);
   }
   if (OP == kOpFlag && a.n_del > 0) {
     // the phase's destinations are the flags' seeds
@@ -1187,8 +1236,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   }
 
   if (OP == kOpPush) {   // a batch's seeds: the pull over A, then OnAdd
-    if (a.seed_pull) pull_stage(a, &sq, &sqs, scratch);
-    if (a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
+    bool st0 = false;
+    if (a.seed_pull) st0 = pull_stage(a, &sq, &sqs, &sa, &sas, scratch, bar, target);
+    if (!st0 && a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
   }
 
   // state shared by all blocks (read before the first barrier; only block 0
@@ -1206,15 +1256,24 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   }
   u32 cur = 0, f = 0, round = 0, splits = 0, jumps = 0, lep = 0;
   bool capped = false, jump = false;
+  // after a single-block episode the loop decides on block 0's snapshot
+  bool snap = false;
+  u64 snap_q = 0;
+  u32 snap_sn = 0, snap_fn = 0, snap_fm = 0;
+  // beside the store update the subtree walk is pointer jumping only (it
+  // reads the parents in s, never a store)
+  if (OP == kOpInval && a.concurrent && !stop) jump = ld_cg_u32(&c->ccnt) > 0;
   for (;;) {
-    if (stop) break;
+    if (stop || (OP == kOpInval && a.concurrent)) break;
     if (round >= a.lim.max_rounds) {
       capped = true;
       break;
     }
-    const u64 q = ld_cg_u64(qcnt_ptr(c, cur));
+    const u64 q = snap ? snap_q : ld_cg_u64(qcnt_ptr(c, cur));
     const u32 ne = (u32)(q >> 32), nedge = (u32)q;
-    const u32 nsmall = ld_cg_u32(scnt_ptr(c, cur));
+    const u32 nsmall = snap ? snap_sn : ld_cg_u32(scnt_ptr(c, cur));
+    const bool from_snap = snap;
+    snap = false;
     const u32 sgroups = (nsmall + 31) / 32;
     const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
     bool split = false;
@@ -1234,6 +1293,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       round = ls.round;
       capped = ls.capped != 0;
       stop = ls.stop != 0;
+      snap = true;
+      snap_q = ls.q;
+      snap_sn = ls.nsmall;
+      snap_fn = ls.n_far;
+      snap_fm = ls.fmin;
       n_edges += ls.n_edges;
       n_imp += ls.n_imp;
       n_enq += ls.n_enq;
@@ -1242,10 +1306,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       continue;
     }
     if (items == 0) {
-      if (nf) n_far = ld_cg_u32(fcnt_ptr(c, f));
+      if (nf) n_far = from_snap ? snap_fn : ld_cg_u32(fcnt_ptr(c, f));
       if (n_far == 0) break;                       // fixed point reached
       split = true;
-      const u32 fm = ld_cg_u32(fmin_ptr(c, f));
+      const u32 fm = from_snap ? snap_fm : ld_cg_u32(fmin_ptr(c, f));
       thresh = sat_add(thresh > fm ? thresh : fm, a.lim.delta);
     }
     const u32 nxt = next3(cur);
@@ -1316,8 +1380,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       n_enq += op.n_enq;
       n_aff += op.n_aff;
     } else {
-      const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
-      InvalOp op{a.s, qn, qa, a.fwd.row, a.rev.row};
+      InvalOp op{a.s, qn, a.fwd.row, a.cut, &c->ccnt, &c->cmin, &sf};
       for (u32 it = gw; it < items; it += nw) {
         if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
         else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
@@ -1325,7 +1388,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       n_edges += op.n_edges;
       n_enq += op.n_enq;
       n_aff += op.n_aff;
-      flush_queue(qa, scratch);
+      flush_far(&sf, a.cut, &c->ccnt, &c->cmin, scratch);
     }
     // publish this block's staged appends before the barrier
     flush_queue(qn, scratch);
@@ -1343,7 +1406,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     stop = grid_sync(bar, target, c, a.lim);
   }
   if (OP == kOpInval && jump) {
-    const JumpState js = jump_phase(a, bar, target, scratch, &sa, &sas);
+    const JumpState js = jump_phase(a, bar, target, scratch, &sf);
     target = js.target;
     jumps = js.jumps;
     capped = capped || js.capped != 0;
@@ -1393,12 +1456,37 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
 
 // --- pull (one pass over A) -----------------------------------------------
 
-// Pull stage (block-collective): every vertex of A takes the minimum over
-// its in-edges; the improved ones form the push loop's first frontier
-// (queue slot 0).
-__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
+// Pull stage (block-collective).  The invalidation's cut vertices become the
+// affected list A, sized by their in-degrees in the updated reverse store
+// (the invalidation may have run beside the store update, so it could not
+// size them); after a grid barrier every vertex of A takes the minimum over
+// its in-edges, and the improved ones form the push loop's first frontier
+// (queue slot 0).  Returns whether a wait bound was hit.
+__device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst, Stage *sa,
+                                        Stage *sas, u32 *scratch, u64 *bar, u64 &target) {
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
+  {
+    const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, sa, sas);
+    const u32 ncut = ld_cg_u32(&c->ccnt);
+    const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const u32 nw = (gridDim.x * blockDim.x) >> 5;
+    u64 dummy = 0;
+    for (u32 base = gw * 32 * K; base < ncut; base += nw * 32 * K) {
+      u32 v[K];
+      bool want[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const u32 i = base + lane + 32 * k;
+        want[k] = i < ncut;
+        v[k] = want[k] ? __ldcg(a.cut + i) : 0u;
+      }
+      enqueue(qa, a.rev.row, v, want, K, dummy);
+    }
+    flush_queue(qa, scratch);
+  }
+  target += gridDim.x;
+  if (grid_sync(bar, target, c, a.lim)) return true;
   const u64 ac = ld_cg_u64(&c->acnt);
   const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
   const u32 nsmall = ld_cg_u32(&c->ascnt);
@@ -1421,6 +1509,7 @@ __device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst
     if (q) atomicAdd(&c->seeds, q);
     if (re) atomicExch(&c->range_err, 1);
   }
+  return false;
 }
 
 // --- OnAdd: relax every applied insertion ---------------------------------
@@ -1775,6 +1864,8 @@ LoopArgs make_args(sp_graph *g) {
   a.n_del = 0;
   a.prflag = g->prflag;
   a.ptag = g->prtag;
+  a.cut = g->cut;
+  a.concurrent = 0;
   a.seed_pull = 0;
   a.keys = g->bb.keys;
   a.vals = g->bb.vals;
@@ -1814,14 +1905,23 @@ void launch_init(sp_graph *g, int source, int *launches) {
   ++*launches;
 }
 
-static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) {
+// Blocks of a persistent loop; an invalidation beside the store update
+// takes a quarter of the SMs and leaves the rest to the count and merge.
+static int loop_grid(const sp_graph *g, int op, int concurrent) {
   int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
   if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
+  if (concurrent) blocks = std::max(1, std::min(blocks, g->num_sms / 4));
+  return blocks;
+}
+
+static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
+                               cudaStream_t stream) {
+  const int blocks = loop_grid(g, op, a.concurrent);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kPersistThreads);
   cfg.dynamicSmemBytes = kLoopSmem;
-  cfg.stream = g->stream;
+  cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
   attr[0].val.cooperative = 1;
@@ -1836,13 +1936,13 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches) 
 const void *inval_fn() { return (const void *)k_loop<kOpInval>; }
 
 cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node, const int *ds,
-                           const int *dd, long long nd) {
+                           const int *dd, long long nd, int concurrent) {
   LoopArgs a = make_args(g);
   a.del_src = ds;
   a.del_dst = dd;
   a.n_del = nd;
-  int blocks = g->loop_blocks_inval;
-  if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
+  a.concurrent = concurrent;
+  const int blocks = loop_grid(g, kOpInval, concurrent);
   void *args[1] = {&a};
   cudaKernelNodeParams p = {};
   p.func = (void *)k_loop<kOpInval>;
@@ -1853,19 +1953,21 @@ cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node
   return cudaGraphExecKernelNodeSetParams(ex, node, &p);
 }
 
-cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches) {
+cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd, int *launches,
+                         int concurrent, cudaStream_t stream) {
   LoopArgs a = make_args(g);
   a.del_src = ds;
   a.del_dst = dd;
   a.n_del = nd;
-  return launch_loop(g, kOpInval, a, launches);
+  a.concurrent = concurrent;
+  return launch_loop(g, kOpInval, a, launches, concurrent && stream ? stream : g->stream);
 }
 
 cudaError_t launch_push(sp_graph *g, int *launches, int pull, long long n_items) {
   LoopArgs a = make_args(g);
   a.seed_pull = pull;
   a.n_items = n_items;
-  return launch_loop(g, kOpPush, a, launches);
+  return launch_loop(g, kOpPush, a, launches, g->stream);
 }
 
 void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches) {
@@ -1878,7 +1980,7 @@ cudaError_t launch_flag(sp_graph *g, const int *dst, long long n, int *launches)
   LoopArgs a = make_args(g);
   a.del_dst = dst;
   a.n_del = n;
-  return launch_loop(g, kOpFlag, a, launches);
+  return launch_loop(g, kOpFlag, a, launches, g->stream);
 }
 
 void launch_pr_fill(sp_graph *g, float value, int *launches) {

@@ -100,6 +100,10 @@ struct LoopArgs {
   // PageRank flags: prflag[v] == ptag marks v for the current phase
   u32 *prflag;
   u32 ptag;
+  // the invalidation's cut vertices; concurrent != 0: the invalidation runs
+  // beside the store update, so it reads neither store (no frontier rounds)
+  u32 *cut;
+  int concurrent;
   // first stage of the push loop of a batch (before its first barrier): the
   // pull over the affected list A, and OnAdd over the sorted batch items
   int seed_pull;
@@ -133,6 +137,12 @@ struct sp_graph {
   sp::u32 *fq[3] = {nullptr, nullptr, nullptr};
   sp::u32 *ftag = nullptr;
   sp::u32 *jmp = nullptr;
+  sp::u32 *cut = nullptr;       // cut vertices of the invalidation
+  // side stream of the invalidation, which runs beside the store update
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaEvent_t ev_inval[2] = {nullptr, nullptr};
+  bool last_beside = false;     // the last timed call ran the invalidation beside
   // PageRank state (allocated by sp_pr_init): ranks in two buffers that
   // agree between calls, the pull accumulators, phase flags and settings
   float *pr[2] = {nullptr, nullptr};
@@ -214,7 +224,7 @@ cudaError_t retarget_batch_sort(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t
                                 const int *ad, const int *aw, long long na);
 const void *inval_fn();
 cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node, const int *ds,
-                           const int *dd, long long nd);
+                           const int *dd, long long nd, int concurrent);
 void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
                         const int *ad, const int *aw, long long na, int *launches);
 
@@ -223,7 +233,7 @@ int loop_blocks(int which, int num_sms);
 void launch_init(sp_graph *g, int source, int *launches);
 void launch_init_multi(sp_graph *g, const int *src_d, int k, int *launches);
 cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd,
-                         int *launches);
+                         int *launches, int concurrent = 0, cudaStream_t stream = nullptr);
 // push fixedPoint; for a batch (pull != 0 or n_items > 0) its first stage
 // pulls over A and relaxes the applied insertions
 cudaError_t launch_push(sp_graph *g, int *launches, int pull = 0, long long n_items = 0);

@@ -103,6 +103,10 @@ struct Ctl {
   alignas(128) u32 lres;
   u32 lcur, lround, lcap;
   u64 lbeat;
+  // what the loop decides on after an episode, as block 0 left it: the
+  // counters of the current frontier slot and of the current far pile
+  u64 lq;
+  u32 lsn, lfn, lfm;
   // PageRank: sum |pr' - pr| of each Jacobi step (rotating) and the steps run
   alignas(128) double prd0;
   alignas(128) double prd1;
@@ -113,6 +117,10 @@ struct Ctl {
   // insertions' corrections by number of updated edges (1, 2, 3)
   alignas(128) u64 tc_static;
   u64 tc_del[3], tc_ins[3];
+  // the invalidation's cut vertices (a plain list: the pull stage of the
+  // push launch turns them into the affected list A)
+  alignas(128) u32 ccnt;
+  u32 cmin;              // unused minimum of the cut list's appends
   // vertices still jumping after each pointer-jumping pass, triple-buffered
   alignas(128) u32 jcnt0;
   alignas(128) u32 jcnt1;

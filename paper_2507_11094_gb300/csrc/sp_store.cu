@@ -193,12 +193,24 @@ __global__ void k_copy_slots(const int2 *__restrict__ src, int2 *dst, long long 
 // batch: control reset, validation, items
 // --------------------------------------------------------------------------
 
+// full: 0 a new call, 1 a new graph, 2 a call rerun after a pool grow,
+// which keeps what the first attempt's invalidation found (it ran beside
+// the store update, changed the distances, and does not run again)
 __global__ void k_ctl_reset(Ctl *c, int full) {
+  const bool keep = full == 2;
   c->status = 0;
   c->need_grow = 0;
   c->range_err = 0;
-  c->timeout = 0;
-  c->to_site = c->to_info = 0;
+  if (!keep) {
+    c->timeout = 0;
+    c->to_site = c->to_info = 0;
+    c->ccnt = 0;
+    c->affected = 0;
+    c->inval_edges = 0;
+    c->rounds_inval = 0;
+    c->jumps = 0;
+  }
+  c->cmin = 0xFFFFFFFFu;
   c->bad = 0;
   c->bar_inval = 0;
   c->bar_push = 0;
@@ -224,16 +236,16 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
   c->del_applied = c->del_absent = c->add_applied = c->add_present = 0;
-  c->affected = c->seeds = c->relaxed = c->improved = 0;
+  c->seeds = c->relaxed = c->improved = 0;
   c->rows_touched = c->rows_relocated = 0;
-  c->inval_edges = c->pull_edges = c->push_vertices = c->enqueued = 0;
+  c->pull_edges = c->push_vertices = c->enqueued = 0;
   c->merge_slots = 0;
   c->far_moves = 0;
-  c->rounds_inval = c->rounds_push = c->splits = 0;
-  c->local_episodes = c->local_rounds = c->jumps = 0;
+  c->rounds_push = c->splits = 0;
+  c->local_episodes = c->local_rounds = 0;
   c->local_ns = c->push_ns = 0;
   c->call = c->call + 1;
-  if (full) {
+  if (full == 1) {
     c->epoch = 1;
     c->phase = 1;
     c->call = 1;

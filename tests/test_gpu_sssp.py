@@ -121,6 +121,35 @@ def test_slack_zero_forces_relocation_and_pool_growth():
         assert g.info().pool_used_fwd > 0
 
 
+def test_pool_growth_rerun_keeps_the_invalidation():
+    # batches that cut tree edges and pile insertions onto a few rows of a
+    # zero-slack graph: the first attempt runs out of pool (its invalidation
+    # has already run beside the store update) and the rerun must keep what
+    # that invalidation found
+    n = 3000
+    ro, col, w = wl.er_digraph(n, 6000, 1, 50, seed=11)
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w, slack=0.0) as g:
+        g.sssp_init(0)
+        rng = np.random.default_rng(3)
+        regrows = 0
+        for k in range(8):
+            d, p = g.get_dist(parent=True)
+            kids = [x for x in rng.permutation(n) if p[x] >= 0][:40]
+            ds = np.array([p[x] for x in kids], np.int32)
+            dd = np.array(kids, np.int32)
+            u = rng.integers(0, 16, size=4000).astype(np.int32)
+            v = rng.integers(0, n, size=4000).astype(np.int32)
+            ww = rng.integers(1, 50, size=4000).astype(np.int32)
+            st = g.apply_batch(ds, dd, u, v, ww, stats=True)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == ref.apply_batch(ds, dd, u, v, ww)
+            assert st.n_del_applied == len(kids)
+            regrows += st.regrows
+            check_all(g, ref, 0)
+        assert regrows > 0
+
+
 # ---------------------------------------------------------------- edge cases
 
 def small_graph(seed=4, n=500, m=4000):
