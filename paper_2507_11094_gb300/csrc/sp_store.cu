@@ -232,6 +232,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->lbeat = 0;
   c->mcnt = 0;
   c->bstrips = 0;
+  c->mpos = 0;
   c->n_seg = 0;
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
@@ -615,6 +616,7 @@ __device__ __forceinline__ u32 warp_lower_bound(const u32 *__restrict__ a, u32 l
 // loads per strip are the strip record, the row's segment, the searches and
 // one round of item loads.
 constexpr int kStripItems = 128;   // items staged per warp
+constexpr int kMergeGrab = 4;      // strips a warp takes at a time
 struct StripItems {
   u64 pre[kStripItems];            // applied (ins << 32 | dels) of the row before the item
   u32 col[kStripItems];
@@ -630,18 +632,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
   const int lane = threadIdx.x & 31;
   StripItems &S = sitems[threadIdx.x >> 5];
   const u32 nstrips = ld_cg_u32(&c->bstrips);
-  const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
-  const u32 nw = (gridDim.x * blockDim.x) >> 5;
   const u64 cmask = (1ull << a.bits) - 1;
   bool bad = false;
-  // the next strip's record and segment are loaded while this one is
-  // processed, which takes two dependent loads off every strip's chain
-  int2 sp = gw < nstrips ? __ldcg(a.strips + gw) : make_int2(0, 0);
-  Seg sg;
-  if (gw < nstrips) sg = a.seg[sp.x];
-  for (u32 sidx = gw; sidx < nstrips; sidx += nw) {
-    const u32 nx = sidx + nw;
-    const int2 spn = nx < nstrips ? __ldcg(a.strips + nx) : sp;
+  // warps take strips kMergeGrab at a time from a global counter, so blocks
+  // that start late (SMs busy with the invalidation beside the merge) find
+  // only the work that is left
+  u32 grab = 0, gend = 0;
+  for (;;) {
+    if (grab == gend) {
+      u32 b0 = 0;
+      if (lane == 0) b0 = atomicAdd(&c->mpos, (u32)kMergeGrab);
+      grab = __shfl_sync(kFull, b0, 0);
+      gend = min(grab + (u32)kMergeGrab, nstrips);
+      if (grab >= nstrips) break;
+    }
+    const u32 sidx = grab++;
+    const int2 sp = __ldcg(a.strips + sidx);
+    const Seg sg = a.seg[sp.x];
     const Store &st = a.st[sg.dir];
     const int2 *old = st.adj + sg.old_start;
     int2 *dst = st.adj + sg.dest;
@@ -653,7 +660,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
       const int j = j0 + lane + 32 * t;
       en[t] = j < jl ? old[j] : make_int2(0, 0);
     }
-    const Seg sgn = a.seg[spn.x];
     if (j0 == 0 && lane == 0) {
       RowMeta nm;
       nm.start = sg.dest;
@@ -740,8 +746,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
         }
       }
     }
-    sp = spn;
-    sg = sgn;
   }
   if (bad) atomicExch(&c->bad, 1);
 }
