@@ -1157,8 +1157,8 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
   return out;
 }
 
-__device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst, Stage *sa,
-                                        Stage *sas, u32 *scratch, u64 *bar, u64 &target);
+__device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch);
+__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 __device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 
 template <int OP>
@@ -1235,10 +1235,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     flush_queue(q0, scratch);
   }
 
-  if (OP == kOpPush) {   // a batch's seeds: the pull over A, then OnAdd
-    bool st0 = false;
-    if (a.seed_pull) st0 = pull_stage(a, &sq, &sqs, &sa, &sas, scratch, bar, target);
-    if (!st0 && a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
+  if (OP == kOpPush) {   // a batch's seeds: OnAdd, and the pull over A
+    // (the cut list becomes A while OnAdd runs; the pull needs all of A)
+    if (a.seed_pull) cut_to_a(a, &sa, &sas, scratch);
+    if (a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
+    if (a.seed_pull) {
+      target += gridDim.x;
+      if (!grid_sync(bar, target, c, a.lim)) pull_stage(a, &sq, &sqs, scratch);
+    }
   }
 
   // state shared by all blocks (read before the first barrier; only block 0
@@ -1456,14 +1460,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
 
 // --- pull (one pass over A) -----------------------------------------------
 
-// Pull stage (block-collective).  The invalidation's cut vertices become the
-// affected list A, sized by their in-degrees in the updated reverse store
-// (the invalidation may have run beside the store update, so it could not
-// size them); after a grid barrier every vertex of A takes the minimum over
-// its in-edges, and the improved ones form the push loop's first frontier
-// (queue slot 0).  Returns whether a wait bound was hit.
-__device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst, Stage *sa,
-                                        Stage *sas, u32 *scratch, u64 *bar, u64 &target) {
+// Seeding stages of the push launch (block-collective).  cut_to_a: the
+// invalidation's cut vertices become the affected list A, sized by their
+// in-degrees in the updated reverse store (the invalidation may have run
+// beside the store update, so it could not size them).  pull_stage (after a
+// grid barrier): every vertex of A takes the minimum over its in-edges, and
+// the improved ones join the push loop's first frontier (queue slot 0).
+__device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch) {
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   {
@@ -1485,8 +1488,11 @@ __device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst
     }
     flush_queue(qa, scratch);
   }
-  target += gridDim.x;
-  if (grid_sync(bar, target, c, a.lim)) return true;
+}
+
+__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
+  Ctl *c = a.ctl;
+  const int lane = threadIdx.x & 31;
   const u64 ac = ld_cg_u64(&c->acnt);
   const u32 ne = (u32)(ac >> 32), nedge = (u32)ac;
   const u32 nsmall = ld_cg_u32(&c->ascnt);
@@ -1509,7 +1515,6 @@ __device__ __noinline__ bool pull_stage(const LoopArgs &a, Stage *st, Stage *sst
     if (q) atomicAdd(&c->seeds, q);
     if (re) atomicExch(&c->range_err, 1);
   }
-  return false;
 }
 
 // --- OnAdd: relax every applied insertion ---------------------------------
