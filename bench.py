@@ -57,8 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--delta", type=int, default=None,
-                    help="near-far bucket width of the push loop (default: 0 for R-MAT/ER, "
-                         "1500 for grids)")
+                    help="near-far bucket width of the push loop (default: picked on the "
+                         "graph by the autotuner from a few multiples of the mean weight)")
     ap.add_argument("--inval-switch", type=int, default=None,
                     help="frontier rounds of the invalidation before pointer jumping "
                          "(-1 never; default: the library's)")
@@ -287,8 +287,16 @@ def run_gb300(args):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         g = sp.Graph(W.n, W.row_off, W.col, W.w, stream=stream)
-    delta = args.delta if args.delta is not None else (1500 if W.name.startswith("grid") else 0)
-    g.set_delta(delta)
+    if args.delta is not None:
+        delta = args.delta
+        g.set_delta(delta)
+    else:   # the project's autotuner picks the near-far width on this graph
+        from paper_2507_11094_gb300 import autotune
+        with torch.cuda.stream(stream):
+            tune = autotune.tune_delta(g, lambda h, stats=False: h.sssp_init(W.source, stats=stats),
+                                       W.w, reps=1)
+        delta = tune["delta"]
+        cfg["delta_tuned_ms"] = tune["ms"]
     cfg["delta"] = delta
     if args.inval_switch is not None:
         g.set_inval_switch(args.inval_switch)
