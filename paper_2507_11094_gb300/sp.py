@@ -211,6 +211,8 @@ def _torch():
 
 
 def _is_cuda_tensor(x) -> bool:
+    if _TORCH is not None:   # the common case: one isinstance check
+        return isinstance(x, _TORCH.Tensor) and x.is_cuda
     return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
 
 
@@ -221,10 +223,9 @@ class _Arrays:
         self.keep = []
         self.ptrs = []
         dev = [a is not None and _is_cuda_tensor(a) for a in arrays]
-        present = [a is not None for a in arrays]
-        if any(dev) and not all(d for d, p in zip(dev, present) if p):
-            raise TypeError("mix of host and device arrays")
         self.on_device = any(dev)
+        if self.on_device and not all(d for d, a in zip(dev, arrays) if a is not None):
+            raise TypeError("mix of host and device arrays")
         for a, dt in zip(arrays, dtypes):
             if a is None:
                 self.ptrs.append(None)
