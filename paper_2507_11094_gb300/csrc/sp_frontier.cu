@@ -503,28 +503,24 @@ struct PullOp {
 
   __device__ __forceinline__ u32 vdata(u32) { return 0; }
   __device__ __forceinline__ u64 load(int2 e) { return ld_cg_u64(s + e.x); }
-  __device__ __forceinline__ bool offer(u32 v, u64 best) {
-    if (best == ~0ull || best >= ld_cg_u64(s + v)) return false;
-    const u64 old = atomicMin((unsigned long long *)(s + v), best);
-    if (!(best < old)) return false;
-    atomicMin(seed_min, dist_of(best));
-    return atomicExch(qflag + v, tag) != tag;
-  }
   __device__ __forceinline__ void run(const bool *act, const u32 *ov, const u32 *,
                                       const int2 *ed, const u64 *sx) {
     const int lane = threadIdx.x & 31;
-    u32 tx[K];
-    bool want[K];
-    int nw = 0;
+    // the lane's candidates: a run of edges of one vertex that ends inside
+    // the lane is kept in the slot of the edge that ended it (slot 0 never
+    // ends a run, so it takes the lane's last run once the warp has combined
+    // it with the lanes that end on the same vertex); every offer's load,
+    // atomicMin and dedupe exchange then goes out together
+    u32 cv[K];
+    u64 cb[K];
+    bool has[K];
     u32 bv = kNoEdge;
     u64 best = ~0ull;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      want[k] = false;
-      tx[k] = 0;
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+      has[k] = false;
+      cv[k] = 0;
+      cb[k] = ~0ull;
       if (act[k]) {
         ++n_edges;
         u64 cand = ~0ull;
@@ -535,10 +531,10 @@ struct PullOp {
           else cand = pack(nd, (u32)ed[k].x);
         }
         if (ov[k] != bv) {           // owner changed inside this lane's run
-          if (bv != kNoEdge && offer(bv, best)) {
-            tx[nw] = bv;
-            want[nw] = true;
-            ++nw;
+          if (bv != kNoEdge && best != ~0ull) {
+            cv[k] = bv;
+            cb[k] = best;
+            has[k] = true;
           }
           bv = ov[k];
           best = ~0ull;
@@ -555,12 +551,33 @@ struct PullOp {
     }
     const u32 pv = __shfl_up_sync(kFull, bv, 1);
     const bool head = bv != kNoEdge && (lane == 0 || pv != bv);
-    if (head && nw < K && offer(bv, best)) {
-      tx[nw] = bv;
-      want[nw] = true;
-      ++nw;
+    if (head && best != ~0ull) {
+      cv[0] = bv;
+      cb[0] = best;
+      has[0] = true;
     }
-    enqueue(next, row, tx, want, K, n_enq);
+    u64 cur[K], old[K];
+    bool imp[K], want[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) cur[k] = has[k] ? ld_cg_u64(s + cv[k]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      has[k] = has[k] && cb[k] < cur[k];
+      old[k] = has[k] ? atomicMin((unsigned long long *)(s + cv[k]), cb[k]) : 0ull;
+    }
+    u32 mind = kInf;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      imp[k] = has[k] && cb[k] < old[k];
+      if (imp[k] && dist_of(cb[k]) < mind) mind = dist_of(cb[k]);
+    }
+    if (mind < kInf) atomicMin(seed_min, mind);
+    u32 pr[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) pr[k] = imp[k] ? atomicExch(qflag + cv[k], tag) : tag;
+#pragma unroll
+    for (int k = 0; k < K; ++k) want[k] = imp[k] && pr[k] != tag;
+    enqueue(next, row, cv, want, K, n_enq);
   }
 };
 
