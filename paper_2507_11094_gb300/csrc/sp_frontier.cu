@@ -86,18 +86,21 @@ __device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Li
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd((unsigned long long *)bar, 1ull);
-    if (ld_acquire_u64(bar) < target) {
+    // the count before this arrival says whether it was the last one; the
+    // wait polls the count alone and looks at the timeout flag and the
+    // clock every 16th poll
+    if (atomicAdd((unsigned long long *)bar, 1ull) + 1 < target) {
       const u64 t0 = globaltimer_ns();
-      u32 nap = 20;
+      u32 polls = 0;
       while (ld_acquire_u64(bar) < target) {
-        if (ld_cg_i32(&c->timeout) != 0) break;
-        if (globaltimer_ns() - t0 > lim.wait_ns) {
-          raise_timeout(c, 2, 2, (u32)(target / gridDim.x));
-          break;
+        if ((++polls & 15u) == 0) {
+          if (ld_cg_i32(&c->timeout) != 0) break;
+          if (globaltimer_ns() - t0 > lim.wait_ns) {
+            raise_timeout(c, 2, 2, (u32)(target / gridDim.x));
+            break;
+          }
         }
-        __nanosleep(nap);
-        if (nap < 256) nap += nap >> 1;
+        __nanosleep(64);
       }
     }
     s_stop = ld_cg_i32(&c->timeout) != 0;
