@@ -213,8 +213,11 @@ cudaError_t retarget_input_nodes(sp_graph *g, const int *ds, const int *dd, long
   return e;
 }
 
-sp_status read_ctl(sp_graph *g) {
-  cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream);
+// The control block of the call, on the host.  mirrored: the call ended
+// with k_finish, which wrote it into the pinned copy already.
+sp_status read_ctl(sp_graph *g, bool mirrored = false) {
+  if (!mirrored)
+    cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream);
   if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
     cudaGetLastError();
     return SP_ECUDA;
@@ -589,7 +592,7 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats) {
     g->state = 2;
     return SP_ECUDA;
   }
-  sp_status rc = read_ctl(g);
+  sp_status rc = read_ctl(g, true);
   if (rc != SP_OK) {
     g->state = 2;
     return rc;
@@ -713,7 +716,7 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
       g->state = 2;
       return SP_ECUDA;
     }
-    rc = read_ctl(g);
+    rc = read_ctl(g, true);   // the batch ends with k_finish, replayed or not
     if (rc != SP_OK) {
       g->state = 2;
       return rc;
@@ -776,7 +779,7 @@ sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
   rec(g, timed, SP_NPHASE - 1);
   sp::launch_finish(g, &launches);
   rec(g, timed, SP_NPHASE);
-  sp_status rc = read_ctl(g);
+  sp_status rc = read_ctl(g, true);
   g->al.put(src_d, (size_t)k * 4);
   if (e != cudaSuccess) {
     g->last_err = (int)e;
@@ -921,7 +924,7 @@ sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, cons
       cudaStreamSynchronize(g->stream);
       return SP_ECUDA;
     }
-    rc = read_ctl(g);
+    rc = read_ctl(g, true);
     if (rc != SP_OK) return rc;
     const Ctl &c = *g->ctl_host;
     if (c.status != 0) return (sp_status)c.status;
@@ -1194,7 +1197,7 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
       g->tc_state = 0;
       return SP_ECUDA;
     }
-    rc = read_ctl(g);
+    rc = read_ctl(g, true);
     if (rc != SP_OK) return rc;
     const Ctl &c = *g->ctl_host;
     if (c.status != 0) return (sp_status)c.status;   // nothing changed

@@ -750,10 +750,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
   if (bad) atomicExch(&c->bad, 1);
 }
 
-__global__ void k_finish(Ctl *c) {
-  if (c->status == 0 && c->need_grow == 0) {
+// The call's bookkeeping, then the whole control block into the host's
+// pinned copy (mapped memory), so the host needs no copy of its own.
+__global__ void k_finish(Ctl *c, Ctl *host) {
+  if (threadIdx.x == 0 && c->status == 0 && c->need_grow == 0) {
     c->pool_used[0] = c->pool_need[0];
     c->pool_used[1] = c->pool_need[1];
+  }
+  __syncthreads();
+  if (host) {
+    const u32 *src = (const u32 *)c;
+    u32 *dst = (u32 *)host;
+    for (u32 i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
   }
 }
 
@@ -1011,7 +1019,7 @@ void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd,
 }
 
 void launch_finish(sp_graph *g, int *launches) {
-  k_finish<<<1, 1, 0, g->stream>>>(g->ctl);
+  k_finish<<<1, 256, 0, g->stream>>>(g->ctl, g->ctl_host);
   ++*launches;
 }
 
