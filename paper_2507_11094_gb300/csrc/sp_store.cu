@@ -628,7 +628,7 @@ struct StripItems {
 __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
   __shared__ StripItems sitems[kThreads / 32];
   Ctl *c = a.ctl;
-  if (!merge_enabled(c)) return;
+  if (!__shfl_sync(kFull, (int)merge_enabled(c), 0)) return;   // warp-uniform
   const int lane = threadIdx.x & 31;
   StripItems &S = sitems[threadIdx.x >> 5];
   const u32 nstrips = ld_cg_u32(&c->bstrips);

@@ -423,6 +423,72 @@ def test_merge_tiers_hub_rows():
         assert g.info().pool_used_fwd > 0      # the hub row moved on the second batch
 
 
+def test_store_update_strip_cases():
+    """The store update's strips: a 40,000-edge row (157 strips, so the
+    look-back crosses several windows) touched in its last strip only and
+    then all over; a 10-edge row that gets 400 items (more than a strip
+    stages: runs of duplicate insertions, delete-and-reinsert, an absent
+    deletion); a 3,000-edge row with 450 items inside one strip."""
+    n = 90000
+    rng = np.random.default_rng(21)
+    edges = {}
+    for v in range(2, 80002, 2):
+        edges[(0, v)] = int(rng.integers(1, 100))
+    for v in rng.choice(np.arange(2, n), 10, replace=False):
+        edges[(1, int(v))] = int(rng.integers(1, 100))
+    for k in range(1, 3001):
+        edges[(2, 3 * k)] = int(rng.integers(1, 100))
+    for _ in range(80000):
+        a, b = int(rng.integers(3, n)), int(rng.integers(n))
+        if a != b:
+            edges.setdefault((a, b), int(rng.integers(1, 100)))
+    keys = sorted(edges)
+    u = np.array([k[0] for k in keys], np.int64)
+    ro = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(u, minlength=n), out=ro[1:])
+    col = np.array([k[1] for k in keys], np.int32)
+    w = np.array([edges[k] for k in keys], np.int32)
+    ref = oracle.OracleGraph(n, ro, col, w)
+
+    def apply(g, ds, dd, as_, ad, aw):
+        ds, dd, as_, ad, aw = (np.asarray(x, np.int32) for x in (ds, dd, as_, ad, aw))
+        st = g.apply_batch(ds, dd, as_, ad, aw, stats=True)
+        cnt = ref.apply_batch(ds, dd, as_, ad, aw)
+        assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                st.n_add_present) == cnt
+        check_all(g, ref, 0)
+
+    with sp.Graph(n, ro, col, w) as g:
+        g.sssp_init(0)
+        check_all(g, ref, 0)
+        # row 0, last strip only: five deletions, three insertions
+        row0 = col[ro[0]:ro[1]]
+        apply(g, [0] * 5, row0[-5:], [0] * 3, [80003, 79999, 80001], [5, 6, 7])
+        # row 1: 300 new edges, 60 duplicates of them, delete 5, reinsert 3
+        row1 = col[ro[1]:ro[2]]
+        absent = np.setdiff1d(np.arange(3, n), np.concatenate([row1, [1]]))
+        new1 = rng.choice(absent, 300, replace=False)
+        dup = rng.choice(new1, 60)
+        add_d = np.concatenate([new1, dup, row1[:3]])
+        add_w = rng.integers(1, 100, add_d.size)
+        del_d = np.concatenate([row1[:5], [absent[-1]]])
+        apply(g, [1] * del_d.size, del_d, [1] * add_d.size, add_d, add_w)
+        # row 2: one strip (entries 1280..1535) gets 450 items
+        row2 = np.arange(3, 9003, 3)
+        span = row2[1280:1536]
+        gone = rng.choice(span, 200, replace=False)
+        back = gone[:50]
+        fresh = rng.choice(np.arange(span[0] + 1, span[-1], 3), 150, replace=False)
+        add_d = np.concatenate([back, fresh, fresh[:50]])
+        add_w = rng.integers(1, 100, add_d.size)
+        apply(g, [2] * gone.size, gone, [2] * add_d.size, add_d, add_w)
+        # row 0 all over: 2,000 deletions and 2,000 insertions
+        row0 = ref.csr()[1][ref.csr()[0][0]:ref.csr()[0][1]]
+        dels = rng.choice(row0, 2000, replace=False)
+        ins = rng.choice(np.arange(3, 80003, 2), 2000, replace=False)
+        apply(g, [0] * 2000, dels, [0] * 2000, ins, rng.integers(1, 100, 2000))
+
+
 @pytest.mark.parametrize("delta", [1, 300, 2500])
 def test_grid_near_far_matches_oracle(delta):
     W = wl.grid(48, 48, batch_frac=0.03, seed=4)
