@@ -623,6 +623,8 @@ struct StripItems {
   u32 w[kStripItems];
   u32 opos[kStripItems];
   unsigned char fl[kStripItems];   // bit0 applied, bit1 present, bit2 insertion
+  Seg seg[kMergeGrab];             // the grabbed strips' segments
+  int2 sp[kMergeGrab];             // ... and strip records
 };
 
 __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
@@ -637,18 +639,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
   // warps take strips kMergeGrab at a time from a global counter, so blocks
   // that start late (SMs busy with the invalidation beside the merge) find
   // only the work that is left
-  u32 grab = 0, gend = 0;
+  u32 grab = 0, gend = 0, g0 = 0;
   for (;;) {
     if (grab == gend) {
       u32 b0 = 0;
       if (lane == 0) b0 = atomicAdd(&c->mpos, (u32)kMergeGrab);
-      grab = __shfl_sync(kFull, b0, 0);
+      grab = g0 = __shfl_sync(kFull, b0, 0);
       gend = min(grab + (u32)kMergeGrab, nstrips);
       if (grab >= nstrips) break;
+      // the grabbed strips' records and segments in one round of loads
+      // each, one lane per strip (the later strips' old entries are
+      // prefetched toward L2 a strip ahead)
+      __syncwarp();   // every lane is done with the previous grab's records
+      if (lane < (int)(gend - grab)) {
+        const int2 q = __ldcg(a.strips + grab + lane);
+        S.sp[lane] = q;
+        S.seg[lane] = a.seg[q.x];
+      }
+      __syncwarp();
     }
     const u32 sidx = grab++;
-    const int2 sp = __ldcg(a.strips + sidx);
-    const Seg sg = a.seg[sp.x];
+    const int2 sp = S.sp[sidx - g0];
+    const Seg sg = S.seg[sidx - g0];
+    if (grab < gend && lane < kStrip * 8 / 128) {   // the next strip's old entries
+      const Seg &nx = S.seg[grab - g0];
+      const int nj = S.sp[grab - g0].y + lane * (128 / 8);
+      if (nj < nx.old_deg) {
+        const int2 *p = a.st[nx.dir].adj + nx.old_start + nj;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+      }
+    }
     const Store &st = a.st[sg.dir];
     const int2 *old = st.adj + sg.old_start;
     int2 *dst = st.adj + sg.dest;

@@ -424,11 +424,11 @@ def test_merge_tiers_hub_rows():
 
 
 def test_store_update_strip_cases():
-    """The store update's strips: a 40,000-edge row (157 strips, so the
-    look-back crosses several windows) touched in its last strip only and
-    then all over; a 10-edge row that gets 400 items (more than a strip
-    stages: runs of duplicate insertions, delete-and-reinsert, an absent
-    deletion); a 3,000-edge row with 450 items inside one strip."""
+    """The store update's strips: a 40,000-edge row (157 strips) touched in
+    its last strip only and then all over; a 10-edge row that gets 400 items
+    (more than a strip stages: runs of duplicate insertions,
+    delete-and-reinsert, an absent deletion); a 3,000-edge row with 450
+    items inside one strip."""
     n = 90000
     rng = np.random.default_rng(21)
     edges = {}
