@@ -244,51 +244,86 @@ __device__ __forceinline__ u32 block_excl_scan(u32 x, u32 *scratch, u32 *total) 
   return r;
 }
 
-// Publish a block's staged queue entries (block-collective): one global
-// atomic for the whole block, then entries and chunk owners are written.
-__device__ __noinline__ void flush_queue(const Queue &q, u32 *scratch) {
-  Stage *st = q.st;
+// Publish a block's staged appends (block-collective): up to two queues
+// (entries with their chunk owners, and small lists) and one far pile.
+// Every list takes one global atomic, each issued by its own thread and all
+// of them together, so the block waits for one round trip instead of one per
+// list; then the entries are written out.  scratch needs 39 words.
+__device__ __forceinline__ void flush_stages(const Queue *q1, const Queue *q2, Stage *fst,
+                                          u32 *pile, u32 *pcnt, u32 *pmin, u32 *scratch) {
   __syncthreads();
-  const u32 n = *(volatile u32 *)&st->n;
-  if (n) {
-    const u32 per = (n + blockDim.x - 1) / blockDim.x;
-    const u32 b = min(threadIdx.x * per, n), e = min(b + per, n);
-    u32 sum = 0;
-    for (u32 i = b; i < e; ++i) sum += st->d[i];
-    u32 total;
-    u32 run = block_excl_scan(sum, scratch, &total);
-    if (threadIdx.x == 0) {
-      const u64 base = atomicAdd(q.cnt, ((u64)n << 32) | (u64)total);
-      scratch[32] = (u32)(base >> 32);
-      scratch[33] = (u32)base;
+  const Queue *qs[2] = {q1, q2};
+  const u32 t = threadIdx.x;
+  u32 n[2], ns[2], b[2], e[2], run[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    n[j] = qs[j] && qs[j]->st ? *(volatile u32 *)&qs[j]->st->n : 0u;
+    ns[j] = qs[j] && qs[j]->sst ? *(volatile u32 *)&qs[j]->sst->n : 0u;
+    b[j] = e[j] = run[j] = 0;
+    if (n[j]) {   // block-uniform
+      const Stage *st = qs[j]->st;
+      const u32 per = (n[j] + blockDim.x - 1) / blockDim.x;
+      b[j] = min(t * per, n[j]);
+      e[j] = min(b[j] + per, n[j]);
+      u32 sum = 0;
+      for (u32 i = b[j]; i < e[j]; ++i) sum += st->d[i];
+      u32 total;
+      run[j] = block_excl_scan(sum, scratch, &total);
+      if (t == 64u * j) {
+        const u64 base = atomicAdd(qs[j]->cnt, ((u64)n[j] << 32) | (u64)total);
+        scratch[32 + 3 * j] = (u32)(base >> 32);
+        scratch[33 + 3 * j] = (u32)base;
+      }
     }
-    __syncthreads();
-    u32 slot = scratch[32] + b;
-    u32 eb = scratch[33] + run;
-    for (u32 i = b; i < e; ++i) {
-      const u32 d = st->d[i];
-      q.ent[slot] = make_int2((int)st->v[i], (int)eb);
-      const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + d - 1) / kChunk;
-      for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
-      ++slot;
-      eb += d;
+    if (ns[j] && t == 64u * j + 32u) scratch[34 + 3 * j] = atomicAdd(qs[j]->scnt, ns[j]);
+  }
+  const u32 nf = fst ? *(volatile u32 *)&fst->n : 0u;
+  if (nf && t == 128u) {
+    scratch[38] = atomicAdd(pcnt, nf);
+    atomicMin(pmin, *(volatile u32 *)&fst->vmin);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (n[j]) {
+      const Queue &q = *qs[j];
+      u32 slot = scratch[32 + 3 * j] + b[j];
+      u32 eb = scratch[33 + 3 * j] + run[j];
+      for (u32 i = b[j]; i < e[j]; ++i) {
+        const u32 d = q.st->d[i];
+        q.ent[slot] = make_int2((int)q.st->v[i], (int)eb);
+        const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + d - 1) / kChunk;
+        for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
+        ++slot;
+        eb += d;
+      }
+    }
+    if (ns[j]) {
+      const u32 base = scratch[34 + 3 * j];
+      for (u32 i = t; i < ns[j]; i += blockDim.x) qs[j]->sv[base + i] = qs[j]->sst->v[i];
+    }
+  }
+  if (nf) {
+    const u32 base = scratch[38];
+    for (u32 i = t; i < nf; i += blockDim.x) pile[base + i] = fst->v[i];
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (qs[j] && qs[j]->st) qs[j]->st->n = 0;
+      if (qs[j] && qs[j]->sst) qs[j]->sst->n = 0;
+    }
+    if (fst) {
+      fst->n = 0;
+      fst->vmin = 0xFFFFFFFFu;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) st->n = 0;
-  Stage *ss = q.sst;
-  if (ss) {   // small list: one atomic, then a coalesced copy
-    const u32 ns = *(volatile u32 *)&ss->n;
-    if (ns) {
-      if (threadIdx.x == 0) scratch[34] = atomicAdd(q.scnt, ns);
-      __syncthreads();
-      const u32 base = scratch[34];
-      for (u32 i = threadIdx.x; i < ns; i += blockDim.x) q.sv[base + i] = ss->v[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) ss->n = 0;
-  }
-  __syncthreads();
+}
+
+__device__ __forceinline__ void flush_queue(const Queue &q, u32 *scratch) {
+  flush_stages(&q, nullptr, nullptr, nullptr, nullptr, nullptr, scratch);
 }
 
 // Append each lane's wanted vertices to a far pile (warp-collective) and
@@ -337,25 +372,9 @@ __device__ __forceinline__ void far_append(u32 *pile, u32 *cnt, u32 *far_min, St
 }
 
 // Publish a block's staged far-pile entries (block-collective).
-__device__ __noinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *far_min,
-                                       u32 *scratch) {
-  __syncthreads();
-  const u32 n = *(volatile u32 *)&st->n;
-  if (n) {
-    if (threadIdx.x == 0) {
-      scratch[32] = atomicAdd(cnt, n);
-      atomicMin(far_min, *(volatile u32 *)&st->vmin);
-    }
-    __syncthreads();
-    const u32 base = scratch[32];
-    for (u32 i = threadIdx.x; i < n; i += blockDim.x) pile[base + i] = st->v[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->n = 0;
-    st->vmin = 0xFFFFFFFFu;
-  }
-  __syncthreads();
+__device__ __forceinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *far_min,
+                                          u32 *scratch) {
+  flush_stages(nullptr, nullptr, st, pile, cnt, far_min, scratch);
 }
 
 // --- edge operations ------------------------------------------------------
@@ -1235,8 +1254,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       if (!a.concurrent) enqueue(q0, a.fwd.row, v, hit, 1, n_enq);
       far_append(a.cut, &c->ccnt, &c->cmin, &sf, v, hit, 1, 0u);
     }
-    if (!a.concurrent) flush_queue(q0, scratch);
-    flush_far(&sf, a.cut, &c->ccnt, &c->cmin, scratch);
+    flush_stages(a.concurrent ? nullptr : &q0, nullptr, &sf, a.cut, &c->ccnt, &c->cmin, scratch);
   }
   if (OP == kOpFlag && a.n_del > 0) {
     // the phase's destinations are the flags' seeds
@@ -1259,6 +1277,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     // (the cut list becomes A while OnAdd runs; the pull needs all of A)
     if (a.seed_pull) cut_to_a(a, &sa, &sas, scratch);
     if (a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
+    if (a.seed_pull || a.n_items > 0) {   // both stages' appends in one flush
+      const Queue qa = make_queue(a.aent, a.aown, &c->acnt, a.asv, &c->ascnt, &sa, &sas);
+      const Queue q0 =
+          make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, &sq, &sqs);
+      flush_stages(a.seed_pull ? &qa : nullptr, a.n_items > 0 ? &q0 : nullptr, nullptr,
+                   nullptr, nullptr, nullptr, scratch);
+    }
     if (a.seed_pull) {
       target += gridDim.x;
       if (!grid_sync(bar, target, c, a.lim)) pull_stage(a, &sq, &sqs, scratch);
@@ -1412,13 +1437,16 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       n_edges += op.n_edges;
       n_enq += op.n_enq;
       n_aff += op.n_aff;
-      flush_far(&sf, a.cut, &c->ccnt, &c->cmin, scratch);
     }
-    // publish this block's staged appends before the barrier
-    flush_queue(qn, scratch);
-    if (nf) {
+    // publish this block's staged appends before the barrier: the next
+    // frontier and the far pile (the invalidation's: the cut list)
+    if (OP == kOpInval) {
+      flush_stages(&qn, nullptr, &sf, a.cut, &c->ccnt, &c->cmin, scratch);
+    } else if (nf) {
       const u32 fp = split ? fk : f;
-      flush_far(&sf, a.fq[fp], fcnt_ptr(c, fp), fmin_ptr(c, fp), scratch);
+      flush_stages(&qn, nullptr, &sf, a.fq[fp], fcnt_ptr(c, fp), fmin_ptr(c, fp), scratch);
+    } else {
+      flush_queue(qn, scratch);
     }
     if (split) {
       f = next3(f);
@@ -1506,7 +1534,7 @@ __device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, 
       }
       enqueue(qa, a.rev.row, v, want, K, dummy);
     }
-    flush_queue(qa, scratch);
+    // published by the caller, together with OnAdd's appends
   }
 }
 
@@ -1587,7 +1615,7 @@ __device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst,
     }
     enqueue(q0, a.fwd.row, v, want, 1, n_enq);
   }
-  flush_queue(q0, scratch);
+  // published by the caller, together with the cut list's
   u64 q = warp_sum(n_enq);
   int re = __any_sync(kFull, range_err);
   if (lane == 0) {

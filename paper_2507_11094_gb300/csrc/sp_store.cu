@@ -616,7 +616,7 @@ __device__ __forceinline__ u32 warp_lower_bound(const u32 *__restrict__ a, u32 l
 // loads per strip are the strip record, the row's segment, the searches and
 // one round of item loads.
 constexpr int kStripItems = 128;   // items staged per warp
-constexpr int kMergeGrab = 4;      // strips a warp takes at a time
+constexpr int kMergeGrab = 8;      // strips a warp takes at a time
 struct StripItems {
   u64 pre[kStripItems];            // applied (ins << 32 | dels) of the row before the item
   u32 col[kStripItems];
