@@ -1196,9 +1196,9 @@ __device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32
   return out;
 }
 
-__device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch);
-__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
-__device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
+__device__ __forceinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch);
+__device__ __forceinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
+__device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 
 template <int OP>
 __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
@@ -1514,7 +1514,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
 // beside the store update, so it could not size them).  pull_stage (after a
 // grid barrier): every vertex of A takes the minimum over its in-edges, and
 // the improved ones join the push loop's first frontier (queue slot 0).
-__device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch) {
+__device__ __forceinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, u32 *scratch) {
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   {
@@ -1538,7 +1538,7 @@ __device__ __noinline__ void cut_to_a(const LoopArgs &a, Stage *sa, Stage *sas, 
   }
 }
 
-__device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
+__device__ __forceinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   const u64 ac = ld_cg_u64(&c->acnt);
@@ -1569,7 +1569,7 @@ __device__ __noinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *sst
 
 // OnAdd stage (block-collective): every applied insertion (u, v, w) is
 // relaxed; an improved v joins the push loop's first frontier (slot 0).
-__device__ __noinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
+__device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch) {
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   const u32 tag = ld_cg_u32(&c->epoch);
