@@ -930,7 +930,7 @@ struct LocalState {      // what an episode hands back to the loop
 
 // Block 0 only (block-collective).  smem: 7 * kLocalCap words that no other
 // stage of the push loop uses while the episode runs.
-__device__ __noinline__ LocalState local_rounds(const LoopArgs &a, u32 cur, u32 round, u32 thresh,
+__device__ __forceinline__ LocalState local_rounds(const LoopArgs &a, u32 cur, u32 round, u32 thresh,
                                                 u32 f, u32 phase, bool nf, u32 *smem,
                                                 Stage *sf, u32 *scratch) {
   LocalState out{};
@@ -1115,7 +1115,7 @@ __device__ __noinline__ LocalState local_rounds(const LoopArgs &a, u32 cur, u32 
 // runs them and hands the loop state back through the control block; the
 // others wait for it, bounded by block 0's heartbeat.  Counters in the
 // result are this thread's.
-__device__ __noinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32 cur, u32 round,
+__device__ __forceinline__ LocalState local_episode(const LoopArgs &a, u32 lep, u32 cur, u32 round,
                                                  u32 thresh, u32 f, u32 phase, bool nf,
                                                  u32 *smem, Stage *sf, u32 *scratch) {
   Ctl *c = a.ctl;
