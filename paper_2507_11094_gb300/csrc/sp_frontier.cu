@@ -809,7 +809,7 @@ struct JumpState {
   u32 jumps, capped;
 };
 
-__device__ __noinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 target,
+__device__ __forceinline__ JumpState jump_phase(const LoopArgs &a, u64 *bar, u64 target,
                                              u32 *scratch, Stage *cst) {
   Ctl *c = a.ctl;
   u32 jumps = 0;
