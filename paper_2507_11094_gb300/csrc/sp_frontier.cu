@@ -248,7 +248,8 @@ __device__ __forceinline__ u32 block_excl_scan(u32 x, u32 *scratch, u32 *total) 
 // (entries with their chunk owners, and small lists) and one far pile.
 // Every list takes one global atomic, each issued by its own thread and all
 // of them together, so the block waits for one round trip instead of one per
-// list; then the entries are written out.  scratch needs 39 words.
+// list; then the entries are written out.  scratch needs 39 words and the
+// block more than 128 threads.
 __device__ __forceinline__ void flush_stages(const Queue *q1, const Queue *q2, Stage *fst,
                                           u32 *pile, u32 *pcnt, u32 *pmin, u32 *scratch) {
   __syncthreads();
