@@ -473,10 +473,12 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
                             int inputs_on_device, int64_t *count, sp_batch_stats *stats);
 
 /*
- * sp_apply_batch runs its ~35 kernels as a cached CUDA graph when a batch has
- * the same shape (deletion and insertion counts, stats or not) as the one
- * before it: the inputs are copied to internal buffers and one graph launch
- * replaces the kernel launches.  The graph is rebuilt when a buffer or a
+ * sp_apply_batch runs its kernels (seven per batch) as a cached CUDA graph
+ * when a batch has the same shape (deletion and insertion counts, stats or
+ * not) as the one before it: one graph launch replaces the kernel launches.
+ * Device inputs are read where they are (the two kernels that read them are
+ * pointed at this call's arrays before the launch); host inputs are first
+ * copied to internal buffers.  The graph is rebuilt when a buffer or a
  * setting changes.  on = 0 turns it off (every call launches kernels one by
  * one); the default is 1.  Results do not depend on it.  Requires a
  * non-default stream (graphs are never used on the legacy stream).
@@ -491,8 +493,8 @@ sp_status sp_set_batch_graphs(sp_graph *g, int32_t on);
  * spent in the push loop, [9] the bound that ended the last call early (0
  * none, 1 a round or pass cap, 2 a barrier wait), [10] where it was hit (1
  * a loop's round cap, 2 a loop's grid barrier, 3 the wait for a
- * single-block episode, 4 the batch sort's grid barrier), [11] the round,
- * barrier index or episode there.  k (<= 12) entries are written; the
+ * single-block episode, 4 the batch sort's grid barrier, 5 the count pass's
+ * grid barrier), [11] the round, barrier index or episode there.  k (<= 12) entries are written; the
  * figures are those of the last synchronous call.
  */
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
