@@ -64,7 +64,13 @@ def parse():
                          "(-1 never; default: the library's)")
     ap.add_argument("--local-rounds", type=int, default=None,
                     help="frontier-edge bound of single-block push rounds (0 = off; "
-                         "default: the library's)")
+                         "default: picked by the autotuner)")
+    ap.add_argument("--pool-rounds", type=int, default=None,
+                    help="block-local sub-rounds per push round (0 = off; default: "
+                         "picked by the autotuner)")
+    ap.add_argument("--small-deg", type=int, default=None,
+                    help="out-degree bound of thread-per-vertex expansion (default: "
+                         "picked by the autotuner)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--algo", default="sssp", choices=["sssp", "pr", "tc"],
                     help="sssp (default), pr (dynamic PageRank on the same workloads) or "
@@ -287,23 +293,25 @@ def run_gb300(args):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         g = sp.Graph(W.n, W.row_off, W.col, W.w, stream=stream)
-    if args.delta is not None:
-        delta = args.delta
-        g.set_delta(delta)
-    else:   # the project's autotuner picks the near-far width on this graph
-        from paper_2507_11094_gb300 import autotune
+    from paper_2507_11094_gb300 import autotune
+    manual = {"delta": args.delta, "pool_rounds": args.pool_rounds,
+              "small_deg": args.small_deg, "local_edges": args.local_rounds}
+    if any(v is not None for v in manual.values()):
+        sched = {k: (v if v is not None else autotune.DEFAULT[k]) for k, v in manual.items()}
+        autotune.apply_schedule(g, sched)
+        cfg["schedule_source"] = "command line"
+    else:   # the project's autotuner picks the push schedule on this graph
         with torch.cuda.stream(stream):
-            tune = autotune.tune_delta(g, lambda h, stats=False: h.sssp_init(W.source, stats=stats),
-                                       W.w, reps=1)
-        delta = tune["delta"]
-        cfg["delta_tuned_ms"] = tune["ms"]
-    cfg["delta"] = delta
+            tune = autotune.tune_schedule(
+                g, lambda h, stats=False: h.sssp_init(W.source, stats=stats), W.w, reps=1)
+        sched = tune["schedule"]
+        cfg["schedule_source"] = "autotuner (from-scratch solve per candidate)"
+        cfg["schedule_tuned_ms"] = dict(sorted(tune["ms"].items(), key=lambda kv: kv[1])[:6])
+    cfg["schedule"] = sched
+    cfg["delta"] = sched["delta"]
     if args.inval_switch is not None:
         g.set_inval_switch(args.inval_switch)
         cfg["inval_switch"] = args.inval_switch
-    if args.local_rounds is not None:
-        g.set_local_rounds(args.local_rounds)
-        cfg["local_rounds"] = args.local_rounds
     g.sssp_init(W.source)
 
     tree = W.tree_fraction > 0
@@ -423,6 +431,31 @@ def run_gb300(args):
         if ent and ent.get("valid", False):
             traffic = ent["bytes_per_launch"]
 
+    # the relaxation kernels' own roofline (the push launch: pull, OnAdd and
+    # the push fixedPoint), for the dynamic repair and the static recompute
+    n_steps = max(1, len(lat_ms))
+    push_dyn_b = ph_bytes["push"] / n_steps
+    push_dyn_ms = ph_ms["push"] / n_steps
+    push_st_b = sst.alg_bytes[sp.PHASES.index("push")]
+    push_st_ms = sst.ms_phase[sp.PHASES.index("push")]
+
+    def _push_roof(b, ms, traffic_key):
+        ach = b / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        tr = None
+        if os.path.exists(tf):
+            with open(tf) as f:
+                ent = json.load(f).get(W.name, {}).get(traffic_key)
+            if ent and ent.get("valid", False):
+                tr = ent["bytes_per_launch"]
+        return {"achieved": ach, "frac": ach / peak if peak else None,
+                "alg_bytes_per_launch": b, "ms_per_launch": ms, "traffic": tr,
+                "traffic_frac": (tr / (ms * 1e-3) / 1e9 / peak) if (tr and peak and ms > 0)
+                else None}
+
+    roof_push = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                 "dynamic": _push_roof(push_dyn_b, push_dyn_ms, "push"),
+                 "static": _push_roof(push_st_b, push_st_ms, "push_static")}
+
     line = None
     if rank == 0:
         cpu = None
@@ -471,6 +504,7 @@ def run_gb300(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "traffic": traffic},
+            "roofline_push": roof_push,
             "phase_ms": {p: ph_ms[p] / len(lat_ms) for p in phases},
             "phase_alg_bytes": {p: ph_bytes[p] / len(lat_ms) for p in phases},
             "per_step": {
@@ -496,13 +530,7 @@ def run_gb300(args):
 
 
 def batched_workloads(seed: int, k: int = 64):
-    """64 R-MAT graphs, scales ~U{12..18}, edge factor 16, w~U[1,100], own
-    source (max out-degree), own batch of ~U[0.5%, 5%] of its m (50/50)."""
-    rng = np.random.default_rng(seed)
-    scales = rng.integers(12, 19, size=k)
-    fracs = rng.uniform(0.005, 0.05, size=k)
-    return [wl.rmat(scale=int(sc), batch_frac=float(fr), seed=seed * 100 + i)
-            for i, (sc, fr) in enumerate(zip(scales, fracs))]
+    return wl.batched_rmat(seed, k)
 
 
 def run_batched(args):
@@ -519,7 +547,7 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     B = batched.BatchedGraphs([(W.n, W.row_off, W.col, W.w) for W in ws],
                               [W.source for W in ws], stream=stream)
-    tune = autotune.tune_delta(B.g, lambda h, stats=False: h.sssp_init_multi(
+    tune = autotune.tune_schedule(B.g, lambda h, stats=False: h.sssp_init_multi(
         B.packed.sources, stats=stats), B.packed.w, reps=1)
     packed = [batched.pack_batches(B.packed, r) for r in rounds]
     dev_rounds = [[torch.from_numpy(a).cuda() for a in arr] for arr in packed]
@@ -576,7 +604,8 @@ def run_batched(args):
         "config": {"workload": "batched64-rmat12..18", "graphs": len(ws),
                    "n_total": int(sum(W.n for W in ws)), "m_total": int(sum(W.m for W in ws)),
                    "updates_per_round": int(packed[0][0].size + packed[0][2].size),
-                   "delta": tune["delta"], "l2": "flushed between steps"},
+                   "schedule": tune["schedule"], "delta": tune["delta"],
+                   "l2": "flushed between steps"},
         "sequential": {"value": ups / (sum(ms_s) * 1e-3), "ms_per_step": sum(ms_s) / K},
         "speedup_vs_sequential": sum(ms_s) / sum(ms_b),
         "p50_ms": percentile(ms_b, 50), "p99_ms": percentile(ms_b, 99),
@@ -587,29 +616,11 @@ def run_batched(args):
 
 
 def serving_workloads(seed: int, big_scale: int = 22):
-    """2 R-MAT graphs of scale big_scale + 6 of scale ~U{16..20}, edge factor
-    16, w~U[1,100], each with its own source (max out-degree vertex)."""
-    rng = np.random.default_rng(seed)
-    scales = [big_scale, big_scale] + [int(x) for x in rng.integers(16, 21, size=6)]
-    return [wl.rmat(scale=sc, batch_frac=0.001, seed=seed * 100 + 50 + i)
-            for i, sc in enumerate(scales)]
+    return wl.serving_graphs(seed, big_scale)
 
 
 def serving_requests(ws, count: int, seed: int):
-    """`count` batches: graph uniform over ws, size log-uniform in [1e3, 1e6]
-    (at most half the graph's edges), 50/50 deletions/insertions; a query of
-    1024 random vertices of the same graph after every 4th batch."""
-    rng = np.random.default_rng(seed)
-    reqs = []
-    for i in range(count):
-        gi = int(rng.integers(0, len(ws)))
-        W = ws[gi]
-        size = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
-        size = max(2, min(size, W.m // 2))
-        b = W.stream.next(size // 2, size - size // 2, seed=seed * 100000 + i)
-        q = (rng.integers(0, W.n, size=1024).astype(np.int32) if i % 4 == 3 else None)
-        reqs.append((gi, b, q))
-    return reqs
+    return wl.serving_requests(ws, count, seed)
 
 
 def run_serving(args):

@@ -29,8 +29,14 @@
  *   - A device-side bound being hit (SP_ETIMEOUT) or a distance that does not
  *     fit (SP_ERANGE) during a repair leaves distances unspecified: the graph
  *     is then in SP_ESTATE until sp_sssp_init() is called again.  The edge set
- *     is always consistent with the batches that returned SP_OK, SP_ERANGE or
- *     SP_ETIMEOUT (the CSR merge completes before any repair starts).
+ *     includes every batch that returned SP_OK or SP_ERANGE, and a batch that
+ *     returned SP_ETIMEOUT from its repair (sp_loop_counters site 1-3: the
+ *     CSR merge completes before any repair starts); a batch stopped in its
+ *     sort or count pass (site 4 or 5) did not change the edge set.
+ *   - SP_ENOMEM from a batch (a buffer or the spare pool could not grow)
+ *     leaves the edge set and the distances as they were: distances that the
+ *     invalidation had already changed are recomputed from the last init's
+ *     sources before the call returns (without allocating).
  */
 #ifndef SP_H
 #define SP_H
@@ -182,6 +188,37 @@ sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent,
 sp_status sp_graph_num_edges(const sp_graph *g, int64_t *m);
 
 /*
+ * Install distances and parents exported earlier by sp_get_dist (host
+ * arrays if in_on_device == 0, else device arrays of the graph's device;
+ * n entries each), for `source`, without a recompute -- a checkpoint of the
+ * node properties dist and parent of the problem statement (Section 3.2),
+ * restored after the graph was rebuilt from its edge set.  The pair is
+ * checked on the device first: dist[source] = 0 with parent -1, every other
+ * finite distance realised by a tight parent edge, SP_INF with parent -1
+ * elsewhere, and no edge offering a shorter distance.  Those conditions hold
+ * exactly for the shortest-path distances of the current edge set, so the
+ * restored state equals what sp_sssp_init would compute (parents may differ
+ * where ties allow).  SP_EINVAL (and nothing changed) if any check fails.
+ * The inputs are copied.  On success the graph is in the valid state.
+ */
+sp_status sp_set_dist(sp_graph *g, int32_t source, const int32_t *dist,
+                      const int32_t *parent, int in_on_device);
+
+/*
+ * An upper bound of the device bytes (sp_graph_info.device_bytes) a handle
+ * holds once created from a graph of n vertices and m edges with the given
+ * slack and sized by sp_reserve(max_updates) for batches of up to
+ * max_updates updates given in host memory.  It stays an upper bound until
+ * the graph outgrows its spare pools (rows relocated by insertions) or its
+ * edge count grows far past m.  Computed for the current device.  The
+ * serving runtime admits graphs by it.  SP_EINVAL on out-of-range
+ * arguments.  (No counterpart in the paper: memory accounting for the
+ * resident-graph budget.)
+ */
+sp_status sp_footprint_bound(int32_t n, int64_t m, float slack, int64_t max_updates,
+                             int64_t *bytes);
+
+/*
  * Export the current edge set as a row-sorted CSR: row_off[n+1], col[m],
  * w[m] with m from sp_graph_num_edges.  `reverse` = 1 exports the reverse
  * (transpose) store instead: row v lists the sources u of edges u -> v with
@@ -259,6 +296,25 @@ sp_status sp_set_inval_switch(sp_graph *g, int32_t rounds);
  * bound is clamped to 4096 (the default).  Results do not depend on it.
  */
 sp_status sp_set_local_rounds(sp_graph *g, int32_t max_edges);
+
+/*
+ * Work schedule of the push fixedPoint (the Incremental `fixedPoint` with
+ * `Min` of Section 3.2, whose generated CUDA code runs one thread per vertex
+ * and one launch per iteration).  Results do not depend on it.
+ *   small_deg (0..64, default 8): a frontier vertex with at most small_deg
+ *     out-edges is expanded by one thread; a larger one is cut into 256-edge
+ *     chunks, one warp each, spread over the whole grid (a hub's edges reach
+ *     every SM).  0 chunks every vertex.
+ *   pool_rounds (0..16384, default 0 = off): block-local relaxation.  Every
+ *     thread block keeps the vertices it improved below the near-far
+ *     threshold (those with at most 16 out-edges) in a pool in shared memory
+ *     and expands them itself, in up to pool_rounds sub-rounds ended by block
+ *     barriers, before the round's grid barrier; a shortest-path wave then
+ *     crosses many edges per grid round.  Meant for high-diameter graphs,
+ *     where grid rounds, not relaxations, bound the time.
+ * SP_EINVAL outside these ranges.
+ */
+sp_status sp_set_schedule(sp_graph *g, int32_t small_deg, int32_t pool_rounds);
 
 /*
  * Multi-source form of sp_sssp_init: dist[v] is the shortest distance from
@@ -341,12 +397,20 @@ sp_status sp_set_loop_blocks(sp_graph *g, int32_t blocks);
  * of different graphs run concurrently on n_slots worker slots (one CUDA
  * stream each), so their work overlaps on the device and a request that
  * arrives while others are running starts as soon as a slot is free
- * (continuous batching).  Graphs are admitted by an HBM budget: when a
- * request needs a graph that is not resident, idle resident graphs are
- * evicted least-recently-used (their edge set is checkpointed to host
- * memory) until the graph fits, and the graph is rebuilt from its checkpoint
- * with distances recomputed from its source.  Distances are unique, so a
- * query's answer does not depend on the mix it ran in.
+ * (continuous batching).  Graphs are admitted by an HBM budget, counting
+ * each graph at the upper bound of its footprint (sp_footprint_bound, with
+ * batch buffers reserved for max_batch_updates) or at its measured size if
+ * that is larger (its spare pool grew): when a request needs a graph that
+ * is not resident, idle resident graphs are evicted least-recently-used
+ * (their edge set, distances and parents are checkpointed to host memory)
+ * until the graph fits, and the graph is rebuilt from its checkpoint with
+ * its distances restored by sp_set_dist (checked exact; recomputed from the
+ * source if the check fails).  No request starts while the resident graphs
+ * are over the budget; a request that can fit by no eviction fails with
+ * SP_ENOMEM_BUDGET.  Each graph's cooperative kernels use a share of
+ * SMs/n_slots blocks, each block an SM of its own, so the grids of all slots
+ * are resident at once.  Distances are unique, so a query's answer does not
+ * depend on the mix it ran in.
  * ---------------------------------------------------------------------- */
 typedef struct sp_server sp_server;
 
@@ -356,6 +420,8 @@ typedef struct {
     int32_t loop_blocks;       /* persistent-loop blocks per graph (0: SMs/n_slots) */
     float slack;               /* per-row slack of every graph               */
     int32_t delta;             /* near-far width of every graph (0 = off)    */
+    int64_t max_batch_updates; /* largest batch a request may carry; batch
+                                  buffers are reserved for it (0: 1,048,576) */
 } sp_server_config;
 
 typedef struct {
@@ -366,6 +432,9 @@ typedef struct {
     int64_t updates;           /* deletions + insertions of a batch          */
     double submit_ms, start_ms, done_ms;   /* server clock                   */
     int32_t loaded;            /* 1 if the graph was (re)loaded for it       */
+    double gpu_start_ms, gpu_done_ms;   /* the request's work on the device:
+                                  CUDA events on its graph's stream, ms since
+                                  the server was created (-1: none ran)      */
 } sp_request_info;
 
 typedef struct {
@@ -374,6 +443,8 @@ typedef struct {
     int32_t resident_graphs, registered_graphs;
     int64_t recoveries;        /* batches whose repair hit a device bound and
                                   whose distances were recomputed from the source */
+    int64_t restores;          /* reloads whose distances came from the
+                                  checkpoint (sp_set_dist), not a recompute   */
 } sp_server_stats;
 
 sp_status sp_server_create(const sp_server_config *cfg, sp_server **out);
@@ -383,7 +454,8 @@ sp_status sp_server_destroy(sp_server *s);
 sp_status sp_server_add_graph(sp_server *s, int32_t n, int64_t m, const int64_t *row_off,
                               const int32_t *col, const int32_t *w, int32_t source,
                               int32_t *graph_id);
-/* Submit a batch (host arrays, copied); *request_id identifies it. */
+/* Submit a batch (host arrays, copied); *request_id identifies it.
+ * SP_EINVAL if it carries more than max_batch_updates updates. */
 sp_status sp_server_submit_batch(sp_server *s, int32_t graph_id,
                                  int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
                                  int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
@@ -494,10 +566,25 @@ sp_status sp_set_batch_graphs(sp_graph *g, int32_t on);
  * none, 1 a round or pass cap, 2 a barrier wait), [10] where it was hit (1
  * a loop's round cap, 2 a loop's grid barrier, 3 the wait for a
  * single-block episode, 4 the batch sort's grid barrier, 5 the count pass's
- * grid barrier), [11] the round, barrier index or episode there.  k (<= 12) entries are written; the
- * figures are those of the last synchronous call.
+ * grid barrier), [11] the round, barrier index or episode there, [12]
+ * block-local sub-rounds of the pool schedule (summed over blocks), [13]
+ * entries appended to the block pools, [14] ns block 0 spent in block-local
+ * sub-rounds, [15] block 0's block-local sub-rounds.  k (<= 16) entries
+ * are written; the figures are those of the last synchronous call.
  */
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k);
+
+/*
+ * Test hook of the bounded waits (the failure detection of the repair
+ * loops' termination bound, Section 3.2's fixedPoint run on the device):
+ * from now on thread block 0 does not arrive at the grid barriers of one
+ * wait site -- 2 the repair loops' barrier, 4 the batch sort's, 5 the count
+ * pass's -- so every wait of that barrier runs out after the wait bound of
+ * sp_set_limits and the call returns SP_ETIMEOUT with that site in
+ * sp_loop_counters.  Nothing faults or hangs: each wait is bounded.  0
+ * turns it off.  SP_EINVAL for any other site.
+ */
+sp_status sp_inject_missed_arrival(sp_graph *g, int32_t site);
 
 /* Name of the CUDA error behind the handle's last SP_ECUDA from a failed
  * launch ("cudaSuccess" if none); static storage. */

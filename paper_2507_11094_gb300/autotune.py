@@ -1,11 +1,29 @@
 """Schedule autotuner for the push fixedPoint.
 
-The knob is the near-far bucket width delta (sp_set_push_delta): 0 gives
-plain frontier rounds (few rounds, some redundant relaxations -- right for
-low-diameter graphs), a delta of a few edge weights gives ordered rounds
-(far fewer relaxations, more rounds -- right for high-diameter graphs).
-The tuner times a from-scratch solve on the handle for each candidate and
-keeps the fastest; results are cached per graph signature.
+The paper leaves the work schedule to its backends and to a batch-size knob
+(the `Batch` construct of Section 3.2); its CUDA code runs one thread per
+vertex and one launch per fixedPoint iteration.  Here the schedule has four
+knobs, none of which changes a distance:
+
+- delta (sp_set_push_delta): the near-far bucket width.  0 gives plain
+  frontier rounds (few rounds, redundant relaxations: low-diameter graphs);
+  a width of a few edge weights orders the relaxations (high diameter).
+- pool_rounds (sp_set_schedule): block-local relaxation.  Each thread block
+  expands the vertices it improved itself, in up to pool_rounds sub-rounds
+  with block barriers, before the grid barrier: a high-diameter wave then
+  crosses many edges per grid round.
+- small_deg (sp_set_schedule): the out-degree up to which a frontier vertex
+  is one thread's work; larger vertices are cut into 256-edge chunks, one
+  warp each (thread-per-vertex against warp-per-chunk).
+- local_edges (sp_set_local_rounds): frontier rounds with at most this many
+  edges run in one block, with a block barrier instead of a grid barrier.
+
+The tuner times a from-scratch solve on the handle (sp_sssp_init or the
+multi-source init of the batched form) for each candidate, one knob group at
+a time (coordinate search), keeps the fastest, leaves the handle with it and
+with valid distances, and caches the choice per graph signature.  The
+invalidation switch is not tuned: a from-scratch solve runs no invalidation,
+and the default (pointer jumping at once) is never slower on these graphs.
 """
 from __future__ import annotations
 
@@ -16,6 +34,8 @@ import numpy as np
 
 _cache: dict = {}
 
+DEFAULT = {"delta": 0, "pool_rounds": 0, "small_deg": 8, "local_edges": 4096}
+
 
 def signature(n: int, m: int, w) -> str:
     w = np.asarray(w)
@@ -23,6 +43,7 @@ def signature(n: int, m: int, w) -> str:
 
 
 def candidates(w) -> list[int]:
+    """Near-far widths: off, and 1..64 times the mean weight."""
     w = np.asarray(w)
     if w.size == 0:
         return [0]
@@ -32,21 +53,84 @@ def candidates(w) -> list[int]:
     return sorted({0, mean, 2 * mean, 4 * mean, 16 * mean, 64 * mean})
 
 
-def tune_delta(g, init, w, reps: int = 2, cache_file: str | None = None) -> dict:
-    """Pick delta for handle g.  init(g, stats=True) runs one from-scratch
-    solve (sssp_init or sssp_init_multi) and returns its BatchStats.
-    Returns {"delta": best, "ms": {delta: ms}}; g is left with the best
-    delta set and valid distances."""
+POOL_ROUNDS = (0, 64)
+POOL_REFINE = (16, 256)
+SMALL_DEG = (0, 8, 32)
+LOCAL_EDGES = (0, 1024, 4096)
+
+
+def apply_schedule(g, s: dict):
+    g.set_delta(int(s["delta"]))
+    g.set_schedule(int(s["small_deg"]), int(s["pool_rounds"]))
+    g.set_local_rounds(int(s["local_edges"]))
+
+
+def _key(s: dict) -> str:
+    return (f"delta={s['delta']},pool={s['pool_rounds']},small={s['small_deg']},"
+            f"local={s['local_edges']}")
+
+
+def tune_schedule(g, init, w, reps: int = 2, cache_file: str | None = None) -> dict:
+    """Pick the push schedule for handle g.  init(g, stats=True) runs one
+    from-scratch solve (sssp_init or sssp_init_multi) and returns its
+    BatchStats.  Returns {"schedule": {...}, "ms": {candidate: ms}}; g is
+    left with the best schedule set and valid distances."""
     sig = signature(g.n, g.m, w)
     if cache_file and os.path.exists(cache_file):
         with open(cache_file) as f:
             _cache.update(json.load(f))
+    if sig in _cache and "schedule" in _cache[sig]:
+        apply_schedule(g, _cache[sig]["schedule"])
+        init(g)
+        return _cache[sig]
+    timings: dict = {}
+
+    def timed(s: dict) -> float:
+        k = _key(s)
+        if k not in timings:
+            apply_schedule(g, s)
+            best = None
+            for _ in range(reps):
+                st = init(g, stats=True)
+                best = st.ms_total if best is None else min(best, st.ms_total)
+            timings[k] = best
+        return timings[k]
+
+    apply_schedule(g, DEFAULT)
+    init(g)   # untimed: the first solve of a handle pays one-time costs
+    best = dict(DEFAULT)
+    # 1. near-far width together with the block-local pools (they interact:
+    #    a pool sub-round relaxes below the threshold only)
+    grid = [dict(DEFAULT, delta=d, pool_rounds=p, local_edges=0 if p else 4096)
+            for d in candidates(w) for p in POOL_ROUNDS]
+    best = min(grid, key=timed)
+    # 2. the pool budget around the winner
+    if best["pool_rounds"]:
+        best = min([best] + [dict(best, pool_rounds=p) for p in POOL_REFINE], key=timed)
+    # 3. thread-per-vertex bound
+    best = min([dict(best, small_deg=s) for s in SMALL_DEG], key=timed)
+    # 4. single-block rounds
+    best = min([dict(best, local_edges=e) for e in LOCAL_EDGES], key=timed)
+    apply_schedule(g, best)
+    init(g)
+    res = {"schedule": best, "delta": int(best["delta"]),
+           "ms": {k: float(v) for k, v in timings.items()}}
+    _cache[sig] = res
+    if cache_file:
+        with open(cache_file, "w") as f:
+            json.dump(_cache, f, indent=1)
+    return res
+
+
+def tune_delta(g, init, w, reps: int = 2, cache_file: str | None = None) -> dict:
+    """The near-far width alone (the other knobs at their defaults)."""
+    sig = "delta-" + signature(g.n, g.m, w)
     if sig in _cache:
         g.set_delta(_cache[sig]["delta"])
         init(g)
         return _cache[sig]
     timings = {}
-    init(g)   # untimed: the first solve of a handle pays one-time costs
+    init(g)
     for d in candidates(w):
         g.set_delta(d)
         best = None
@@ -59,7 +143,4 @@ def tune_delta(g, init, w, reps: int = 2, cache_file: str | None = None) -> dict
     init(g)
     res = {"delta": int(delta), "ms": {str(k): float(v) for k, v in timings.items()}}
     _cache[sig] = res
-    if cache_file:
-        with open(cache_file, "w") as f:
-            json.dump(_cache, f, indent=1)
     return res

@@ -6,6 +6,7 @@
 // backend instead copies a `finished` flag to the host every fixedPoint
 // iteration, Section 5.3).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -51,58 +52,78 @@ namespace {
 constexpr long long kMaxEdges = (1LL << 31) - 1;
 
 // Buffers sized by the batch: grown (never shrunk) when a larger batch comes.
+// Grow the per-call buffers to ni items (and nb_host staged host inputs).
+// New buffers are allocated before the old ones are released, so a failed
+// allocation (SP_ENOMEM) leaves every buffer as it was.
 sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
   sp::BatchBufs &b = g->bb;
+  auto &al = g->al;
   const long long want = std::max<long long>(ni + 1, 1024);
   if (want > b.cap_items) {
-    long long c = std::max(want, b.cap_items * 2);
-    auto &al = g->al;
-    long long old = b.cap_items;
+    const long long c = std::max(want, b.cap_items * 2);
+    const size_t tmp_bytes = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
+                                       sp::batch_sort_tmp_bytes(g->sort_blocks)}) + 1024;
+    void *p[9];
+    const size_t sz[9] = {(size_t)c * 8, (size_t)c * 8, (size_t)c * 4, (size_t)c * 4, (size_t)c,
+                          (size_t)c * 8, (size_t)c * 4, (size_t)c * sizeof(sp::Seg), tmp_bytes};
+    bool ok = true;
+    for (int i = 0; i < 9; ++i) {
+      p[i] = ok ? al.get(sz[i]) : nullptr;
+      ok = ok && p[i];
+    }
+    if (!ok) {
+      for (int i = 0; i < 9; ++i) al.put(p[i], sz[i]);
+      return SP_ENOMEM;
+    }
+    const long long old = b.cap_items;
     al.put(b.keys, old * 8); al.put(b.keys_alt, old * 8);
     al.put(b.vals, old * 4); al.put(b.vals_alt, old * 4);
     al.put(b.flags, old); al.put(b.item_pref, old * 8);
     al.put(b.opos, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
     al.put(b.tmp, b.tmp_bytes);
-    b.keys = (u64 *)al.get(c * 8); b.keys_alt = (u64 *)al.get(c * 8);
-    b.vals = (u32 *)al.get(c * 4); b.vals_alt = (u32 *)al.get(c * 4);
-    b.flags = (unsigned char *)al.get(c);
-    b.item_pref = (u64 *)al.get(c * 8);
-    b.opos = (u32 *)al.get(c * 4);
-    b.seg = (sp::Seg *)al.get(c * sizeof(sp::Seg));
-    b.tmp_bytes = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
-                            sp::batch_sort_tmp_bytes(g->sort_blocks)}) + 1024;
-    b.tmp = al.get(b.tmp_bytes);
+    b.keys = (u64 *)p[0]; b.keys_alt = (u64 *)p[1];
+    b.vals = (u32 *)p[2]; b.vals_alt = (u32 *)p[3];
+    b.flags = (unsigned char *)p[4];
+    b.item_pref = (u64 *)p[5];
+    b.opos = (u32 *)p[6];
+    b.seg = (sp::Seg *)p[7];
+    b.tmp = p[8];
+    b.tmp_bytes = tmp_bytes;
     b.cap_items = c;
     ++g->gen;
-    if (!b.keys || !b.keys_alt || !b.vals || !b.vals_alt || !b.flags ||
-        !b.item_pref || !b.opos || !b.seg || !b.tmp) {
-      return SP_ENOMEM;
-    }
   }
   if (nb_host > b.cap_in) {
-    long long c = std::max(nb_host, b.cap_in * 2);
-    long long old = b.cap_in;
-    auto &al = g->al;
+    const long long c = std::max(nb_host, b.cap_in * 2);
+    int *p[5];
+    bool ok = true;
+    for (int i = 0; i < 5; ++i) {
+      p[i] = ok ? (int *)al.get((size_t)c * 4) : nullptr;
+      ok = ok && p[i];
+    }
+    if (!ok) {
+      for (int i = 0; i < 5; ++i) al.put(p[i], (size_t)c * 4);
+      return SP_ENOMEM;
+    }
+    const long long old = b.cap_in;
     al.put(b.in_del_src, old * 4); al.put(b.in_del_dst, old * 4);
     al.put(b.in_add_src, old * 4); al.put(b.in_add_dst, old * 4); al.put(b.in_add_w, old * 4);
-    b.in_del_src = (int *)al.get(c * 4); b.in_del_dst = (int *)al.get(c * 4);
-    b.in_add_src = (int *)al.get(c * 4); b.in_add_dst = (int *)al.get(c * 4);
-    b.in_add_w = (int *)al.get(c * 4);
+    b.in_del_src = p[0]; b.in_del_dst = p[1];
+    b.in_add_src = p[2]; b.in_add_dst = p[3];
+    b.in_add_w = p[4];
     b.cap_in = c;
     ++g->gen;
-    if (!b.in_del_src || !b.in_del_dst || !b.in_add_src || !b.in_add_dst || !b.in_add_w)
-      return SP_ENOMEM;
   }
   // merge strips: at most (old entries of touched rows) / 256 + one per row
   const long long sneed = (2 * g->m) / 256 + ni + 64;
   if (sneed > b.strips_cap) {
     const long long c = std::max(sneed, 2 * b.strips_cap);
-    g->al.put(b.strips, (size_t)b.strips_cap * 8);
-    b.strips = (int2 *)g->al.get((size_t)c * 8);
-    b.strips_cap = b.strips ? c : 0;
+    int2 *ns = (int2 *)al.get((size_t)c * 8);
+    if (!ns) return SP_ENOMEM;
+    al.put(b.strips, (size_t)b.strips_cap * 8);
+    b.strips = ns;
+    b.strips_cap = c;
     ++g->gen;
-    if (!b.strips) return SP_ENOMEM;
   }
   return SP_OK;
 }
@@ -236,6 +257,9 @@ void set_limits(sp_graph *g) {
   g->lim.delta = (u32)std::max(0, g->delta_user);
   g->lim.jump_round = g->jump_round_user;
   g->lim.local_edges = (u32)g->local_edges_user;
+  g->lim.small_deg = (u32)g->small_deg_user;
+  g->lim.pool_rounds = (u32)g->pool_rounds_user;
+  g->lim.miss_site = (u32)g->miss_site_user;
   ++g->gen;
 }
 
@@ -281,7 +305,12 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
   rec(g, timed, 1);
   const bool beside = mode == kInvalBeside && n_del > 0;
   g->last_beside = beside && timed;
-  if (beside) {   // fork: the side stream starts once the batch is validated
+  sp::launch_count(g, ni, launches);
+  rec(g, timed, 2);
+  // fork: the invalidation runs beside the merge.  Not beside the count: two
+  // cooperative grids with grid barriers, side by side, could each hold SMs
+  // the other waits for; the merge has no grid barrier
+  if (beside) {
     cudaEventRecord(g->fork_ev, g->stream);
     cudaStreamWaitEvent(g->side, g->fork_ev, 0);
     rec_side(g, timed, 0);
@@ -290,8 +319,6 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
     rec_side(g, timed, 1);
     cudaEventRecord(g->join_ev, g->side);
   }
-  sp::launch_count(g, ni, launches);
-  rec(g, timed, 2);
   sp::launch_merge(g, ni, launches);
   rec(g, timed, 3);
   if (beside) cudaStreamWaitEvent(g->stream, g->join_ev, 0);   // join
@@ -307,6 +334,31 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
   rec(g, timed, 8);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
+}
+
+// A batch that stops before its merge (the store could not grow) leaves the
+// edge set as it was.  If its invalidation already ran beside the store
+// update (touched), the distances are recomputed from the sources of the
+// last init, which allocates nothing; if that fails too the handle needs
+// sp_sssp_init (SP_ESTATE).  Returns rc, the batch's own status.
+sp_status restore_after(sp_graph *g, bool touched, sp_status rc) {
+  if (!touched) return rc;
+  int launches = 0;
+  sp::launch_ctl_reset(g, 0, &launches);
+  if (g->n_src == 1 && g->source >= 0) sp::launch_init(g, g->source, &launches);
+  else if (g->n_src > 1 && g->src_dev) sp::launch_init_multi(g, g->src_dev, g->n_src, &launches);
+  else {
+    g->state = 2;
+    return rc;
+  }
+  cudaError_t e = sp::launch_push(g, &launches);
+  sp::launch_finish(g, &launches);
+  if (e != cudaSuccess || read_ctl(g, true) != SP_OK ||
+      status_of_repair(g, *g->ctl_host) != SP_OK) {
+    cudaGetLastError();
+    g->state = 2;
+  }
+  return rc;
 }
 
 // Buffers big enough for an asynchronous batch of ni items?
@@ -384,6 +436,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(g->prc[0], n * 4); al.put(g->prc[1], n * 4);
   al.put(g->pracc, n * 4); al.put(g->prflag, n * 4);
   al.put(g->ctl, sizeof(Ctl));
+  if (g->src_dev) al.put(g->src_dev, (size_t)g->n_src * 4);
   drop_batch_graphs(g);
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   for (auto &e : g->ev)
@@ -429,10 +482,11 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   g->loop_blocks_push = sp::loop_blocks(0, g->num_sms);
   g->loop_blocks_inval = sp::loop_blocks(1, g->num_sms);
+  g->loop_blocks_pool = sp::loop_blocks(3, g->num_sms);
   g->sort_blocks = sp::batch_sort_blocks(g->num_sms);
   g->count_blocks = sp::count_blocks(g->num_sms);
-  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 || g->sort_blocks <= 0 ||
-      g->count_blocks <= 0) {
+  if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 ||
+      g->loop_blocks_pool <= 0 || g->sort_blocks <= 0 || g->count_blocks <= 0) {
     delete g;
     return SP_ECUDA;
   }
@@ -549,12 +603,13 @@ sp_status sp_set_push_delta(sp_graph *g, int32_t delta) {
 }
 
 sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k) {
-  if (!g || !out || k < 0 || k > 12) return SP_EINVAL;
+  if (!g || !out || k < 0 || k > 16) return SP_EINVAL;
   const Ctl &c = *g->ctl_host;
-  const int64_t v[12] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
+  const int64_t v[16] = {c.rounds_push, c.local_rounds, c.local_episodes, c.splits,
                          (int64_t)c.far_moves, c.rounds_inval, c.jumps,
                          (int64_t)c.local_ns, (int64_t)c.push_ns, c.timeout,
-                         c.to_site, c.to_info};
+                         c.to_site, c.to_info, (int64_t)c.pool_sub, (int64_t)c.pool_in,
+                         (int64_t)c.pool_ns, (int64_t)c.pool_sub0};
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return SP_OK;
 }
@@ -562,6 +617,22 @@ sp_status sp_loop_counters(const sp_graph *g, int64_t *out, int32_t k) {
 sp_status sp_set_local_rounds(sp_graph *g, int32_t max_edges) {
   if (!g || max_edges < 0) return SP_EINVAL;
   g->local_edges_user = std::min<int32_t>(max_edges, (int32_t)sp::kLocalRoundCap);
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_set_schedule(sp_graph *g, int32_t small_deg, int32_t pool_rounds) {
+  if (!g || small_deg < 0 || small_deg > 64 || pool_rounds < 0 || pool_rounds > 16384)
+    return SP_EINVAL;
+  g->small_deg_user = small_deg;
+  g->pool_rounds_user = pool_rounds;
+  set_limits(g);
+  return SP_OK;
+}
+
+sp_status sp_inject_missed_arrival(sp_graph *g, int32_t site) {
+  if (!g || !(site == 0 || site == 2 || site == 4 || site == 5)) return SP_EINVAL;
+  g->miss_site_user = site;
   set_limits(g);
   return SP_OK;
 }
@@ -606,12 +677,11 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats) {
     stats->alg_bytes[SP_PH_PUSH] += (int64_t)g->n * 8;  // the reset of all states
   }
   rc = status_of_repair(g, c);
-  if (rc == SP_OK) {
-    g->state = 1;
-    g->source = source;
-  } else {
-    g->source = source;
-  }
+  g->source = source;
+  if (g->src_dev) g->al.put(g->src_dev, (size_t)g->n_src * 4);
+  g->src_dev = nullptr;
+  g->n_src = 1;
+  if (rc == SP_OK) g->state = 1;
   return rc;
 }
 
@@ -722,24 +792,30 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
       return rc;
     }
     const Ctl &c = *g->ctl_host;
-    if (c.status != 0) return (sp_status)c.status;   // nothing changed
-    if (c.need_grow == 0) break;
-    if (attempt >= 6) {
-      g->state = 2;
-      return SP_ENOMEM;
+    // the edge set is as it was: the merge did not run.  A bound hit in the
+    // batch sort or the count pass (SP_ETIMEOUT) may have let the
+    // invalidation beside them change distances, which then need sp_sssp_init
+    if (c.status != 0) {
+      if (c.status == SP_ETIMEOUT) g->state = 2;
+      return (sp_status)c.status;
     }
+    if (c.need_grow == 0) break;
+    // the merge did not run either; a shortfall that cannot be grown leaves
+    // the edge set as it was and the distances are restored
+    const bool touched = mode0 == kInvalBeside && n_del > 0;
+    if (attempt >= 6) return restore_after(g, touched, SP_ENOMEM);
     ++regrows;
     if (c.need_grow & sp::kGrowPoolFwd) {
       rc = sp::store_grow_pool(g, &g->fwd, (long long)c.pool_need[0] + 1024);
-      if (rc != SP_OK) return rc;
+      if (rc != SP_OK) return restore_after(g, touched, rc);
     }
     if (c.need_grow & sp::kGrowPoolRev) {
       rc = sp::store_grow_pool(g, &g->rev, (long long)c.pool_need[1] + 1024);
-      if (rc != SP_OK) return rc;
+      if (rc != SP_OK) return restore_after(g, touched, rc);
     }
     if (c.need_grow & (sp::kGrowPoolFwd | sp::kGrowPoolRev)) {
       rc = sp::ensure_owner_tables(g);
-      if (rc != SP_OK) return rc;
+      if (rc != SP_OK) return restore_after(g, touched, rc);
     }
 
   }
@@ -780,7 +856,10 @@ sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
   sp::launch_finish(g, &launches);
   rec(g, timed, SP_NPHASE);
   sp_status rc = read_ctl(g, true);
-  g->al.put(src_d, (size_t)k * 4);
+  // the list stays with the handle (a failed batch restores from it)
+  if (g->src_dev) g->al.put(g->src_dev, (size_t)g->n_src * 4);
+  g->src_dev = src_d;
+  g->n_src = k;
   if (e != cudaSuccess) {
     g->last_err = (int)e;
     cudaGetLastError();
@@ -835,7 +914,10 @@ sp_status sp_apply_batch_async(sp_graph *g, int64_t n_del, const int32_t *del_sr
 sp_status sp_apply_batch_finish(sp_graph *g, const void *result_host, sp_batch_stats *stats) {
   if (!g || !result_host) return SP_EINVAL;
   const Ctl &c = *(const Ctl *)result_host;
-  if (c.status != 0) return (sp_status)c.status;   // nothing changed
+  if (c.status != 0) {   // the edge set did not change
+    if (c.status == SP_ETIMEOUT) g->state = 2;
+    return (sp_status)c.status;
+  }
   if (c.need_grow) return SP_ENOMEM;               // nothing changed: use sp_apply_batch
   g->m += (long long)c.add_applied - (long long)c.del_applied;
   fill_stats(g, c, stats, g->async_launches, 0, g->async_ni, false);
@@ -1326,6 +1408,68 @@ sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_de
     cudaGetLastError();
     return SP_ECUDA;
   }
+  return SP_OK;
+}
+
+sp_status sp_set_dist(sp_graph *g, int32_t source, const int32_t *dist, const int32_t *parent,
+                      int in_on_device) {
+  if (!g || !dist || !parent || source < 0 || source >= g->n) return SP_EINVAL;
+  const int *dd = dist, *pd = parent;
+  if (!in_on_device) {   // staged in the unpack buffers
+    cudaMemcpyAsync(g->out_dist, dist, (size_t)g->n * 4, cudaMemcpyHostToDevice, g->stream);
+    cudaMemcpyAsync(g->out_parent, parent, (size_t)g->n * 4, cudaMemcpyHostToDevice, g->stream);
+    dd = g->out_dist;
+    pd = g->out_parent;
+  }
+  int launches = 0;
+  sp::launch_ctl_reset(g, 0, &launches);
+  sp::launch_state_check(g, dd, pd, source, &launches);
+  sp_status rc = read_ctl(g);
+  if (rc != SP_OK) return rc;
+  if (g->ctl_host->status != 0) return SP_EINVAL;   // not the exact solution: nothing changed
+  sp::launch_state_pack(g, dd, pd, &launches);
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    g->state = 2;
+    return SP_ECUDA;
+  }
+  g->source = source;
+  if (g->src_dev) g->al.put(g->src_dev, (size_t)g->n_src * 4);
+  g->src_dev = nullptr;
+  g->n_src = 1;
+  g->state = 1;
+  return SP_OK;
+}
+
+sp_status sp_footprint_bound(int32_t n, int64_t m, float slack, int64_t max_updates,
+                             int64_t *bytes) {
+  if (!bytes || n <= 0 || m < 0 || m > kMaxEdges || !(slack >= 0.f) || slack > 16.f ||
+      max_updates < 0 || max_updates > (1LL << 30))
+    return SP_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ECUDA;
+  }
+  const double N = (double)n, M = (double)m;
+  // a row of deg edges gets round4(deg + max(slack * deg, 4)) <= (1 + slack) deg + 8
+  // slots per region (the float product rounded up), two regions per row
+  const double main_slots = 2.0 * ((1.0 + (double)slack * (1.0 + 1e-6)) * M + 9.0 * N);
+  const double pool = std::max(main_slots / 4.0 + 4.0, 65536.0);
+  const double slots = main_slots + pool;
+  double b = 0;
+  b += (double)sizeof(Ctl) + 92.0 * N;                   // state, queues, lists, tags
+  b += 2.0 * (24.0 * N + 8.0 * slots);                   // two stores: row, alt, adj
+  b += 16.0 * (slots / sp::kChunk + 64.0);               // chunk-owner tables
+  const long long c = std::max<long long>(2 * max_updates + 1, 1024);
+  const int sblocks = sp::batch_sort_blocks(sms);
+  const size_t tmp = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
+                               sp::batch_sort_tmp_bytes(sblocks)}) + 1024;
+  b += (double)c * (8 + 8 + 4 + 4 + 1 + 8 + 4 + sizeof(sp::Seg)) + (double)tmp;
+  b += 8.0 * (2.0 * M / 256.0 + 2.0 * (double)max_updates + 64.0);   // merge strips
+  b += 20.0 * (double)max_updates;                       // staged host inputs
+  *bytes = (int64_t)std::ceil(b) + 64 * 256;             // allocation slack
   return SP_OK;
 }
 

@@ -31,12 +31,15 @@ namespace sp {
 
 namespace {
 
-constexpr int kOpPush = 0, kOpInval = 1, kOpFlag = 2;
+// kOpPool: the push fixedPoint with block-local relaxation (pool schedule)
+constexpr int kOpPush = 0, kOpInval = 1, kOpFlag = 2, kOpPool = 3;
 constexpr int K = kEdgesPerLane;
 // block stages of the persistent loops (dynamic shared memory)
 constexpr u32 kStageQ = 4096, kStageQS = 12288, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
 constexpr size_t kLoopSmem =
     (2 * kStageQ + kStageQS + 2 * kStageA + kStageAS + kStageF) * sizeof(u32);
+// the pool schedule's two entry lists follow the stages
+constexpr size_t kLoopSmemPool = kLoopSmem + 2 * kPoolCap * sizeof(uint4);
 constexpr u32 kStageK = 1024;    // stages of the one-pass kernels (static)
 constexpr u32 kNoEdge = 0xFFFFFFFFu;
 constexpr u32 kFull = 0xffffffffu;
@@ -89,13 +92,16 @@ __device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Li
     // the count before this arrival says whether it was the last one; the
     // wait polls the count alone and looks at the timeout flag and the
     // clock every 16th poll
-    if (atomicAdd((unsigned long long *)bar, 1ull) + 1 < target) {
+    // (the test hook lim.miss_site == 2: block 0 does not arrive)
+    const bool miss = lim.miss_site == 2u && blockIdx.x == 0;
+    const u64 arrived = miss ? ld_acquire_u64(bar) : atomicAdd((unsigned long long *)bar, 1ull) + 1;
+    if (arrived < target) {
       const u64 t0 = globaltimer_ns();
       u32 polls = 0;
       while (ld_acquire_u64(bar) < target) {
         if ((++polls & 15u) == 0) {
           if (ld_cg_i32(&c->timeout) != 0) break;
-          if (globaltimer_ns() - t0 > lim.wait_ns) {
+          if (globaltimer_ns() - t0 > lim.wait_ns || polls > kMaxPolls) {
             raise_timeout(c, 2, 2, (u32)(target / gridDim.x));
             break;
           }
@@ -148,7 +154,7 @@ __device__ __forceinline__ bool stage_reserve(Stage *st, u32 cnt, u32 &pos) {
 }
 
 // Append up to K vertices per lane to queue q (warp-collective).  A vertex
-// with 1..kSmallDeg edges goes to the small list; a larger one reserves deg
+// with 1..q.small edges goes to the small list; a larger one reserves deg
 // slots of the queue's edge space, and the chunk-owner table gets its slot
 // for every chunk whose first edge falls in that range.  With block stages
 // the vertices wait there and are published when the block flushes.
@@ -160,7 +166,7 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     d[k] = (k < kk && want[k]) ? __ldg(&row[x[k]].deg) : 0;
-    if (d[k] > kSmallDeg) {
+    if (d[k] > (int)q.small) {
       ++cnt;
       sum += (u32)d[k];
     } else if (d[k] > 0) {
@@ -186,7 +192,7 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
     u32 p = __shfl_sync(kFull, pos, 0) + si - scount;
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (d[k] > 0 && d[k] <= kSmallDeg) dst[p++] = x[k];
+      if (d[k] > 0 && d[k] <= (int)q.small) dst[p++] = x[k];
   }
   if (!any) return;
   const u32 ci = warp_incl_scan(cnt), si = warp_incl_scan(sum);
@@ -199,7 +205,7 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
       u32 p = __shfl_sync(kFull, pos, 0) + ci - cnt;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        if (d[k] > kSmallDeg) {
+        if (d[k] > (int)q.small) {
           q.st->v[p] = x[k];
           q.st->d[p] = (u32)d[k];
           ++p;
@@ -215,7 +221,7 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
   u32 eb = (u32)base + si - sum;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (d[k] > kSmallDeg) {
+    if (d[k] > (int)q.small) {
       q.ent[slot] = make_int2((int)x[k], (int)eb);
       const u32 c0 = (eb + kChunk - 1) / kChunk, c1 = (eb + (u32)d[k] - 1) / kChunk;
       for (u32 ch = c0; ch <= c1; ++ch) q.owner[ch] = slot;
@@ -378,6 +384,246 @@ __device__ __forceinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *f
   flush_stages(nullptr, nullptr, st, pile, cnt, far_min, scratch);
 }
 
+// --- block-local relaxation (pool schedule of the push loop) ----------------
+//
+// On a high-diameter graph a push round advances the frontier by one edge,
+// and a grid barrier per edge of the deepest shortest path costs more than
+// the relaxations.  With the pool schedule every block keeps the vertices it
+// improved below the near threshold in a pool in shared memory and expands
+// them itself, in sub-rounds ended by block barriers, before it meets the
+// other blocks at the grid barrier.  A wave then crosses many edges per grid
+// round.  Blocks relax any vertex, not a partition of their own: two blocks
+// that reach one vertex race through the packed atomicMin, and only the
+// winner's entry survives.  Correctness rests on the same invariant as the
+// frontier rounds: every vertex improved below the threshold is expanded
+// with its final distance, here from the pool of the block that improved it
+// last, or from the global frontier when its degree or a full pool sends it
+// there.
+
+constexpr u32 kPoolUnknown = 0xFFFFFFFFu;   // entry degree not read yet
+constexpr int kPU = 4;                       // pool edges per lane and step
+
+// Fetch a line toward L2 without waiting for it: a pool entry's next use is
+// one sub-round later, by then its row is on chip.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Append each lane's improved near targets to pool list b (warp-collective).
+// A target with 1..kPoolDeg out-edges becomes an entry (x, nd, start / 4,
+// deg); with kMeta false the row is not known yet and the entry carries
+// kPoolUnknown instead (the drain reads it).  A target without out-edges
+// needs nothing; a larger one, or one that finds the list full, comes back
+// in rest[] for the global frontier.
+template <bool kMeta>
+__device__ __forceinline__ void pool_push(Pool *pl, u32 b, const u32 *x, const u32 *nd,
+                                          const bool *want, int kk, const long long *mst,
+                                          const int *mdg, bool *rest, u64 &n_in,
+                                          const RowMeta *row, const int2 *adj) {
+  const int lane = threadIdx.x & 31;
+  bool take[K];
+  u32 cnt = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    rest[k] = false;
+    take[k] = false;
+    if (k < kk && want[k]) {
+      if (!kMeta || (mdg[k] > 0 && mdg[k] <= kPoolDeg)) {
+        take[k] = true;
+        ++cnt;
+      } else if (mdg[k] > kPoolDeg) {
+        rest[k] = true;
+      }
+    }
+  }
+  if (!__ballot_sync(kFull, cnt > 0)) return;
+  const u32 ci = warp_incl_scan(cnt), tot = __shfl_sync(kFull, ci, 31);
+  u32 base = 0;
+  if (lane == 31) base = atomicAdd(&pl->n[b], tot);
+  base = __shfl_sync(kFull, base, 31) + ci - cnt;
+  uint4 *E = pl->e[b];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (take[k]) {
+      if (base < kPoolCap) {
+        E[base] = kMeta ? make_uint4(x[k], nd[k], (u32)(mst[k] >> 2), (u32)mdg[k])
+                        : make_uint4(x[k], nd[k], 0u, kPoolUnknown);
+        // what the entry's expansion reads first: its edges (or its row)
+        if (kMeta) {
+          prefetch_l2(adj + mst[k]);
+          prefetch_l2(adj + mst[k] + mdg[k] - 1);
+        } else {
+          prefetch_l2(row + x[k]);
+        }
+        ++n_in;
+      } else {
+        rest[k] = true;
+      }
+      ++base;
+    }
+  }
+}
+
+struct PoolCounters {
+  u64 n_edges = 0, n_imp = 0, n_enq = 0, n_in = 0, ns = 0;
+  u32 subs = 0;
+  int range_err = 0;
+};
+
+// Sub-rounds over the block's pool (block-collective, every thread of the
+// block), starting from list 0, until the pool is empty or lim.pool_rounds
+// sub-rounds have run; then the entries left go to the global frontier qn.
+// An entry whose vertex holds a smaller distance by now is skipped (the
+// improvement that lowered it appended its own entry).  Each lane expands
+// one entry, kPU edges per step, with every edge's load, packed atomicMin and
+// (speculative) read of the target's row in flight together, so that a
+// target it improves enters the other list with its row already known.
+// Improved targets at or above thresh go to the far pile (pile != nullptr).
+__device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thresh, u32 tag,
+                                           u32 phase, const Queue &qn, u32 *pile, u32 *pcnt,
+                                           u32 *pmin, Stage *sf, PoolCounters &pc) {
+  const int lane = threadIdx.x & 31;
+  const u32 bs = blockDim.x;
+  const RowMeta *row = a.fwd.row;
+  const u64 t_in = globaltimer_ns();
+  u32 p = 0, sub = 0;
+  for (;;) {
+    __syncthreads();
+    const u32 nraw = *(volatile u32 *)&pl->n[p];
+    const u32 n = nraw < kPoolCap ? nraw : kPoolCap;
+    if (n == 0 || sub >= a.lim.pool_rounds) break;   // block-uniform
+    const u32 q = p ^ 1;
+    const uint4 *E = pl->e[p];
+    for (u32 base = threadIdx.x & ~31u; base < n; base += bs) {
+      const u32 i = base + lane;
+      uint4 en = make_uint4(0u, 0u, 0u, 0u);
+      if (i < n) en = E[i];
+      const u32 v = en.x, d = en.y;
+      u32 deg = en.w;
+      long long start = (long long)en.z << 2;
+      u64 sv = 0ull;
+      if (deg == kPoolUnknown) {     // appended by the round's frontier expansion
+        const int4 r = __ldg((const int4 *)(row + v));
+        sv = ld_cg_u64(a.s + v);
+        start = (long long)(((u64)(u32)r.y << 32) | (u32)r.x);
+        deg = (u32)r.z;
+      } else if (deg) {
+        sv = ld_cg_u64(a.s + v);
+      }
+      // the first step's edges load together with the state word, before
+      // anything waits for either
+      int2 ed0[kPU];
+#pragma unroll
+      for (int k = 0; k < kPU; ++k)
+        ed0[k] = (u32)k < deg && deg <= (u32)kPoolDeg ? __ldg(a.fwd.adj + start + k)
+                                                       : make_int2(0, 0);
+      // a vertex with more out-edges than a lane takes goes to the frontier
+      bool big[K] = {};
+      u32 bx[K] = {};
+      big[0] = deg > (u32)kPoolDeg && dist_of(sv) == d;
+      bx[0] = v;
+      if (big[0]) big[0] = atomicExch(a.qflag + v, tag) != tag;
+      enqueue(qn, row, bx, big, 1, pc.n_enq);
+      if (deg > (u32)kPoolDeg) deg = 0;
+      u32 steps = (deg + kPU - 1) / kPU;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const u32 y = __shfl_xor_sync(kFull, steps, o);
+        steps = y > steps ? y : steps;
+      }
+      bool live = false;
+      for (u32 t = 0; t < steps; ++t) {
+        int2 ed[kPU];
+#pragma unroll
+        for (int k = 0; k < kPU; ++k) {
+          const u32 e = t * kPU + (u32)k;
+          ed[k] = t == 0 ? ed0[k] : (e < deg ? __ldg(a.fwd.adj + start + e) : make_int2(0, 0));
+        }
+        if (t == 0) live = deg > 0 && dist_of(sv) == d;
+        u32 tx[K], nd[K];
+        u64 cand[kPU], old[kPU];
+        long long mst[K];
+        int mdg[K];
+        bool act[kPU];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          tx[k] = 0;
+          nd[k] = kInf;
+          mst[k] = 0;
+          mdg[k] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kPU; ++k) {
+          act[k] = live && t * kPU + (u32)k < deg;
+          tx[k] = (u32)ed[k].x;
+          nd[k] = d + (u32)ed[k].y;
+          if (act[k]) {
+            ++pc.n_edges;
+            if (nd[k] >= kInf) {
+              pc.range_err = 1;
+              act[k] = false;
+            }
+          }
+          cand[k] = pack(nd[k], v);
+          old[k] = act[k] ? atomicMin((unsigned long long *)(a.s + tx[k]), cand[k]) : 0ull;
+          if (act[k]) {
+            const int4 r = __ldg((const int4 *)(row + tx[k]));
+            mst[k] = (long long)(((u64)(u32)r.y << 32) | (u32)r.x);
+            mdg[k] = r.z;
+          }
+        }
+        bool near[K], far[K];
+        u32 fmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < K; ++k) near[k] = far[k] = false;
+#pragma unroll
+        for (int k = 0; k < kPU; ++k) {
+          if (act[k] && cand[k] < old[k]) {
+            ++pc.n_imp;
+            if (nd[k] < thresh) {
+              near[k] = true;
+            } else if (pile) {
+              far[k] = atomicExch(a.ftag + tx[k], phase) != phase;
+              if (far[k] && nd[k] < fmin) fmin = nd[k];
+            }
+          }
+        }
+        bool rest[K], want[K];
+        pool_push<true>(pl, q, tx, nd, near, kPU, mst, mdg, rest, pc.n_in, row, a.fwd.adj);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          want[k] = k < kPU && rest[k] && atomicExch(a.qflag + tx[k], tag) != tag;
+        enqueue(qn, row, tx, want, kPU, pc.n_enq);
+        if (pile) far_append(pile, pcnt, pmin, sf, tx, far, kPU, fmin);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pl->n[p] = 0u;
+    p = q;
+    ++sub;
+  }
+  pc.subs += sub;
+  if (sub) pc.ns += globaltimer_ns() - t_in;
+  // entries left when the budget ran out: to the global frontier
+  {
+    const u32 nraw = *(volatile u32 *)&pl->n[p];
+    const u32 n = nraw < kPoolCap ? nraw : kPoolCap;
+    const uint4 *E = pl->e[p];
+    for (u32 base = threadIdx.x & ~31u; base < n; base += bs) {
+      const u32 i = base + lane;
+      bool want[K] = {};
+      u32 x[K] = {};
+      if (i < n) {
+        x[0] = E[i].x;
+        want[0] = atomicExch(a.qflag + x[0], tag) != tag;
+      }
+      enqueue(qn, row, x, want, 1, pc.n_enq);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) pl->n[0] = pl->n[1] = 0u;
+}
+
 // --- edge operations ------------------------------------------------------
 //
 // Each op provides vdata(v) (a per-source datum read once per queue entry),
@@ -398,7 +644,8 @@ struct PushOp {
   u32 *pile, *pcnt, *far_min, *ftag;
   u32 phase;
   Stage *fst;
-  u64 n_edges = 0, n_imp = 0, n_enq = 0;
+  Pool *pool;              // pool schedule: near improvements go to list 0
+  u64 n_edges = 0, n_imp = 0, n_enq = 0, n_in = 0;
   int range_err = 0;
 
   __device__ __forceinline__ u32 vdata(u32 v) { return dist_of(ld_cg_u64(s + v)); }
@@ -430,13 +677,23 @@ struct PushOp {
 #pragma unroll
     for (int k = 0; k < K; ++k)
       old[k] = tried[k] ? atomicMin((unsigned long long *)(s + ed[k].x), cand[k]) : 0ull;
+    bool pw[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      pw[k] = false;
       if (tried[k] && cand[k] < old[k]) {
         ++n_imp;
-        if (nd[k] < thresh) want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
-        else far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
+        if (nd[k] >= thresh) far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
+        else if (pool) pw[k] = true;
+        else want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
       }
+    }
+    if (pool) {
+      bool rest[K];
+      pool_push<false>(pool, 0, tx, nd, pw, K, nullptr, nullptr, rest, n_in, row, nullptr);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (rest[k]) want[k] = atomicExch(qflag + tx[k], tag) != tag;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -725,8 +982,10 @@ __device__ __forceinline__ bool repair_enabled_block(Ctl *c) {
 }
 
 __device__ __forceinline__ Queue make_queue(int2 *ent, u32 *own, u64 *cnt, u32 *sv, u32 *scnt,
-                                            Stage *st = nullptr, Stage *sst = nullptr) {
+                                            Stage *st = nullptr, Stage *sst = nullptr,
+                                            u32 small = kSmallDeg) {
   Queue q;
+  q.small = small;
   q.ent = ent;
   q.owner = own;
   q.cnt = (unsigned long long *)cnt;
@@ -1160,9 +1419,13 @@ __device__ __forceinline__ LocalState local_episode(const LoopArgs &a, u32 lep, 
     if (threadIdx.x == 0) {
       // bounded wait: block 0 refreshes a heartbeat every round
       const u64 t0 = globaltimer_ns();
-      u32 nap = 32;
+      u32 nap = 32, polls = 0;
       while (ld_acquire_u32(&c->lres) < lep) {
         if (ld_cg_i32(&c->timeout) != 0) break;
+        if (++polls > kMaxPolls) {
+          raise_timeout(c, 2, 3, lep);
+          break;
+        }
         // the heartbeat is block 0's clock, read after this block's: it can
         // be the later of the two, and then nothing has run out yet
         const u64 beat = ld_cg_u64(&c->lbeat), now = globaltimer_ns();
@@ -1202,9 +1465,12 @@ __device__ __forceinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *
 __device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 
 template <int OP>
-__global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
-  extern __shared__ u32 dsm[];
+__global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads, 1)
+    k_loop(LoopArgs a) {
+  extern __shared__ __align__(16) u32 dsm[];
   __shared__ Stage sq, sqs, sa, sas, sf;
+  __shared__ Pool pool;
+  constexpr bool kPushOp = OP == kOpPush || OP == kOpPool;
   __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
   // beside the store update the invalidation starts once the batch is
@@ -1222,6 +1488,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     sa.n = 0; sa.cap = kStageA; sa.vmin = kInf; sa.v = p; sa.d = p + kStageA; p += 2 * kStageA;
     sas.n = 0; sas.cap = kStageAS; sas.vmin = kInf; sas.v = p; sas.d = nullptr; p += kStageAS;
     sf.n = 0; sf.cap = kStageF; sf.vmin = 0xFFFFFFFFu; sf.v = p; sf.d = nullptr;
+    if (OP == kOpPool) {
+      pool.e[0] = (uint4 *)(dsm + kLoopSmem / sizeof(u32));
+      pool.e[1] = pool.e[0] + kPoolCap;
+      pool.n[0] = pool.n[1] = 0u;
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -1232,7 +1503,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
   u64 n_edges = 0, n_imp = 0, n_enq = 0, n_aff = 0, moved = 0;
   int range_err = 0;
-  u64 *bar = OP == kOpPush ? &c->bar_push : &c->bar_inval;
+  u64 *bar = kPushOp ? &c->bar_push : &c->bar_inval;
+  PoolCounters pc;
   u64 target = 0;
 
   if (OP == kOpInval && a.n_del > 0) {
@@ -1274,7 +1546,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     flush_queue(q0, scratch);
   }
 
-  if (OP == kOpPush) {   // a batch's seeds: OnAdd, and the pull over A
+  if (kPushOp) {   // a batch's seeds: OnAdd, and the pull over A
     // (the cut list becomes A while OnAdd runs; the pull needs all of A)
     if (a.seed_pull) cut_to_a(a, &sa, &sas, scratch);
     if (a.n_items > 0) add_stage(a, &sq, &sqs, scratch);
@@ -1298,7 +1570,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   target += gridDim.x;
   bool stop = grid_sync(bar, target, c, a.lim);
 
-  const bool nf = OP == kOpPush && a.lim.delta > 0;
+  const bool nf = kPushOp && a.lim.delta > 0;
   u32 thresh = 0xFFFFFFFFu;
   if (nf) {
     const u32 sm = ld_cg_u32(&c->seed_min);
@@ -1333,8 +1605,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
       jump = true;   // the remaining levels by pointer jumping
       break;
     }
-    if (OP == kOpPush && items > 0 && ne + nsmall <= a.lim.local_edges &&
-        (u64)nedge + (u64)kSmallDeg * nsmall <= a.lim.local_edges) {
+    if (kPushOp && items > 0 && ne + nsmall <= a.lim.local_edges &&
+        (u64)nedge + (u64)a.lim.small_deg * nsmall <= a.lim.local_edges) {
       // small frontier: block 0 runs rounds alone until it grows or empties
       ++lep;
       const LocalState ls = local_episode(a, lep, cur, round, thresh, f, phase0 + 1u + splits,
@@ -1374,10 +1646,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     }
     const u32 tag = tag0 + 1u + round;
     const u32 phase = phase0 + 1u + splits;
-    const Queue qn =
-        make_queue(a.qent[nxt], a.qown[nxt], qcnt_ptr(c, nxt), a.qsv[nxt], scnt_ptr(c, nxt), &sq, &sqs);
+    const Queue qn = make_queue(a.qent[nxt], a.qown[nxt], qcnt_ptr(c, nxt), a.qsv[nxt],
+                                scnt_ptr(c, nxt), &sq, &sqs,
+                                kPushOp ? a.lim.small_deg : (u32)kSmallDeg);
     const u32 fk = next3(f);
-    if (OP == kOpPush) {
+    if (kPushOp) {
       if (split) {
         // far entries below thresh go back to the near frontier, the rest
         // move to the next pile.  An entry whose vertex was expanded since it
@@ -1390,27 +1663,34 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
           bool near[K] = {}, keep[K] = {};
           u32 x[K] = {};
           u32 kmin = 0xFFFFFFFFu;
+          u32 dx[K] = {};
           if (i < n_far) {
             x[0] = __ldcg(pin + i);
-            const u32 d = dist_of(ld_cg_u64(a.s + x[0]));
-            if (d < kInf) {
-              if (d < thresh) {
-                near[0] = atomicExch(a.qflag + x[0], tag) != tag;
+            dx[0] = dist_of(ld_cg_u64(a.s + x[0]));
+            if (dx[0] < kInf) {
+              if (dx[0] < thresh) {
+                near[0] = OP == kOpPool || atomicExch(a.qflag + x[0], tag) != tag;
               } else {
                 keep[0] = true;
                 a.ftag[x[0]] = phase + 1u;
-                kmin = d;
+                kmin = dx[0];
               }
             }
           }
           moved += near[0];
+          if (OP == kOpPool) {   // into the pool; what does not fit to the frontier
+            bool rest[K];
+            pool_push<false>(&pool, 0, x, dx, near, 1, nullptr, nullptr, rest, pc.n_in,
+                             a.fwd.row, nullptr);
+            near[0] = rest[0] && atomicExch(a.qflag + x[0], tag) != tag;
+          }
           enqueue(qn, a.fwd.row, x, near, 1, n_enq);
           far_append(a.fq[fk], fcnt_ptr(c, fk), fmin_ptr(c, fk), &sf, x, keep, 1, kmin);
         }
       } else {
         PushOp op{a.s, a.qflag, tag, qn, a.fwd.row, thresh,
                   nf ? a.fq[f] : nullptr, fcnt_ptr(c, f), fmin_ptr(c, f), a.ftag,
-                  phase, &sf};
+                  phase, &sf, OP == kOpPool ? &pool : nullptr};
         for (u32 it = gw; it < items; it += nw) {
           if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
           else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
@@ -1418,7 +1698,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
         n_edges += op.n_edges;
         n_imp += op.n_imp;
         n_enq += op.n_enq;
+        pc.n_in += op.n_in;
         range_err |= op.range_err;
+      }
+      if (OP == kOpPool) {
+        // the block relaxes what it improved below thresh before the barrier;
+        // its far appends belong to the phase that follows this round's split
+        const u32 fp = split ? fk : f;
+        pool_drain(a, &pool, thresh, tag, split ? phase + 1u : phase, qn,
+                   nf ? a.fq[fp] : nullptr, fcnt_ptr(c, fp), fmin_ptr(c, fp), &sf, pc);
       }
     } else if (OP == kOpFlag) {
       FlagOp op{a.prflag, a.ptag, qn, a.fwd.row};
@@ -1470,9 +1758,23 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
   n_enq = warp_sum(n_enq);
   n_aff = warp_sum(n_aff);
   moved = warp_sum(moved);
-  range_err = __any_sync(kFull, range_err);
+  range_err = __any_sync(kFull, range_err | pc.range_err);
+  if (OP == kOpPool) {
+    n_edges += warp_sum(pc.n_edges);
+    n_imp += warp_sum(pc.n_imp);
+    n_enq += warp_sum(pc.n_enq);
+    const u64 pin = warp_sum(pc.n_in);
+    if (lane == 0 && pin) atomicAdd(&c->pool_in, pin);
+    if (threadIdx.x == 0 && pc.subs) {
+      atomicAdd(&c->pool_sub, (u64)pc.subs);
+      if (blockIdx.x == 0) {
+        c->pool_ns = pc.ns;
+        c->pool_sub0 = pc.subs;
+      }
+    }
+  }
   if (lane == 0) {
-    if (OP == kOpPush) {
+    if (kPushOp) {
       if (n_edges) atomicAdd(&c->relaxed, n_edges);
       if (n_imp) atomicAdd(&c->improved, n_imp);
       if (n_enq) atomicAdd(&c->enqueued, n_enq);
@@ -1495,7 +1797,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_loop(LoopArgs a) {
     vc->scnt0 = 0u;
     vc->scnt1 = 0u;
     vc->scnt2 = 0u;
-    if (OP == kOpPush) {
+    if (kPushOp) {
       vc->rounds_push = round;
       vc->splits = splits;
       vc->push_ns = globaltimer_ns() - t_start;
@@ -1548,7 +1850,8 @@ __device__ __forceinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *
   const u32 sgroups = (nsmall + 31) / 32;
   const u32 items = sgroups + (nedge + kChunk - 1) / kChunk;
   const u32 tag = ld_cg_u32(&c->epoch);
-  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst);
+  const Queue q0 =
+      make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst, a.lim.small_deg);
   PullOp op{a.s, a.qflag, tag, q0, a.fwd.row, &c->seed_min};
   const u32 gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // interleaved over blocks
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
@@ -1574,7 +1877,8 @@ __device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *s
   Ctl *c = a.ctl;
   const int lane = threadIdx.x & 31;
   const u32 tag = ld_cg_u32(&c->epoch);
-  const Queue q0 = make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst);
+  const Queue q0 =
+      make_queue(a.qent[0], a.qown[0], &c->qcnt0, a.qsv[0], &c->scnt0, st, sst, a.lim.small_deg);
   const u64 cmask = (1ull << a.bits) - 1;
   const long long gw = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1688,6 +1992,76 @@ __global__ void k_unpack(const u64 *__restrict__ s, int n, int *dist, int *paren
     dist[v] = (int)dist_of(x);
     if (parent) parent[v] = (int)parent_of(x);
   }
+}
+
+// --- restoring exported distances -----------------------------------------
+//
+// A (dist, parent) pair exported by sp_get_dist is installed again only if
+// it is the exact shortest-path solution of the current edge set from
+// `src`: dist[src] = 0 with parent -1; every other finite dist[v] has a
+// parent p with an edge p -> v of weight dist[v] - dist[p] (w >= 1 makes
+// the parent chains strictly decreasing, so they are acyclic and end at the
+// source: every finite distance is realised by a path); every infinite one
+// has parent -1; and no edge u -> x offers dist[u] + w < dist[x].  Together
+// these say that dist equals the shortest-path distances (the problem of
+// Section 3.2), so a restore gives the same answer as a recompute.  A
+// violation sets the status (SP_EINVAL) and nothing is installed.
+
+__global__ void k_state_vertices(const int *__restrict__ dist, const int *__restrict__ parent,
+                                 int n, int src, Store fwd, Ctl *c) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int d = dist[v], p = parent[v];
+    bool ok;
+    if (v == src) {
+      ok = d == 0 && p == -1;
+    } else if (d < 0 || d > (int)kInf) {
+      ok = false;
+    } else if (d == (int)kInf) {
+      ok = p == -1;
+    } else if (p < 0 || p >= n || p == (int)v) {
+      ok = false;
+    } else {
+      const int dp = dist[p];
+      ok = false;
+      if (dp >= 0 && dp < d) {   // the parent edge p -> v: a search in p's sorted row
+        const RowMeta rm = fwd.row[p];
+        long long lo = rm.start, hi = rm.start + rm.deg;
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (__ldg(&fwd.adj[mid].x) < (int)v) lo = mid + 1; else hi = mid;
+        }
+        ok = lo < rm.start + rm.deg && __ldg(&fwd.adj[lo].x) == (int)v &&
+             (long long)dp + __ldg(&fwd.adj[lo].y) == (long long)d;
+      }
+    }
+    if (!ok) atomicCAS(&c->status, 0, SP_EINVAL);
+  }
+}
+
+// Every edge: no shorter way into its head (one warp per row).
+__global__ void k_state_edges(const int *__restrict__ dist, int n, Store fwd, Ctl *c) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+  for (long long u = w0; u < n; u += nw) {
+    const int du = dist[u];
+    if (du >= (int)kInf) continue;
+    const RowMeta rm = fwd.row[u];
+    for (int e = lane; e < rm.deg; e += 32) {
+      const int2 ed = __ldg(&fwd.adj[rm.start + e]);
+      if ((long long)du + ed.y < (long long)dist[ed.x]) bad = true;
+    }
+  }
+  if (__any_sync(kFull, bad) && lane == 0) atomicCAS(&c->status, 0, SP_EINVAL);
+}
+
+__global__ void k_state_pack(const int *__restrict__ dist, const int *__restrict__ parent,
+                             int n, u64 *s) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    s[v] = pack((u32)dist[v], (u32)parent[v]);
 }
 
 // --- PageRank (appendix listing "Dynamic PR") ---------------------------------
@@ -1935,10 +2309,13 @@ int loop_blocks(int which, int num_sms) {
   int per_sm = 0;
   const void *fn = which == kOpPush    ? (const void *)k_loop<kOpPush>
                    : which == kOpInval ? (const void *)k_loop<kOpInval>
+                   : which == kOpPool  ? (const void *)k_loop<kOpPool>
                                        : (const void *)k_loop<kOpFlag>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmem) !=
+  const size_t smem = which == kOpPool ? kLoopSmemPool : kLoopSmem;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistThreads, kLoopSmem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, fn, which == kOpPool ? kPoolThreads : kPersistThreads, smem) !=
           cudaSuccess ||
       per_sm < 1)
     return 0;
@@ -1962,7 +2339,9 @@ void launch_init(sp_graph *g, int source, int *launches) {
 // Blocks of a persistent loop; an invalidation beside the store update
 // takes a quarter of the SMs and leaves the rest to the count and merge.
 static int loop_grid(const sp_graph *g, int op, int concurrent) {
-  int blocks = op == kOpPush ? g->loop_blocks_push : g->loop_blocks_inval;
+  int blocks = op == kOpPush   ? g->loop_blocks_push
+               : op == kOpPool ? g->loop_blocks_pool
+                               : g->loop_blocks_inval;
   if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
   if (concurrent) blocks = std::max(1, std::min(blocks, g->num_sms / 4));
   return blocks;
@@ -1973,8 +2352,8 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
   const int blocks = loop_grid(g, op, a.concurrent);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kPersistThreads);
-  cfg.dynamicSmemBytes = kLoopSmem;
+  cfg.blockDim = dim3(op == kOpPool ? kPoolThreads : kPersistThreads);
+  cfg.dynamicSmemBytes = op == kOpPool ? kLoopSmemPool : kLoopSmem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
@@ -1983,6 +2362,7 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
   cfg.numAttrs = 1;
   ++*launches;
   if (op == kOpPush) return cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a);
+  if (op == kOpPool) return cudaLaunchKernelEx(&cfg, k_loop<kOpPool>, a);
   if (op == kOpInval) return cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
   return cudaLaunchKernelEx(&cfg, k_loop<kOpFlag>, a);
 }
@@ -2021,7 +2401,12 @@ cudaError_t launch_push(sp_graph *g, int *launches, int pull, long long n_items)
   LoopArgs a = make_args(g);
   a.seed_pull = pull;
   a.n_items = n_items;
-  return launch_loop(g, kOpPush, a, launches, g->stream);
+  // pool entries carry a row's start / 4 in 32 bits
+  if (g->fwd.slots >= (1LL << 34)) a.lim.pool_rounds = 0;
+  // a single-block round covers kLocalUnroll edges per thread
+  if (a.lim.pool_rounds > 0)
+    a.lim.local_edges = std::min<u32>(a.lim.local_edges, (u32)(kLocalUnroll * kPoolThreads));
+  return launch_loop(g, a.lim.pool_rounds > 0 ? kOpPool : kOpPush, a, launches, g->stream);
 }
 
 void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches) {
@@ -2075,6 +2460,20 @@ cudaError_t launch_pr(sp_graph *g, int *launches) {
   cfg.numAttrs = 1;
   ++*launches;
   return cudaLaunchKernelEx(&cfg, k_pr, p);
+}
+
+void launch_state_check(sp_graph *g, const int *dist_d, const int *parent_d, int src,
+                        int *launches) {
+  const unsigned grid = (unsigned)std::max(1, g->num_sms * 8);
+  k_state_vertices<<<grid, 256, 0, g->stream>>>(dist_d, parent_d, g->n, src, g->fwd, g->ctl);
+  k_state_edges<<<grid, 256, 0, g->stream>>>(dist_d, g->n, g->fwd, g->ctl);
+  *launches += 2;
+}
+
+void launch_state_pack(sp_graph *g, const int *dist_d, const int *parent_d, int *launches) {
+  k_state_pack<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(dist_d, parent_d,
+                                                                            g->n, g->s);
+  ++*launches;
 }
 
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches) {

@@ -17,6 +17,19 @@ constexpr int kSmallDeg = 8;
 constexpr int kLocalRoundCap = 4096;   // frontier edges of a single-block round
 constexpr int kLoopThreads = 1024;      // one-pass frontier kernels (pull, add)
 constexpr int kPersistThreads = 768;    // persistent fixedPoint loops: 80 registers a thread
+// the push loop with block-local relaxation: a sub-round expands about a
+// hundred pool entries per block, so fewer threads with more registers each
+// (128) serve it better than 768 that spill
+constexpr int kPoolThreads = 512;
+// Co-residency of cooperative launches from several handles at once (the
+// serving runtime's slots): a handle with a block share (sp_set_loop_blocks)
+// launches every cooperative kernel with at most that many blocks, each with
+// at least this much dynamic shared memory.  Two such blocks do not fit in
+// one SM's 228 KB, so every cooperative block holds an SM to itself and the
+// shares of all slots, summed, never ask for more SMs than the GPU has: each
+// grid is resident in full whatever the others do, and no grid barrier can
+// wait for a block that has no SM.
+constexpr size_t kExclusiveSmem = 116 * 1024;
 
 // Per-block staging area (shared memory) for appends to a queue or a far
 // pile: warps append here with shared-memory atomics and the block publishes
@@ -40,6 +53,19 @@ struct Queue {
   u32 *sv = nullptr;                   // small list
   u32 *scnt = nullptr;
   Stage *sst = nullptr;
+  u32 small = kSmallDeg;               // largest out-degree kept in the small list
+};
+
+// Block-local relaxation of the push loop: two lists of entries in shared
+// memory, each entry (vertex, distance it was improved to, row start / 4,
+// out-degree) for vertices with at most kPoolDeg out-edges.  A sub-round
+// expands one list into the other; the block runs sub-rounds on its own
+// (block barriers only) before it meets the others at the grid barrier.
+constexpr int kPoolDeg = 16;            // largest out-degree a pool entry may have
+constexpr u32 kPoolCap = 2048;          // entries per list
+struct Pool {
+  uint4 *e[2];
+  u32 n[2];                             // appended so far (may pass kPoolCap)
 };
 
 // One touched (store, row) pair of a batch, after sorting.
@@ -176,6 +202,14 @@ struct sp_graph {
   long long last_nd = -1, last_na = -1;
   int last_timed = -1;
   int32_t local_edges_user = 4096;
+  int32_t small_deg_user = sp::kSmallDeg;   // push frontiers' small-list bound
+  int32_t pool_rounds_user = 0;             // block-local sub-rounds per push round
+  int32_t miss_site_user = 0;               // test hook of the bounded waits
+  // the sources of the last init (one, or the batched form's list on the
+  // device), kept so that a batch that fails after the invalidation can
+  // restore the distances without allocating
+  int *src_dev = nullptr;
+  int32_t n_src = 0;
   long long own_cap = 0;        // entries of each chunk-owner table
   sp::Ctl *ctl = nullptr;       // device
   sp::Ctl *ctl_host = nullptr;  // pinned
@@ -186,7 +220,7 @@ struct sp_graph {
   sp::Limits lim{};
   int32_t max_rounds_user = 0;
   long long wait_ns_user = 0;
-  int loop_blocks_push = 0, loop_blocks_inval = 0;
+  int loop_blocks_push = 0, loop_blocks_inval = 0, loop_blocks_pool = 0;
   int sort_blocks = 0;          // co-resident blocks of the batch sort
   int count_blocks = 0;         // co-resident blocks of the count pass
   int loop_blocks_user = 0;
@@ -238,6 +272,11 @@ cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd
 // pulls over A and relaxes the applied insertions
 cudaError_t launch_push(sp_graph *g, int *launches, int pull = 0, long long n_items = 0);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+// restore of exported distances: the exactness checks (status SP_EINVAL on a
+// violation), then the packed state
+void launch_state_check(sp_graph *g, const int *dist_d, const int *parent_d, int src,
+                        int *launches);
+void launch_state_pack(sp_graph *g, const int *dist_d, const int *parent_d, int *launches);
 // sp_tc.cu
 void launch_tc_sym_check(sp_graph *g, int *launches);
 void launch_tc_static(sp_graph *g, int *launches);

@@ -142,6 +142,10 @@ struct Ctl {
   u32 rounds_inval, rounds_push, splits;
   u32 local_episodes, local_rounds, jumps;
   u64 local_ns, push_ns;   // block 0's time in single-block rounds / in the push loop
+  u64 pool_sub;            // block-local sub-rounds, summed over blocks
+  u64 pool_in;             // entries appended to the block pools
+  u64 pool_ns;             // block 0's time in block-local sub-rounds
+  u64 pool_sub0;           // block 0's block-local sub-rounds
 };
 
 // Launch-time limits and knobs.
@@ -153,7 +157,19 @@ struct Limits {
                          // run in one block (0 = never)
   int jump_round;        // frontier rounds of the invalidation before it
                          // switches to pointer jumping (< 0: never)
+  u32 small_deg;         // push frontiers: vertices with at most this many
+                         // out-edges are expanded one lane each, larger ones
+                         // as edge chunks spread over warps
+  u32 pool_rounds;       // block-local relaxation: block sub-rounds per push
+                         // round (0 = off, plain frontier rounds)
+  u32 miss_site;         // test hook: block 0 does not arrive at the grid
+                         // barriers of this wait site (0 = none), so that
+                         // their bounded waits run out
 };
+
+// Every barrier wait also ends after this many polls, whatever the clock
+// says (a poll sleeps 64 ns and reads one word: seconds in all).
+constexpr u32 kMaxPolls = 1u << 24;
 
 // ---------------------------------------------------------------------------
 // Small device helpers.
@@ -193,37 +209,47 @@ __device__ __forceinline__ u64 ld_acquire_u64_(const u64 *p) {
 }
 
 // Grid barrier of a cooperative launch on a monotone arrival count (zeroed
-// when the call starts): barrier k waits for k * gridDim.x arrivals.  A wait
-// is bounded by wait_ns; one that runs out raises the call's timeout (kind
-// 2, at `site`) and SP_ETIMEOUT status, and every later wait returns at
-// once.  Returns whether a timeout was raised, the same in every thread.
-// Callers use it before anything has changed, so the status leaves the
-// graph as it was.
+// when the call starts): barrier k waits for k * gridDim.x arrivals.  Used by
+// the batch sort (site 4) and the count pass (site 5), which run before the
+// merge changes anything.  A wait is bounded by wait_ns (and kMaxPolls); the
+// first one that runs out sets the call's status to SP_ETIMEOUT and records
+// its site (over a loop's earlier record: the site then says that the store
+// update stopped, and the edge set is as it was).  Every wait also ends when
+// the status is set (the kernel's other blocks failed, or the batch was
+// invalid), so all blocks leave together.  A timeout of another kernel (the
+// invalidation beside the store update) does not stop these barriers.
+// Returns whether the kernel must stop, the same in every thread.
 __device__ __forceinline__ bool coop_barrier(u64 *bar, u64 target, Ctl *c, u64 wait_ns,
-                                             u32 site) {
+                                             u32 site, u32 miss_site = 0) {
   __shared__ int s_stop;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     // the count before this arrival says whether it was the last one; the
-    // wait polls the count alone and looks at the timeout flag and the
-    // clock every 16th poll
-    if (atomicAdd((unsigned long long *)bar, 1ull) + 1 < target) {
+    // wait polls the count alone and looks at the status and the clock every
+    // 16th poll.  (miss_site: block 0 does not arrive, and every wait of the
+    // barrier runs out.)
+    const bool miss = miss_site == site && blockIdx.x == 0;
+    const u64 arrived = miss ? ld_acquire_u64_(bar) : atomicAdd((unsigned long long *)bar, 1ull) + 1;
+    if (arrived < target) {
       const u64 t0 = globaltimer_ns();
       u32 polls = 0;
       while (ld_acquire_u64_(bar) < target) {
         if ((++polls & 15u) == 0) {
-          if (ld_cg_i32(&c->timeout) != 0) break;
-          if (globaltimer_ns() - t0 > wait_ns) {
-            raise_timeout(c, 2, site, (u32)(target / gridDim.x));
+          if (ld_cg_i32(&c->status) != 0) break;
+          if (globaltimer_ns() - t0 > wait_ns || polls > kMaxPolls) {
+            if (atomicCAS(&c->status, 0, SP_ETIMEOUT) == 0) {
+              atomicExch(&c->timeout, 2);
+              c->to_site = site;
+              c->to_info = (u32)(target / gridDim.x);
+            }
             break;
           }
         }
         __nanosleep(64);
       }
     }
-    s_stop = ld_cg_i32(&c->timeout) != 0;
-    if (s_stop) atomicCAS(&c->status, 0, SP_ETIMEOUT);
+    s_stop = ld_cg_i32(&c->status) != 0;
   }
   __syncthreads();
   return s_stop != 0;

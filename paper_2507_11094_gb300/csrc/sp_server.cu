@@ -3,12 +3,17 @@
 // A request loop over several graphs: worker slots (threads) take the oldest
 // runnable request whose graph is not already in use, so requests of one
 // graph keep their order while requests of different graphs run at the same
-// time on their own CUDA streams.  Graphs are admitted under an HBM budget:
-// before a non-resident graph is loaded, idle resident graphs are evicted in
-// least-recently-used order (their edge set is exported to host memory and
-// the handle destroyed); a reloaded graph is rebuilt from that checkpoint and
-// its distances recomputed from its source.  Each graph's persistent loops
-// use a share of the SMs so that several can be resident together.
+// time on their own CUDA streams.  Graphs are admitted under an HBM budget,
+// by an upper bound of their footprint (sp_footprint_bound, with the batch
+// buffers reserved for the largest batch a request may carry): before a
+// non-resident graph is loaded, idle resident graphs are evicted in
+// least-recently-used order (their edge set and their distances and parents
+// are exported to host memory and the handle destroyed); a reloaded graph is
+// rebuilt from that checkpoint and its distances restored (sp_set_dist
+// checks that they are exact) instead of recomputed.  No request starts
+// while the resident graphs are over the budget.  Each graph's cooperative
+// kernels use a share of the SMs (sp_set_loop_blocks), each block an SM of
+// its own, so that the grids of all slots are resident together.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -45,10 +50,12 @@ struct GEnt {
   int32_t source = 0;
   sp_graph *g = nullptr;
   cudaStream_t stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // device interval of a request
   std::vector<int64_t> ro;  // checkpoint of the edge set while not resident
   std::vector<int32_t> col, w;
-  int64_t bytes = 0;        // device bytes when last resident (0: estimate)
-  int64_t bytes_est = 0;
+  std::vector<int32_t> ck_dist, ck_parent;   // and of the distances (if valid)
+  int64_t bound = 0;        // footprint bound of the checkpointed graph
+  int64_t charge = 0;       // bytes counted in `resident` while resident
   bool busy = false;        // a worker holds it (request, load or eviction)
   std::deque<Req *> pending;
   int64_t last_used = 0;
@@ -70,18 +77,24 @@ struct sp_server {
   int64_t resident = 0, max_resident = 0, loads = 0, evictions = 0;
   int64_t batches = 0, queries = 0, updates = 0;
   std::atomic<int64_t> recovered{0};
+  int64_t restores = 0;       // reloads that restored distances (no recompute)
   Clock::time_point t0 = Clock::now();
+  cudaStream_t ref_stream = nullptr;
+  cudaEvent_t ref_ev = nullptr;   // the device clock's origin for request intervals
 
   double now_ms() const {
     return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
   }
   void worker(int slot);
-  sp_status make_room(std::unique_lock<std::mutex> &lk, int64_t need, bool wait);
+  sp_status make_room(std::unique_lock<std::mutex> &lk, int64_t need, bool wait,
+                      const GEnt *self = nullptr);
   sp_status load(GEnt *ge);
   sp_status evict(GEnt *ge);
 };
 
-// Build a handle from the checkpoint and recompute distances (mu not held).
+// Build a handle from the checkpoint (mu not held): batch buffers reserved
+// for the largest batch, distances restored from the checkpoint when it
+// holds them (checked exact on the device), else computed from the source.
 sp_status sp_server::load(GEnt *ge) {
   sp_graph *g = nullptr;
   const int64_t m = ge->ro.empty() ? 0 : ge->ro.back();
@@ -91,7 +104,11 @@ sp_status sp_server::load(GEnt *ge) {
   int lb = cfg.loop_blocks > 0 ? cfg.loop_blocks : std::max(1, num_sms / std::max(1, cfg.n_slots));
   sp_set_loop_blocks(g, lb);
   sp_set_push_delta(g, cfg.delta);
-  rc = sp_sssp_init(g, ge->source, nullptr);
+  rc = sp_reserve(g, cfg.max_batch_updates);
+  bool restored = false;
+  if (rc == SP_OK && !ge->ck_dist.empty())
+    restored = sp_set_dist(g, ge->source, ge->ck_dist.data(), ge->ck_parent.data(), 0) == SP_OK;
+  if (rc == SP_OK && !restored) rc = sp_sssp_init(g, ge->source, nullptr);
   if (rc != SP_OK) {
     sp_graph_destroy(g);
     return rc;
@@ -103,14 +120,18 @@ sp_status sp_server::load(GEnt *ge) {
     return SP_ENOMEM_BUDGET;
   }
   ge->g = g;
-  ge->bytes = info.device_bytes;
+  ge->charge = std::max<int64_t>(ge->bound, info.device_bytes);
+  if (restored) ++restores;
   std::vector<int64_t>().swap(ge->ro);   // the checkpoint is stale from here on
   std::vector<int32_t>().swap(ge->col);
   std::vector<int32_t>().swap(ge->w);
+  std::vector<int32_t>().swap(ge->ck_dist);
+  std::vector<int32_t>().swap(ge->ck_parent);
   return SP_OK;
 }
 
-// Checkpoint the edge set to host memory and release the handle.
+// Checkpoint the edge set, the distances and the parents to host memory and
+// release the handle.
 sp_status sp_server::evict(GEnt *ge) {
   int64_t m = 0;
   sp_status rc = sp_graph_num_edges(ge->g, &m);
@@ -122,28 +143,39 @@ sp_status sp_server::evict(GEnt *ge) {
   if (rc != SP_OK) return rc;
   ge->col.resize((size_t)m);
   ge->w.resize((size_t)m);
-  sp_graph_info info{};
-  sp_graph_info_get(ge->g, &info);
-  ge->bytes = info.device_bytes;
+  ge->ck_dist.assign((size_t)ge->n, 0);
+  ge->ck_parent.assign((size_t)ge->n, 0);
+  if (sp_get_dist(ge->g, ge->ck_dist.data(), ge->ck_parent.data(), 0) != SP_OK) {
+    std::vector<int32_t>().swap(ge->ck_dist);   // no valid distances: recompute on load
+    std::vector<int32_t>().swap(ge->ck_parent);
+  }
+  int64_t b = 0;
+  ge->bound = sp_footprint_bound(ge->n, m, cfg.slack, cfg.max_batch_updates, &b) == SP_OK
+                  ? b : ge->charge;
   sp_graph_destroy(ge->g);
   ge->g = nullptr;
   return SP_OK;
 }
 
 // Evict idle resident graphs, least recently used first, until `need` more
-// bytes fit the budget (mu held; released around each eviction).  When every
-// resident graph is running, wait for one to finish if `wait`, else stop
-// there; with nothing resident and running, the request runs over budget
-// alone (its graph was admitted by a lower-bound estimate).
-sp_status sp_server::make_room(std::unique_lock<std::mutex> &lk, int64_t need, bool wait) {
+// bytes fit the budget (mu held; released around each eviction).  `self` is
+// the graph the caller holds (never a victim, and not counted as running).
+// When every other resident graph is running, wait for one to finish if
+// `wait`, else stop there (SP_OK: the caller re-checks before its next
+// request).  SP_ENOMEM_BUDGET when nothing is left to evict or wait for.
+sp_status sp_server::make_room(std::unique_lock<std::mutex> &lk, int64_t need, bool wait,
+                               const GEnt *self) {
   while (resident + need > cfg.hbm_budget_bytes) {
     GEnt *victim = nullptr;
     for (auto &g : graphs)
       if (g->g && !g->busy && (!victim || g->last_used < victim->last_used)) victim = g.get();
     if (!victim) {
+      // graphs being loaded or running a request (not those waiting for
+      // admission, which hold nothing yet)
       bool running = loading > 0;
-      for (auto &g : graphs) running |= (g->g && g->busy);
-      if (!running || !wait) return SP_OK;
+      for (auto &g : graphs) running |= (g.get() != self && g->g && g->busy);
+      if (!wait) return SP_OK;
+      if (!running) return SP_ENOMEM_BUDGET;
       cv_done.wait(lk);
       continue;
     }
@@ -152,7 +184,8 @@ sp_status sp_server::make_room(std::unique_lock<std::mutex> &lk, int64_t need, b
     const sp_status rc = evict(victim);
     lk.lock();
     if (rc == SP_OK) {
-      resident -= victim->bytes;
+      resident -= victim->charge;
+      victim->charge = 0;
       ++evictions;
     }
     victim->busy = false;
@@ -184,38 +217,44 @@ void sp_server::worker(int slot) {
     ge->pending.pop_front();
     r->info.start_ms = now_ms();
     r->info.slot = slot;
+    r->info.gpu_start_ms = r->info.gpu_done_ms = -1.0;
     sp_status rc = SP_OK;
     if (!ge->g) {
-      // admission: evict idle resident graphs (LRU) until this one fits
-      const int64_t want = ge->bytes ? ge->bytes : ge->bytes_est;
-      rc = make_room(lk, want, true);
+      // admission: evict idle resident graphs (LRU) until the footprint
+      // bound of this one fits
+      rc = make_room(lk, ge->bound, true, ge);
       if (rc == SP_OK) {
-        resident += want;
+        resident += ge->bound;
         max_resident = std::max(max_resident, resident);
         ++loading;
         lk.unlock();
         rc = load(ge);
         lk.lock();
         --loading;
-        resident += (rc == SP_OK ? ge->bytes : 0) - want;
-        max_resident = std::max(max_resident, resident);
         if (rc == SP_OK) {
+          resident += ge->charge - ge->bound;   // the measured size, if above the bound
           ++loads;
           r->info.loaded = 1;
-          // the first load of a graph replaces an estimate by its size
-          if (resident > cfg.hbm_budget_bytes) (void)make_room(lk, 0, false);
+        } else {
+          resident -= ge->bound;
         }
+        max_resident = std::max(max_resident, resident);
       }
+    } else if (resident > cfg.hbm_budget_bytes) {
+      // a graph outgrew its bound (its spare pool grew): no request starts
+      // until the others make room
+      rc = make_room(lk, 0, true, ge);
     }
     lk.unlock();
     if (rc == SP_OK) {
+      cudaEventRecord(ge->ev[0], ge->stream);
       if (r->kind == 0) {
         rc = sp_apply_batch(ge->g, (int64_t)r->ds.size(), r->ds.data(), r->dd.data(),
                             (int64_t)r->as.size(), r->as.data(), r->ad.data(), r->aw.data(), 0,
                             nullptr);
         if (rc == SP_ETIMEOUT) {
-          // a device bound stopped the repair after the edges were merged:
-          // recompute the distances from the source (exact), once
+          // a device bound stopped the repair: recompute the distances from
+          // the source (exact), once
           rc = sp_sssp_init(ge->g, ge->source, nullptr);
           if (rc == SP_OK) ++recovered;
         }
@@ -223,15 +262,24 @@ void sp_server::worker(int slot) {
         r->qout.assign(r->qv.size(), 0);
         rc = sp_query(ge->g, (int32_t)r->qv.size(), r->qv.data(), r->qout.data(), 0);
       }
+      cudaEventRecord(ge->ev[1], ge->stream);
+      float t0 = 0.f, t1 = 0.f;
+      if (cudaEventSynchronize(ge->ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&t0, ref_ev, ge->ev[0]) == cudaSuccess &&
+          cudaEventElapsedTime(&t1, ref_ev, ge->ev[1]) == cudaSuccess) {
+        r->info.gpu_start_ms = t0;
+        r->info.gpu_done_ms = t1;
+      }
+      cudaGetLastError();
     }
     sp_graph_info info{};
     if (ge->g) sp_graph_info_get(ge->g, &info);
     lk.lock();
-    if (ge->g && info.device_bytes != ge->bytes) {   // batch buffers may have grown
-      resident += info.device_bytes - ge->bytes;
-      ge->bytes = info.device_bytes;
+    if (ge->g && info.device_bytes > ge->charge) {   // the spare pool grew
+      resident += info.device_bytes - ge->charge;
+      ge->charge = info.device_bytes;
       max_resident = std::max(max_resident, resident);
-      if (resident > cfg.hbm_budget_bytes) (void)make_room(lk, 0, false);
+      if (resident > cfg.hbm_budget_bytes) (void)make_room(lk, 0, false, ge);
     }
     r->info.status = rc;
     r->info.done_ms = now_ms();
@@ -254,16 +302,23 @@ extern "C" {
 
 sp_status sp_server_create(const sp_server_config *cfg, sp_server **out) {
   if (!cfg || !out || cfg->n_slots < 1 || cfg->n_slots > 64 || cfg->hbm_budget_bytes <= 0 ||
-      cfg->loop_blocks < 0 || cfg->delta < 0 || !(cfg->slack >= 0.f))
+      cfg->loop_blocks < 0 || cfg->delta < 0 || !(cfg->slack >= 0.f) || cfg->slack > 16.f ||
+      cfg->max_batch_updates < 0 || cfg->max_batch_updates > (1LL << 30))
     return SP_EINVAL;
   *out = nullptr;
   sp_server *s = new (std::nothrow) sp_server();
   if (!s) return SP_ENOMEM;
   s->cfg = *cfg;
+  if (s->cfg.max_batch_updates == 0) s->cfg.max_batch_updates = 1 << 20;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) !=
-          cudaSuccess) {
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->ref_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&s->ref_ev) != cudaSuccess || cudaEventRecord(s->ref_ev, s->ref_stream) !=
+      cudaSuccess || cudaEventSynchronize(s->ref_ev) != cudaSuccess) {
     cudaGetLastError();
+    if (s->ref_ev) cudaEventDestroy(s->ref_ev);
+    if (s->ref_stream) cudaStreamDestroy(s->ref_stream);
     delete s;
     return SP_ECUDA;
   }
@@ -283,8 +338,12 @@ sp_status sp_server_destroy(sp_server *s) {
   for (auto &t : s->workers) t.join();
   for (auto &g : s->graphs) {
     if (g->g) sp_graph_destroy(g->g);
+    for (auto &e : g->ev)
+      if (e) cudaEventDestroy(e);
     if (g->stream) cudaStreamDestroy(g->stream);
   }
+  cudaEventDestroy(s->ref_ev);
+  cudaStreamDestroy(s->ref_stream);
   delete s;
   return SP_OK;
 }
@@ -301,13 +360,16 @@ sp_status sp_server_add_graph(sp_server *s, int32_t n, int64_t m, const int64_t 
   ge->ro.assign(row_off, row_off + n + 1);
   ge->col.assign(col, col + m);
   ge->w.assign(w, w + m);
-  // lower bound of the device footprint before the first load: per-vertex
-  // state and frontier queues (~92 B), row metadata of both stores, and two
-  // regions of at least deg slots (8 B) per row in both stores
-  ge->bytes_est = (int64_t)n * 124 + m * 32;
-  if (ge->bytes_est > s->cfg.hbm_budget_bytes) return SP_ENOMEM_BUDGET;
-  if (cudaStreamCreateWithFlags(&ge->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // admitted by an upper bound of its footprint, batch buffers included
+  sp_status rc = sp_footprint_bound(n, m, s->cfg.slack, s->cfg.max_batch_updates, &ge->bound);
+  if (rc != SP_OK) return rc;
+  if (ge->bound > s->cfg.hbm_budget_bytes) return SP_ENOMEM_BUDGET;
+  if (cudaStreamCreateWithFlags(&ge->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&ge->ev[0]) != cudaSuccess || cudaEventCreate(&ge->ev[1]) != cudaSuccess) {
     cudaGetLastError();
+    for (auto &e : ge->ev)
+      if (e) cudaEventDestroy(e);
+    if (ge->stream) cudaStreamDestroy(ge->stream);
     return SP_ECUDA;
   }
   std::lock_guard<std::mutex> lk(s->mu);
@@ -340,7 +402,7 @@ sp_status sp_server_submit_batch(sp_server *s, int32_t graph_id, int64_t n_del,
                                  const int32_t *add_src, const int32_t *add_dst,
                                  const int32_t *add_w, int64_t *request_id) {
   if (!s || !request_id || n_del < 0 || n_add < 0 || (n_del && (!del_src || !del_dst)) ||
-      (n_add && (!add_src || !add_dst || !add_w)))
+      (n_add && (!add_src || !add_dst || !add_w)) || n_del + n_add > s->cfg.max_batch_updates)
     return SP_EINVAL;
   auto r = std::make_unique<Req>();
   r->kind = 0;
@@ -403,6 +465,7 @@ sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out) {
   for (auto &g : s->graphs) res += g->g ? 1 : 0;
   out->resident_graphs = res;
   out->recoveries = s->recovered.load();
+  out->restores = s->restores;
   return SP_OK;
 }
 

@@ -235,6 +235,7 @@ struct BatchSortArgs {
   Seg *seg;
   Ctl *ctl;
   unsigned long long wait_ns;
+  u32 miss_site;         // test hook of the bounded waits (Limits::miss_site)
   u32 n_items, chunk;
 };
 
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
   a.tab[(size_t)b * kBins + t] = s_hist[t];
 
   for (int p = 0; p < a.passes; ++p) {
-    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4)) return;
+    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4, a.miss_site)) return;
     const int shift = p * kBits;
     // digit bases of this chunk: thread t sums digits 4*(t % 128) .. +3 over
     // the rows q = t / 128 (mod 4) with 16-byte loads; the four partial sums
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
       s_off[t] += s_hist[t];
       __syncthreads();
     }
-    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4)) return;
+    if (coop_barrier(bar, ++nbar * G, c, a.wait_ns, 4, a.miss_site)) return;
     if (p + 1 < a.passes) {   // the next digit's counts over this chunk
       const int nshift = shift + kBits;
       s_hist[t] = 0;
@@ -603,7 +604,7 @@ size_t sort_tmp_bytes(long long n) {
 int batch_sort_blocks(int num_sms) {
   int per_sm = 0;
   if (cudaFuncSetAttribute(k_batch_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kBSmem) != cudaSuccess ||
+                           (int)std::max(kBSmem, kExclusiveSmem)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_sort, kBT, kBSmem) !=
           cudaSuccess ||
       per_sm < 1)
@@ -616,6 +617,12 @@ size_t batch_sort_tmp_bytes(int max_blocks) {
 }
 
 namespace {
+
+// Dynamic shared memory of a launch: a handle with a block share gives each
+// block an SM of its own (kExclusiveSmem).
+size_t sort_smem(const sp_graph *g) {
+  return g->loop_blocks_user > 0 ? std::max(kBSmem, kExclusiveSmem) : kBSmem;
+}
 
 // Arguments and grid of the batch sort for these inputs.
 int batch_sort_args(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
@@ -641,6 +648,7 @@ int batch_sort_args(sp_graph *g, const int *ds, const int *dd, long long nd, con
   a.seg = bb.seg;
   a.ctl = g->ctl;
   a.wait_ns = g->lim.wait_ns;
+  a.miss_site = g->lim.miss_site;
   a.n_items = (u32)ni;
   a.chunk = (u32)((ni + G - 1) / G);
   return G;
@@ -659,7 +667,7 @@ cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long lo
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kBT);
-  cfg.dynamicSmemBytes = kBSmem;
+  cfg.dynamicSmemBytes = sort_smem(g);
   cfg.stream = g->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
@@ -680,7 +688,7 @@ cudaError_t retarget_batch_sort(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t
   p.func = (void *)k_batch_sort;
   p.gridDim = dim3((unsigned)G);
   p.blockDim = dim3(kBT);
-  p.sharedMemBytes = (unsigned)kBSmem;
+  p.sharedMemBytes = (unsigned)sort_smem(g);
   p.kernelParams = args;
   return cudaGraphExecKernelNodeSetParams(ex, node, &p);
 }

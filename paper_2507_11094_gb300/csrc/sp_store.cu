@@ -245,6 +245,8 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->rounds_push = c->splits = 0;
   c->local_episodes = c->local_rounds = 0;
   c->local_ns = c->push_ns = 0;
+  c->pool_sub = c->pool_in = 0;
+  c->pool_ns = c->pool_sub0 = 0;
   c->call = c->call + 1;
   if (full == 1) {
     c->epoch = 1;
@@ -305,6 +307,7 @@ struct CountArgs {
   u32 chunk;           // items per block
   int n;
   u64 wait_ns;
+  u32 miss_site;         // test hook of the bounded waits (Limits::miss_site)
 };
 
 // The merge works on strips of kStrip old entries of a row, one warp each.
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
     }
   }
   if (t == 0) __stcg(a.tab + b, s_run);
-  if (coop_barrier(bar, (u64)G, c, a.wait_ns, 5)) return;
+  if (coop_barrier(bar, (u64)G, c, a.wait_ns, 5, a.miss_site)) return;
   {   // this block's base: the totals of the blocks before it
     u64 part = 0;
     for (u32 q = t; q < b; q += kCT) part += __ldcg(a.tab + q);
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
     for (u32 i = cb + t; i < ce; i += kCT) a.item_pref[i] += all;
     if (b == G - 1 && t == 0) a.item_pref[ni] = all + s_run;
   }
-  if (coop_barrier(bar, 2ull * G, c, a.wait_ns, 5)) return;
+  if (coop_barrier(bar, 2ull * G, c, a.wait_ns, 5, a.miss_site)) return;
 
   const u32 nseg = ld_cg_u32(&c->n_seg);
   u64 touched = 0, relocated = 0, slots = 0;
@@ -933,22 +936,33 @@ sp_status store_grow_pool(sp_graph *g, Store *st, long long min_pool_slots) {
   return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
+// Chunk-owner tables sized for the stores' slots.  The new tables are
+// allocated before the old ones are released: on SP_ENOMEM the old ones
+// stay (they still cover the edge set, which did not change).
 sp_status ensure_owner_tables(sp_graph *g) {
   const long long slots = std::max(g->fwd.slots, g->rev.slots);
   const long long need = slots / kChunk + 64;
   if (need <= g->own_cap && g->qown[0]) return SP_OK;
   const long long c = std::max(need, g->own_cap * 2);
-  for (int b = 0; b < 3; ++b) g->al.put(g->qown[b], (size_t)g->own_cap * 4);
-  g->al.put(g->aown, (size_t)g->own_cap * 4);
+  u32 *p[4];
   bool ok = true;
-  for (int b = 0; b < 3; ++b) {
-    g->qown[b] = (u32 *)g->al.get((size_t)c * 4);
-    ok = ok && g->qown[b];
+  for (int b = 0; b < 4; ++b) {
+    p[b] = ok ? (u32 *)g->al.get((size_t)c * 4) : nullptr;
+    ok = ok && p[b];
   }
-  g->aown = (u32 *)g->al.get((size_t)c * 4);
+  if (!ok) {
+    for (int b = 0; b < 4; ++b) g->al.put(p[b], (size_t)c * 4);
+    return SP_ENOMEM;
+  }
+  for (int b = 0; b < 3; ++b) {
+    g->al.put(g->qown[b], (size_t)g->own_cap * 4);
+    g->qown[b] = p[b];
+  }
+  g->al.put(g->aown, (size_t)g->own_cap * 4);
+  g->aown = p[3];
   ++g->gen;
   g->own_cap = c;
-  return (ok && g->aown) ? SP_OK : SP_ENOMEM;
+  return SP_OK;
 }
 
 void launch_ctl_reset(sp_graph *g, int full, int *launches) {
@@ -958,7 +972,9 @@ void launch_ctl_reset(sp_graph *g, int full, int *launches) {
 
 int count_blocks(int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count, kCT, 0) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kExclusiveSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count, kCT, 0) != cudaSuccess ||
       per_sm < 1)
     return 0;
   return per_sm * num_sms;
@@ -984,14 +1000,17 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   a.n_items = (u32)ni;
   a.n = g->n;
   a.wait_ns = g->lim.wait_ns;
+  a.miss_site = g->lim.miss_site;
   int G = (int)std::min<long long>((ni + kCTile - 1) / kCTile, g->count_blocks);
-  if (g->loop_blocks_user > 0 && g->loop_blocks_user * 4 < G) G = g->loop_blocks_user * 4;
+  // a block share: at most that many blocks, each holding an SM alone
+  const bool share = g->loop_blocks_user > 0;
+  if (share && g->loop_blocks_user < G) G = g->loop_blocks_user;
   if (G < 1) G = 1;
   a.chunk = (u32)((ni + G - 1) / G);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kCT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = share ? kExclusiveSmem : 0;
   cfg.stream = g->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident

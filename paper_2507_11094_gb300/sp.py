@@ -74,7 +74,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32),
                 ("loop_blocks", ctypes.c_int32), ("slack", ctypes.c_float),
-                ("delta", ctypes.c_int32)]
+                ("delta", ctypes.c_int32), ("max_batch_updates", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -82,7 +82,8 @@ class RequestInfo(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("slot", ctypes.c_int32),
                 ("updates", ctypes.c_int64), ("submit_ms", ctypes.c_double),
                 ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
-                ("loaded", ctypes.c_int32)]
+                ("loaded", ctypes.c_int32), ("gpu_start_ms", ctypes.c_double),
+                ("gpu_done_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,7 +94,8 @@ class ServerStats(ctypes.Structure):
                 ("loads", ctypes.c_int64), ("evictions", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("queries", ctypes.c_int64),
                 ("updates", ctypes.c_int64), ("resident_graphs", ctypes.c_int32),
-                ("registered_graphs", ctypes.c_int32), ("recoveries", ctypes.c_int64)]
+                ("registered_graphs", ctypes.c_int32), ("recoveries", ctypes.c_int64),
+                ("restores", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +122,11 @@ SIGNATURES = {
     "sp_set_push_delta": (ctypes.c_int, [_P, _I32]),
     "sp_set_inval_switch": (ctypes.c_int, [_P, _I32]),
     "sp_set_local_rounds": (ctypes.c_int, [_P, _I32]),
+    "sp_set_schedule": (ctypes.c_int, [_P, _I32, _I32]),
+    "sp_inject_missed_arrival": (ctypes.c_int, [_P, _I32]),
+    "sp_set_dist": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_int]),
+    "sp_footprint_bound": (ctypes.c_int, [_I32, _I64, ctypes.c_float, _I64,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "sp_set_batch_graphs": (ctypes.c_int, [_P, _I32]),
     "sp_loop_counters": (ctypes.c_int, [_P, _P, _I32]),
     "sp_pr_init": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, _I32, _P]),
@@ -196,6 +203,38 @@ def _check(rc: int, what: str, h=None):
         raise SpError(rc, what)
 
 
+def _check_export_targets(g, row_off, col, w):
+    """The export writes n+1 int64 offsets and m int32 columns and weights
+    through raw device pointers: reject anything else before the call."""
+    import torch
+    m = g.m
+    want = ((row_off, torch.int64, g.n + 1, "row_off"), (col, torch.int32, max(m, 1), "col"),
+            (w, torch.int32, max(m, 1), "w"))
+    dev = torch.device("cuda", g.device)
+    for t, dt, need, name in want:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name}: a torch tensor is required")
+        if t.dtype != dt:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected {dt}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{name}: {t.numel()} elements, at least {need} needed")
+    for t, dt, need, name in want:
+        if not t.is_cuda:
+            raise ValueError(f"{name}: must be a CUDA tensor")
+        if t.device != dev:
+            raise ValueError(f"{name}: must be on the graph's device")
+    spans = []
+    for t, dt, need, name in want:
+        lo = t.data_ptr()
+        spans.append((lo, lo + need * t.element_size(), name))
+    spans.sort()
+    for (a0, a1, an), (b0, b1, bn) in zip(spans, spans[1:]):
+        if b0 < a1:
+            raise ValueError(f"{an} and {bn} overlap")
+
+
 _TORCH = None
 
 
@@ -249,10 +288,14 @@ class Graph:
     """A device-resident dynamic graph with SSSP distances (libsp handle)."""
 
     def __init__(self, n, row_off, col, w, slack: float = 0.25, stream=None,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, refuse_alloc=None):
+        """refuse_alloc: optional callable(nbytes) -> bool; True makes that
+        device allocation fail (returns NULL to the library), for tests of the
+        SP_ENOMEM paths.  It needs torch_allocator."""
         torch = _torch()
         lib = load()
         self.n = int(n)
+        self.device = torch.cuda.current_device()
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         self._alloc = None
         alloc_p = None
@@ -260,6 +303,8 @@ class Graph:
             dev = torch.cuda.current_device()
 
             def _a(ctx, size, st):
+                if refuse_alloc is not None and refuse_alloc(int(size)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(size), dev, st or 0)
                 except Exception:
@@ -404,6 +449,7 @@ class Graph:
         col[m], int32 w[m]).  noalloc=True uses sp_export_csr_noalloc, which
         allocates no device memory during the call."""
         lib = load()
+        _check_export_targets(self, row_off, col, w)
         p = [ctypes.c_void_p(t.data_ptr()) for t in (row_off, col, w)]
         if noalloc:
             rc = lib.sp_export_csr_noalloc(self._h, int(reverse), *p)
@@ -488,12 +534,13 @@ class Graph:
 
     def loop_counters(self) -> dict:
         """Loop counters of the last call (tuning aid)."""
-        out = np.zeros(12, dtype=np.int64)
-        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 12),
+        out = np.zeros(16, dtype=np.int64)
+        _check(load().sp_loop_counters(self._h, out.ctypes.data_as(ctypes.c_void_p), 16),
                "sp_loop_counters")
         keys = ("rounds_push", "local_rounds", "local_episodes", "splits", "far_moves",
                 "rounds_inval", "jumps", "local_ns", "push_ns", "timeout", "timeout_site",
-                "timeout_index")
+                "timeout_index", "pool_subrounds", "pool_entries", "pool_ns0",
+                "pool_subrounds0")
         return dict(zip(keys, (int(x) for x in out)))
 
     def last_cuda_error(self) -> str:
@@ -506,6 +553,29 @@ class Graph:
     def set_local_rounds(self, max_edges: int):
         """Frontier-edge bound of single-block push rounds (0 = off)."""
         _check(load().sp_set_local_rounds(self._h, int(max_edges)), "sp_set_local_rounds")
+
+    def set_schedule(self, small_deg: int = 8, pool_rounds: int = 0):
+        """Push schedule: small-list degree bound (thread per vertex up to it,
+        warp-wide edge chunks above) and block-local sub-rounds per grid round
+        (0 = off)."""
+        _check(load().sp_set_schedule(self._h, int(small_deg), int(pool_rounds)),
+               "sp_set_schedule")
+
+    def inject_missed_arrival(self, site: int):
+        """Test hook: block 0 skips the grid barriers of wait site 2, 4 or 5,
+        so their bounded waits run out (0 = off)."""
+        _check(load().sp_inject_missed_arrival(self._h, int(site)),
+               "sp_inject_missed_arrival")
+
+    def set_dist(self, source: int, dist, parent):
+        """Install distances and parents exported by get_dist (checked exact
+        on the device; SpError SP_EINVAL otherwise)."""
+        d = np.ascontiguousarray(dist, dtype=np.int32)
+        p = np.ascontiguousarray(parent, dtype=np.int32)
+        if d.size != self.n or p.size != self.n:
+            raise SpError(SP_EINVAL, "dist/parent sizes")
+        _check(load().sp_set_dist(self._h, int(source), d.ctypes.data_as(ctypes.c_void_p),
+                                  p.ctypes.data_as(ctypes.c_void_p), 0), "sp_set_dist")
 
     def set_limits(self, max_rounds: int = 0, wait_ns: int = 0):
         _check(load().sp_set_limits(self._h, int(max_rounds), int(wait_ns)), "sp_set_limits")
@@ -564,10 +634,10 @@ class Server:
     budget with least-recently-used eviction.  All arrays are host (numpy)."""
 
     def __init__(self, hbm_budget_bytes: int, n_slots: int = 2, loop_blocks: int = 0,
-                 slack: float = 0.25, delta: int = 0):
+                 slack: float = 0.25, delta: int = 0, max_batch_updates: int = 0):
         _torch()
         cfg = ServerConfig(int(hbm_budget_bytes), int(n_slots), int(loop_blocks),
-                           float(slack), int(delta))
+                           float(slack), int(delta), int(max_batch_updates))
         h = ctypes.c_void_p()
         _check(load().sp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sp_server_create")
         self._h = h
@@ -657,6 +727,15 @@ class Server:
         rc = load().sp_server_get_dist(self._h, int(graph), d.ctypes.data_as(ctypes.c_void_p))
         _check(rc, "sp_server_get_dist")
         return d
+
+
+def footprint_bound(n: int, m: int, slack: float = 0.25, max_updates: int = 0) -> int:
+    """Upper bound of a handle's device bytes (sp_footprint_bound)."""
+    _torch()
+    v = ctypes.c_int64()
+    _check(load().sp_footprint_bound(int(n), int(m), float(slack), int(max_updates),
+                                     ctypes.byref(v)), "sp_footprint_bound")
+    return int(v.value)
 
 
 def status_str(code: int) -> str:

@@ -485,3 +485,45 @@ def sym_rmat(scale: int = 16, edge_factor: int = 8, batch_frac: float = 0.01, se
     b = max(1, int(round(batch_frac * pairs)))
     return Workload(f"sym-rmat{scale}-ef{edge_factor}", n, ro, col, w,
                     max_out_degree_source(ro), st, 4 * b, seed)
+
+
+# --------------------------------------------- batched and serving workloads
+
+def batched_rmat(seed: int, k: int = 64):
+    """The batched form: k R-MAT graphs, scales ~U{12..18}, edge factor 16,
+    w~U[1,100], each with its own source (max out-degree) and its own batch
+    of ~U[0.5%, 5%] of its m (50/50)."""
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(12, 19, size=k)
+    fracs = rng.uniform(0.005, 0.05, size=k)
+    return [rmat(scale=int(sc), batch_frac=float(fr), seed=seed * 100 + i)
+            for i, (sc, fr) in enumerate(zip(scales, fracs))]
+
+
+def serving_graphs(seed: int, big_scale: int = 22):
+    """The serving form's graphs: 2 R-MAT graphs of scale big_scale + 6 of
+    scale ~U{16..20}, edge factor 16, w~U[1,100], each with its own source
+    (max out-degree vertex)."""
+    rng = np.random.default_rng(seed)
+    scales = [big_scale, big_scale] + [int(x) for x in rng.integers(16, 21, size=6)]
+    return [rmat(scale=sc, batch_frac=0.001, seed=seed * 100 + 50 + i)
+            for i, sc in enumerate(scales)]
+
+
+def serving_requests(ws, count: int, seed: int):
+    """`count` batches: graph uniform over ws, size log-uniform in [1e3, 1e6]
+    (at most half the graph's edges), 50/50 deletions/insertions; a query of
+    1024 random vertices of the same graph after every 4th batch.  Returns
+    (graph index, Batch, query vertices or None) triples; the graphs' batch
+    streams advance as the batches are drawn."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        gi = int(rng.integers(0, len(ws)))
+        W = ws[gi]
+        size = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        size = max(2, min(size, W.m // 2))
+        b = W.stream.next(size // 2, size - size // 2, seed=seed * 100000 + i)
+        q = (rng.integers(0, W.n, size=1024).astype(np.int32) if i % 4 == 3 else None)
+        reqs.append((gi, b, q))
+    return reqs

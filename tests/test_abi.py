@@ -117,3 +117,28 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_export_targets_are_checked_before_any_launch():
+    """export_csr_device writes through raw device pointers, so a wrong dtype,
+    a short or strided tensor, a host tensor or overlapping targets must be
+    refused in the binding, before the C call."""
+    import types
+
+    import torch
+    from paper_2507_11094_gb300 import sp
+    g = types.SimpleNamespace(n=10, m=20, device=0)
+    ok = (torch.zeros(11, dtype=torch.int64), torch.zeros(20, dtype=torch.int32),
+          torch.zeros(20, dtype=torch.int32))
+    cases = [
+        ((torch.zeros(11, dtype=torch.int32),) + ok[1:], "dtype"),
+        ((torch.zeros(10, dtype=torch.int64),) + ok[1:], "at least 11"),
+        ((ok[0], torch.zeros(19, dtype=torch.int32), ok[2]), "at least 20"),
+        ((ok[0], ok[1], torch.zeros(20, dtype=torch.float32)), "dtype"),
+        ((ok[0], torch.zeros(40, dtype=torch.int32)[::2], ok[2]), "contiguous"),
+        ((ok[0], [0] * 20, ok[2]), "torch tensor"),
+        (ok, "CUDA tensor"),
+    ]
+    for args, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            sp._check_export_targets(g, *args)

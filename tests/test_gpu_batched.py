@@ -1,5 +1,5 @@
 """Batched form on the GPU: many graphs in one handle, multi-source init,
-captured CUDA-graph replay, and the delta autotuner -- all against the
+captured CUDA-graph replay, and the schedule autotuner -- all against the
 per-graph CPU oracle."""
 import numpy as np
 import pytest
@@ -92,11 +92,29 @@ def test_autotuner_keeps_distances(torch):
     W = wl.grid(40, 40, seed=2)
     ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
     with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
-        res = autotune.tune_delta(g, lambda h, stats=False: h.sssp_init(W.source, stats=stats),
-                                  W.w, reps=1)
+        res = autotune.tune_schedule(g, lambda h, stats=False: h.sssp_init(W.source, stats=stats),
+                                     W.w, reps=1)
         assert res["delta"] in autotune.candidates(W.w)
         np.testing.assert_array_equal(g.get_dist(), ref.dijkstra(W.source))
         b = W.batch(0, dist=g.get_dist())
         g.apply(b)
         ref.apply(b)
         np.testing.assert_array_equal(g.get_dist(), ref.dijkstra(W.source))
+
+
+def test_autotuned_union_matches_each_graph_oracle(torch):
+    """The batched form with the schedule the tuner picks for the union."""
+    ws = _workloads()
+    B = batched.BatchedGraphs([(W.n, W.row_off, W.col, W.w) for W in ws],
+                              [W.source for W in ws])
+    refs = [oracle.OracleGraph(W.n, W.row_off, W.col, W.w) for W in ws]
+    res = autotune.tune_schedule(B.g, lambda h, stats=False: B.init(stats=stats),
+                                 B.packed.w, reps=1)
+    assert set(res["schedule"]) == {"delta", "pool_rounds", "small_deg", "local_edges"}
+    for k in range(2):
+        bs = [W.batch(k) for W in ws]
+        B.apply(bs)
+        for i, W in enumerate(ws):
+            refs[i].apply(bs[i])
+            np.testing.assert_array_equal(B.dist(i), refs[i].dijkstra(W.source))
+    B.close()

@@ -1,7 +1,10 @@
 """GPU tests of the serving runtime (sp_server_*): requests of several graphs
-run concurrently on worker slots, graphs are evicted and reloaded under an
-HBM budget, and every query answer equals the oracle's distances after the
-batches submitted before it on that graph."""
+run concurrently on worker slots and overlap on the device, graphs are
+evicted and reloaded under an HBM budget that the resident graphs never
+exceed (reloads restore the checkpointed distances), no repair needs a
+recovery (the slots' cooperative grids are co-resident), and every query
+answer equals the oracle's distances after the batches submitted before it
+on that graph, whatever the mix it ran in."""
 import numpy as np
 import pytest
 
@@ -72,6 +75,8 @@ def test_serving_mix_matches_oracle():
     with sp.Server(hbm_budget_bytes=8 << 30, n_slots=3) as srv:
         run_mix(srv, works, batches, dists, np.random.default_rng(1))
         st = srv.stats()
+        assert st.recoveries == 0
+        assert st.max_resident_bytes <= 8 << 30
         assert st.loads == len(works) and st.evictions == 0
         assert st.batches == 4 * len(works)
         assert st.updates == sum(b.size for bs in batches for b in bs)
@@ -96,20 +101,75 @@ def test_serving_evicts_and_reloads_under_budget():
         st = srv.stats()
         assert st.evictions > 0 and st.loads == st.evictions + st.resident_graphs
         assert st.resident_graphs < len(works)
-        assert st.resident_bytes <= budget
+        assert st.resident_bytes <= budget and st.max_resident_bytes <= budget
+        # reloads restore the checkpointed distances instead of recomputing
+        assert st.restores >= 1 and st.restores <= st.loads - len(works)
+        assert st.recoveries == 0
 
 
 def test_serving_graph_over_budget_is_refused():
+    """A graph is admitted by the upper bound of its footprint, so one that
+    could not fit alone is refused when it is registered, and a batch larger
+    than the reserved batch size is refused when it is submitted."""
     W = wl.tiny_er(1)
-    with sp.Server(hbm_budget_bytes=1 << 16, n_slots=1) as srv:
-        with pytest.raises(sp.SpError) as e:   # the lower bound alone is over
+    bound = sp.footprint_bound(W.n, W.m, 0.25, 64)
+    with sp.Server(hbm_budget_bytes=bound - 1, n_slots=1, max_batch_updates=64) as srv:
+        with pytest.raises(sp.SpError) as e:
             srv.add_graph(W.n, W.row_off, W.col, W.w, W.source)
         assert e.value.code == sp.SP_ENOMEM_BUDGET
-    with sp.Server(hbm_budget_bytes=1 << 20, n_slots=1) as srv:
+    with sp.Server(hbm_budget_bytes=bound, n_slots=1, max_batch_updates=64) as srv:
         g = srv.add_graph(W.n, W.row_off, W.col, W.w, W.source)
-        info, _ = srv.wait(srv.submit_query(g, np.arange(4)))
-        assert info.status == sp.SP_ENOMEM_BUDGET
-        assert srv.stats().resident_bytes == 0
+        with pytest.raises(sp.SpError) as e:
+            srv.submit_batch(g, np.zeros(40, np.int32), np.ones(40, np.int32),
+                             np.zeros(25, np.int32), np.ones(25, np.int32),
+                             np.ones(25, np.int32))
+        assert e.value.code == sp.SP_EINVAL
+        b = W.batch(0)
+        info, _ = srv.wait(srv.submit(g, b))
+        assert info.status == sp.SP_OK
+        st = srv.stats()
+        assert 0 < st.resident_bytes <= bound and st.max_resident_bytes <= bound
+
+
+def test_footprint_bound_holds():
+    """The bound is above what a handle holds once it has reserved its batch
+    buffers, on graphs of every kind."""
+    for W in (wl.tiny_er(2), wl.rmat(13, batch_frac=0.01, seed=3),
+              wl.grid(100, 130, batch_frac=0.01, seed=4)):
+        for slack, upd in ((0.25, 1000), (0.0, 50_000), (1.5, 10)):
+            with sp.Graph(W.n, W.row_off, W.col, W.w, slack=slack) as g:
+                g.reserve(upd)
+                held = g.info().device_bytes
+            assert held <= sp.footprint_bound(W.n, W.m, slack, upd), (W.name, slack, upd)
+
+
+def test_requests_of_different_graphs_overlap_on_the_device():
+    """Four slots, four graphs (two R-MAT, two grids), every batch submitted
+    at once: requests of different graphs on different slots run on the
+    device at the same time (their CUDA-event intervals intersect), no repair
+    needs a recovery, and the results equal the oracle's."""
+    works = [wl.rmat(14, batch_frac=0.01, seed=21), wl.rmat(15, batch_frac=0.005, seed=22),
+             wl.grid(256, 256, batch_frac=0.01, seed=23, tree_fraction=0.0),
+             wl.grid(200, 300, batch_frac=0.01, seed=24, tree_fraction=0.0)]
+    batches, dists = expected(works, 4)
+    with sp.Server(hbm_budget_bytes=16 << 30, n_slots=4) as srv:
+        gids = [srv.add_graph(W.n, W.row_off, W.col, W.w, W.source) for W in works]
+        for i in range(len(works)):      # load every graph first
+            srv.wait(srv.submit_query(gids[i], np.arange(4, dtype=np.int32)))
+        ids = [(srv.submit(gids[i], batches[i][k]), i) for k in range(4)
+               for i in range(len(works))]
+        infos = []
+        for rid, i in ids:
+            info, _ = srv.wait(rid)
+            assert info.status == sp.SP_OK
+            assert 0 <= info.gpu_start_ms <= info.gpu_done_ms
+            infos.append((i, info.slot, info.gpu_start_ms, info.gpu_done_ms))
+        overlaps = sum(1 for a in infos for b in infos
+                       if a[0] < b[0] and a[1] != b[1] and a[2] < b[3] and b[2] < a[3])
+        assert overlaps > 0, infos
+        for i, W in enumerate(works):
+            np.testing.assert_array_equal(srv.get_dist(gids[i]), dists[i][-1])
+        assert srv.stats().recoveries == 0
 
 
 def test_serving_bad_requests():
