@@ -91,7 +91,11 @@ typedef struct {
     void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
 } sp_allocator;
 
-/* Counters and timings of one sp_apply_batch (or sp_sssp_init) call. */
+/* Counters and timings of one sp_apply_batch (or sp_sssp_init) call.  The
+ * applied/absent/present counts, the affected count and the round counts
+ * report the batch; the per-phase arrays (alg_bytes, ms_phase) and the split
+ * round counts are an extension for measurement, beyond the paper's
+ * interface. */
 typedef struct {
     int64_t n_del_applied;   /* deletions of present edges                  */
     int64_t n_del_absent;    /* deletions of absent edges (no-ops)          */
@@ -150,7 +154,9 @@ sp_status sp_graph_destroy(sp_graph *g);
  * Compute distances and parents from `source` from scratch (the appendix's
  * staticSSSP: dist = INF and parent = -1 everywhere, then a fixedPoint of
  * Min relaxations seeded by the source).  Also the from-scratch comparator.
- * stats may be NULL.  SP_EINVAL if source is out of range.
+ * stats may be NULL (an extension of the boundary: per-phase timings and
+ * algorithmic bytes for the benchmark; the paper's calls have none).
+ * SP_EINVAL if source is out of range.
  */
 sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats);
 
@@ -178,8 +184,12 @@ sp_status sp_apply_batch(sp_graph *g,
 
 /*
  * Copy distances (dist[n]; SP_INF = unreachable) and, if parent != NULL,
- * parents (parent[n]; -1 for the source and unreachable vertices) out.
- * SP_ESTATE if no valid distances exist.
+ * parents (parent[n]; -1 for the source and unreachable vertices) out:
+ * the node properties dist and parent that the problem statement of Section
+ * 3.2 maintains (propNode<int> dist, propNode<node> parent of the DynSSSP
+ * program).  out_on_device: dist/parent are device arrays of the graph's
+ * device (else host memory).  The call is synchronous.  SP_ESTATE if no
+ * valid distances exist.
  */
 sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent,
                       int out_on_device);
@@ -242,9 +252,13 @@ sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off,
  *   scan's partial sums live in a fixed 512 KiB device array that every GPU
  *   loading the library holds until exit.
  *   The first call on each device looks that array's address up
- *   (cudaGetSymbolAddress); make it before any stream capture.  All calls
- *   share the array, so calls whose work overlaps on the GPU race; nothing
- *   in it needs to start at zero.
+ *   (cudaGetSymbolAddress); make it before any stream capture.  The address
+ *   is kept for the life of the process, so it does not survive a reset of
+ *   the device's primary context (cudaDeviceReset): do not call this again
+ *   on a device after such a reset.  All calls share the array, so calls
+ *   whose work overlaps on the GPU race; nothing in it needs to start at
+ *   zero.  Like sp_export_csr, the call is synchronous: it returns after its
+ *   work on the graph's stream has completed.
  */
 sp_status sp_export_csr_noalloc(sp_graph *g, int reverse, int64_t *row_off,
                                 int32_t *col, int32_t *w);

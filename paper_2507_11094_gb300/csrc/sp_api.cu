@@ -305,12 +305,15 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
   rec(g, timed, 1);
   const bool beside = mode == kInvalBeside && n_del > 0;
   g->last_beside = beside && timed;
-  sp::launch_count(g, ni, launches);
-  rec(g, timed, 2);
-  // fork: the invalidation runs beside the merge.  Not beside the count: two
-  // cooperative grids with grid barriers, side by side, could each hold SMs
-  // the other waits for; the merge has no grid barrier
-  if (beside) {
+  // fork: the invalidation runs beside the count pass and the merge once the
+  // batch is validated.  Two cooperative grids side by side are safe only if
+  // neither can hold SMs the other's blocks wait for: the invalidation's
+  // blocks each need a whole SM, so the count's grid is capped to what the
+  // other SMs hold and is resident in full whichever is placed first.  With
+  // a block share (several handles at once) the invalidation waits for the
+  // count instead, so each handle runs one cooperative grid at a time.
+  const bool share = g->loop_blocks_user > 0;
+  auto fork = [&]() {
     cudaEventRecord(g->fork_ev, g->stream);
     cudaStreamWaitEvent(g->side, g->fork_ev, 0);
     rec_side(g, timed, 0);
@@ -318,7 +321,11 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
     if (e == cudaSuccess) e = ei;
     rec_side(g, timed, 1);
     cudaEventRecord(g->join_ev, g->side);
-  }
+  };
+  if (beside && !share) fork();
+  sp::launch_count(g, ni, launches, beside && !share ? sp::inval_beside_blocks(g) : 0);
+  rec(g, timed, 2);
+  if (beside && share) fork();
   sp::launch_merge(g, ni, launches);
   rec(g, timed, 3);
   if (beside) cudaStreamWaitEvent(g->stream, g->join_ev, 0);   // join

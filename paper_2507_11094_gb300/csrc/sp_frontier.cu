@@ -417,7 +417,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // in rest[] for the global frontier.
 template <bool kMeta>
 __device__ __forceinline__ void pool_push(Pool *pl, u32 b, const u32 *x, const u32 *nd,
-                                          const bool *want, int kk, const long long *mst,
+                                          const bool *want, int kk, const u32 *ms4,
                                           const int *mdg, bool *rest, u64 &n_in,
                                           const RowMeta *row, const int2 *adj) {
   const int lane = threadIdx.x & 31;
@@ -446,12 +446,13 @@ __device__ __forceinline__ void pool_push(Pool *pl, u32 b, const u32 *x, const u
   for (int k = 0; k < K; ++k) {
     if (take[k]) {
       if (base < kPoolCap) {
-        E[base] = kMeta ? make_uint4(x[k], nd[k], (u32)(mst[k] >> 2), (u32)mdg[k])
+        E[base] = kMeta ? make_uint4(x[k], nd[k], ms4[k], (u32)mdg[k])
                         : make_uint4(x[k], nd[k], 0u, kPoolUnknown);
         // what the entry's expansion reads first: its edges (or its row)
         if (kMeta) {
-          prefetch_l2(adj + mst[k]);
-          prefetch_l2(adj + mst[k] + mdg[k] - 1);
+          const int2 *e0 = adj + ((long long)ms4[k] << 2);
+          prefetch_l2(e0);
+          prefetch_l2(e0 + mdg[k] - 1);
         } else {
           prefetch_l2(row + x[k]);
         }
@@ -540,23 +541,18 @@ __device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thre
           ed[k] = t == 0 ? ed0[k] : (e < deg ? __ldg(a.fwd.adj + start + e) : make_int2(0, 0));
         }
         if (t == 0) live = deg > 0 && dist_of(sv) == d;
-        u32 tx[K], nd[K];
-        u64 cand[kPU], old[kPU];
-        long long mst[K];
+        // per edge: target, candidate distance, the target's old state (from
+        // the atomicMin) and its row (start / 4, degree), read together
+        u32 tx[K], nd[K], ms4[K];
         int mdg[K];
-        bool act[kPU];
+        u64 old[K];
+        bool act[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          tx[k] = 0;
-          nd[k] = kInf;
-          mst[k] = 0;
-          mdg[k] = 0;
-        }
-#pragma unroll
-        for (int k = 0; k < kPU; ++k) {
-          act[k] = live && t * kPU + (u32)k < deg;
-          tx[k] = (u32)ed[k].x;
-          nd[k] = d + (u32)ed[k].y;
+          const u32 e = t * kPU + (u32)k;
+          act[k] = k < kPU && live && e < deg;
+          tx[k] = k < kPU ? (u32)ed[k < kPU ? k : 0].x : 0u;
+          nd[k] = k < kPU ? d + (u32)ed[k < kPU ? k : 0].y : kInf;
           if (act[k]) {
             ++pc.n_edges;
             if (nd[k] >= kInf) {
@@ -564,21 +560,21 @@ __device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thre
               act[k] = false;
             }
           }
-          cand[k] = pack(nd[k], v);
-          old[k] = act[k] ? atomicMin((unsigned long long *)(a.s + tx[k]), cand[k]) : 0ull;
+          old[k] = act[k] ? atomicMin((unsigned long long *)(a.s + tx[k]), pack(nd[k], v)) : 0ull;
+          ms4[k] = 0;
+          mdg[k] = 0;
           if (act[k]) {
             const int4 r = __ldg((const int4 *)(row + tx[k]));
-            mst[k] = (long long)(((u64)(u32)r.y << 32) | (u32)r.x);
+            ms4[k] = (u32)((((u64)(u32)r.y << 32) | (u32)r.x) >> 2);
             mdg[k] = r.z;
           }
         }
         bool near[K], far[K];
         u32 fmin = 0xFFFFFFFFu;
 #pragma unroll
-        for (int k = 0; k < K; ++k) near[k] = far[k] = false;
-#pragma unroll
-        for (int k = 0; k < kPU; ++k) {
-          if (act[k] && cand[k] < old[k]) {
+        for (int k = 0; k < K; ++k) {
+          near[k] = far[k] = false;
+          if (act[k] && pack(nd[k], v) < old[k]) {
             ++pc.n_imp;
             if (nd[k] < thresh) {
               near[k] = true;
@@ -589,7 +585,7 @@ __device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thre
           }
         }
         bool rest[K], want[K];
-        pool_push<true>(pl, q, tx, nd, near, kPU, mst, mdg, rest, pc.n_in, row, a.fwd.adj);
+        pool_push<true>(pl, q, tx, nd, near, kPU, ms4, mdg, rest, pc.n_in, row, a.fwd.adj);
 #pragma unroll
         for (int k = 0; k < K; ++k)
           want[k] = k < kPU && rest[k] && atomicExch(a.qflag + tx[k], tag) != tag;
@@ -2368,6 +2364,8 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
 }
 
 const void *inval_fn() { return (const void *)k_loop<kOpInval>; }
+
+int inval_beside_blocks(const sp_graph *g) { return loop_grid(g, kOpInval, 1); }
 
 cudaError_t retarget_inval(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node, const int *ds,
                            const int *dd, long long nd, int concurrent) {

@@ -241,7 +241,9 @@ sp_status store_grow_pool(sp_graph *g, sp::Store *st, long long min_pool_slots);
 sp_status ensure_owner_tables(sp_graph *g);
 void launch_ctl_reset(sp_graph *g, int full, int *launches);
 int count_blocks(int num_sms);
-void launch_count(sp_graph *g, long long n_items, int *launches);
+// the count pass; avoid_sms: SMs held by a cooperative grid running beside
+// it, which its grid must leave free to be resident in full
+void launch_count(sp_graph *g, long long n_items, int *launches, int avoid_sms = 0);
 void launch_merge(sp_graph *g, long long n_items, int *launches);
 void launch_finish(sp_graph *g, int *launches);
 // sp_sort.cu: items, sort and segments of a batch in one cooperative launch
@@ -271,6 +273,8 @@ cudaError_t launch_inval(sp_graph *g, const int *ds, const int *dd, long long nd
 // push fixedPoint; for a batch (pull != 0 or n_items > 0) its first stage
 // pulls over A and relaxes the applied insertions
 cudaError_t launch_push(sp_graph *g, int *launches, int pull = 0, long long n_items = 0);
+// blocks (one per SM) of an invalidation beside the store update
+int inval_beside_blocks(const sp_graph *g);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
 // restore of exported distances: the exactness checks (status SP_EINVAL on a
 // violation), then the packed state

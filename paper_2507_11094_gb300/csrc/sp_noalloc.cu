@@ -17,11 +17,15 @@
 // stand-in, and a kernel given it would fault or, where the GPU can reach host
 // memory, silently use the wrong memory -- so the device address is looked up
 // once per device with cudaGetSymbolAddress (the first call on each device
-// does that look-up; make that first call before any stream capture).  All
-// calls share the array: two calls whose work overlaps on the GPU (e.g. two
-// graphs exported concurrently on different streams) race on it.  The scan
-// writes every partial sum it reads, so nothing in the array has to start at
-// zero and a call never depends on what an earlier call left there.
+// does that look-up; make that first call before any stream capture).  The
+// address is cached for the life of the process; it would be stale after a
+// reset of the device's primary context, so the library is not to be used on
+// a device again after cudaDeviceReset.  All calls share the array: two
+// calls whose work overlaps on the GPU (e.g. two graphs exported
+// concurrently on different streams) race on it.  The scan writes every
+// partial sum it reads, so nothing in the array has to start at zero and a
+// call never depends on what an earlier call left there.  A call returns
+// after its work on the graph's stream has completed.
 #include <mutex>
 
 #include "sp_graph.cuh"

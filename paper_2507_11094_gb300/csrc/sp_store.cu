@@ -980,7 +980,7 @@ int count_blocks(int num_sms) {
   return per_sm * num_sms;
 }
 
-void launch_count(sp_graph *g, long long ni, int *launches) {
+void launch_count(sp_graph *g, long long ni, int *launches, int avoid_sms) {
   if (ni == 0) return;
   BatchBufs &b = g->bb;
   CountArgs a;
@@ -1005,6 +1005,13 @@ void launch_count(sp_graph *g, long long ni, int *launches) {
   // a block share: at most that many blocks, each holding an SM alone
   const bool share = g->loop_blocks_user > 0;
   if (share && g->loop_blocks_user < G) G = g->loop_blocks_user;
+  // beside a cooperative grid that holds avoid_sms whole SMs: at most what
+  // the other SMs hold, so the count is resident in full whichever grid the
+  // GPU places first
+  if (avoid_sms > 0) {
+    const int per_sm = std::max(1, g->count_blocks / std::max(1, g->num_sms));
+    G = std::min(G, per_sm * std::max(1, g->num_sms - avoid_sms));
+  }
   if (G < 1) G = 1;
   a.chunk = (u32)((ni + G - 1) / G);
   cudaLaunchConfig_t cfg = {};

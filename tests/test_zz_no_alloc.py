@@ -64,3 +64,18 @@ def test_noalloc_export_matches_regular_export_twice(torch_cuda):
         np.testing.assert_array_equal(out[0].cpu().numpy(), ro)
         np.testing.assert_array_equal(out[1].cpu().numpy()[:col.size], col)
         np.testing.assert_array_equal(out[2].cpu().numpy()[:col.size], w)
+
+
+def test_noalloc_export_above_one_scan_tile(torch_cuda):
+    """A graph of more than 2048 x 2048 vertices: the scan of the degrees
+    recurses over a second level of partial sums, still inside the fixed
+    array; two exports in a row equal the regular export."""
+    torch = torch_cuda
+    W = wl.grid(2100, 2100, batch_frac=0.001, seed=2)
+    assert W.n > 2048 * 2048
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        for reverse in (False, True):
+            ref, out = _export_pair(torch, g, reverse)
+            for a, b in zip(ref, out):
+                np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        np.testing.assert_array_equal(out[0].cpu().numpy()[-1], W.m)
