@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--serving-big-scale", type=int, default=22)
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-repeats", type=int, default=5,
+                    help="sustained phases (fresh requests each) whose rates give the "
+                         "serving line's value (median) and spread")
     return ap.parse_args()
 
 
@@ -636,12 +639,15 @@ def run_serving(args):
     t_gen = time.perf_counter()
     ws = serving_workloads(args.seed, args.serving_big_scale)
     n_req = args.serving_requests
+    reps = max(1, args.serving_repeats)
+    names = ["warm"] + [f"sustained{r}" for r in range(reps)] + ["rate0.5", "rate0.9"]
     phases = {name: serving_requests(ws, n_req // 3 if name == "warm" else n_req,
                                      args.seed * 10 + j)
-              for j, name in enumerate(("warm", "sustained", "rate0.5", "rate0.9"))}
+              for j, name in enumerate(names)}
     t_gen = time.perf_counter() - t_gen
 
-    # footprint of each graph after a large batch, measured alone
+    # what the server counts for each graph: the upper bound of its footprint
+    # with batch buffers reserved for the largest batch (1e6 updates)
     sizes = []
     with sp.Server(hbm_budget_bytes=200 << 30, n_slots=1, delta=0) as probe:
         for W in ws:
@@ -649,8 +655,7 @@ def run_serving(args):
             gid = probe.add_graph(W.n, W.row_off, W.col, W.w, W.source)
             probe.wait(probe.submit_query(gid, np.arange(4)))
             sizes.append(probe.stats().resident_bytes - before)
-    batch_buf = 160 << 20          # batch buffers of a 1e6-update batch
-    budget = int(sum(sorted(sizes)[-5:]) + 5 * batch_buf)
+    budget = int(sum(sorted(sizes)[-5:]))   # about 5 of the 8 graphs
 
     srv = sp.Server(hbm_budget_bytes=budget, n_slots=args.serving_slots, delta=0)
     gids = [srv.add_graph(W.n, W.row_off, W.col, W.w, W.source) for W in ws]
@@ -681,13 +686,25 @@ def run_serving(args):
 
     collect(submit_all(phases["warm"]))
     st0 = srv.stats().as_dict()
-    t0 = time.perf_counter()
-    sus = collect(submit_all(phases["sustained"]))
-    t_sus = time.perf_counter() - t0
-    ups = sum(sz for _, sz in sus)
-    sustained = ups / t_sus
+    rates, secs, overlap = [], [], 0
+    for r in range(reps):
+        t0 = time.perf_counter()
+        sus = collect(submit_all(phases[f"sustained{r}"]))
+        t_sus = time.perf_counter() - t0
+        ups = sum(sz for _, sz in sus)
+        rates.append(ups / t_sus)
+        secs.append(t_sus)
+        # requests of different graphs on different slots whose device work
+        # intersected in time
+        iv = [(i["graph"], i["slot"], i["gpu_start_ms"], i["gpu_done_ms"]) for i, _ in sus
+              if i["gpu_start_ms"] >= 0]
+        overlap += sum(1 for a in iv for b in iv
+                       if a[0] < b[0] and a[1] != b[1] and a[2] < b[3] and b[2] < a[3])
+    sustained = statistics.median(rates)
+    t_sus = statistics.median(secs)
     st1 = srv.stats().as_dict()
-    mean_batch = ups / n_req
+    mean_batch = sum(b.size for r in range(reps) for _, b, _ in phases[f"sustained{r}"]) / \
+        (reps * n_req)
     runs = {}
     for name, frac in (("rate0.5", 0.5), ("rate0.9", 0.9)):
         rate = frac * sustained / mean_batch           # batches per second
@@ -718,8 +735,11 @@ def run_serving(args):
                    "slots": args.serving_slots, "requests_per_phase": n_req,
                    "inputs": "host arrays copied by the server (H2D inside every request)"},
         "sustained": {"updates_per_s": sustained, "seconds": t_sus,
+                      "repeats": reps, "rates": rates, "min": min(rates), "max": max(rates),
+                      "overlapping_request_pairs": overlap,
                       "loads": st1["loads"] - st0["loads"],
-                      "evictions": st1["evictions"] - st0["evictions"]},
+                      "evictions": st1["evictions"] - st0["evictions"],
+                      "restores": st1["restores"] - st0["restores"]},
         "rates": runs,
         "server_stats": st2,
         "generation_s": t_gen,
