@@ -459,6 +459,7 @@ typedef struct {
                                   whose distances were recomputed from the source */
     int64_t restores;          /* reloads whose distances came from the
                                   checkpoint (sp_set_dist), not a recompute   */
+    double load_ms, evict_ms;  /* host time spent loading / evicting graphs  */
 } sp_server_stats;
 
 sp_status sp_server_create(const sp_server_config *cfg, sp_server **out);

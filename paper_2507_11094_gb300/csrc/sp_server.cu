@@ -78,6 +78,7 @@ struct sp_server {
   int64_t batches = 0, queries = 0, updates = 0;
   std::atomic<int64_t> recovered{0};
   int64_t restores = 0;       // reloads that restored distances (no recompute)
+  double load_ms = 0, evict_ms = 0;   // host time in loads / evictions (under mu)
   Clock::time_point t0 = Clock::now();
   cudaStream_t ref_stream = nullptr;
   cudaEvent_t ref_ev = nullptr;   // the device clock's origin for request intervals
@@ -181,8 +182,11 @@ sp_status sp_server::make_room(std::unique_lock<std::mutex> &lk, int64_t need, b
     }
     victim->busy = true;
     lk.unlock();
+    const double t_ev = now_ms();
     const sp_status rc = evict(victim);
+    const double dt_ev = now_ms() - t_ev;
     lk.lock();
+    evict_ms += dt_ev;
     if (rc == SP_OK) {
       resident -= victim->charge;
       victim->charge = 0;
@@ -228,8 +232,11 @@ void sp_server::worker(int slot) {
         max_resident = std::max(max_resident, resident);
         ++loading;
         lk.unlock();
+        const double t_ld = now_ms();
         rc = load(ge);
+        const double dt_ld = now_ms() - t_ld;
         lk.lock();
+        load_ms += dt_ld;
         --loading;
         if (rc == SP_OK) {
           resident += ge->charge - ge->bound;   // the measured size, if above the bound
@@ -466,6 +473,8 @@ sp_status sp_server_stats_get(sp_server *s, sp_server_stats *out) {
   out->resident_graphs = res;
   out->recoveries = s->recovered.load();
   out->restores = s->restores;
+  out->load_ms = s->load_ms;
+  out->evict_ms = s->evict_ms;
   return SP_OK;
 }
 

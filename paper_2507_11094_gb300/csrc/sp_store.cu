@@ -706,15 +706,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
         S.fl[q] = (unsigned char)((a.flags[i] & 3) | ((key & 1) ? 4 : 0));
       }
       __syncwarp();
+      // first staged item with col >= cj: a lane's entries rise in col, so
+      // each search starts where the lane's previous one ended; a short walk
+      // when the strip has few items (the common case), else a binary search
+      u32 lo = 0;
 #pragma unroll
       for (int t = 0; t < kStrip / 32; ++t) {
         const int j = j0 + lane + 32 * t;
         if (j < jl) {
           const u32 cj = (u32)en[t].x;
-          u32 lo = 0, hi = k;   // first staged item with col >= cj
-          while (lo < hi) {
-            const u32 mid = (lo + hi) >> 1;
-            if (S.col[mid] < cj) lo = mid + 1; else hi = mid;
+          if (k <= 16u) {
+            while (lo < k && S.col[lo] < cj) ++lo;
+          } else {
+            u32 hi = k;
+            while (lo < hi) {
+              const u32 mid = (lo + hi) >> 1;
+              if (S.col[mid] < cj) lo = mid + 1; else hi = mid;
+            }
           }
           const bool del = lo < k && S.col[lo] == cj && (S.fl[lo] & 5) == 1;
           if (!del) {

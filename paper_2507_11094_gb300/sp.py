@@ -95,7 +95,8 @@ class ServerStats(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("queries", ctypes.c_int64),
                 ("updates", ctypes.c_int64), ("resident_graphs", ctypes.c_int32),
                 ("registered_graphs", ctypes.c_int32), ("recoveries", ctypes.c_int64),
-                ("restores", ctypes.c_int64)]
+                ("restores", ctypes.c_int64), ("load_ms", ctypes.c_double),
+                ("evict_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
