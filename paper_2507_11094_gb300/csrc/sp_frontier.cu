@@ -503,6 +503,11 @@ __device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thre
       u32 deg = en.w;
       long long start = (long long)en.z << 2;
       u64 sv = 0ull;
+      if (deg != 0 && (v >= (u32)a.n ||
+                       (deg != kPoolUnknown && start + (long long)deg > a.fwd.slots))) {
+        atomicExch(&a.ctl->bad, 1);   // never expected: record and skip
+        deg = 0;
+      }
       if (deg == kPoolUnknown) {     // appended by the round's frontier expansion
         const int4 r = __ldg((const int4 *)(row + v));
         sv = ld_cg_u64(a.s + v);

@@ -129,6 +129,8 @@ struct Ctl {
   alignas(128) u64 mcnt;           // merge elements: segments << 32 | elements
   alignas(128) u32 bstrips;        // 256-entry strips of big rows
   alignas(128) u32 mpos;           // strips handed out by the merge so far
+  alignas(128) u32 sstrips;        // small rows, merged eight to a warp
+  alignas(128) u32 spos;           // groups of small rows handed out so far
   alignas(128) u32 n_seg;          // touched (dir,row) segments
   u64 pool_used[2];      // spare slots taken (fwd, rev), persistent
   u64 pool_need[2];      // demand seen by the last count pass

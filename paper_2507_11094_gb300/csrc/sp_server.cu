@@ -16,6 +16,7 @@
 // its own, so that the grids of all slots are resident together.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -44,6 +45,54 @@ struct Req {
   bool done = false;
 };
 
+// A host array for checkpoints: page-locked (cudaMallocHost) so that the
+// copies of an eviction and a reload run at full link speed, or ordinary
+// memory if page-locked memory is not to be had.  Page-locking is slow, so
+// an array keeps its memory between checkpoints of its graph (with a quarter
+// to spare for growth) and holds data only while `valid`.
+template <typename T>
+struct HostArr {
+  T *p = nullptr;
+  size_t cap = 0;
+  bool pinned = false;
+  bool valid = false;
+  HostArr() = default;
+  HostArr(const HostArr &) = delete;
+  HostArr &operator=(const HostArr &) = delete;
+  ~HostArr() { free_all(); }
+  bool empty() const { return !valid; }
+  T *data() { return p; }
+  bool alloc(size_t count) {
+    valid = false;
+    if (p && cap >= count) {
+      valid = true;
+      return true;
+    }
+    free_all();
+    const size_t want = std::max<size_t>(count + count / 4, 1);
+    if (cudaMallocHost((void **)&p, want * sizeof(T)) == cudaSuccess) {
+      pinned = true;
+    } else {
+      cudaGetLastError();
+      p = (T *)std::malloc(want * sizeof(T));
+      pinned = false;
+    }
+    cap = p ? want : 0;
+    valid = p != nullptr;
+    return valid;
+  }
+  void release() { valid = false; }   // the data is stale; the memory stays
+  void free_all() {
+    if (p) {
+      if (pinned) cudaFreeHost(p);
+      else std::free(p);
+    }
+    p = nullptr;
+    cap = 0;
+    valid = false;
+  }
+};
+
 struct GEnt {
   int32_t id = 0;
   int32_t n = 0;
@@ -51,9 +100,10 @@ struct GEnt {
   sp_graph *g = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};   // device interval of a request
-  std::vector<int64_t> ro;  // checkpoint of the edge set while not resident
-  std::vector<int32_t> col, w;
-  std::vector<int32_t> ck_dist, ck_parent;   // and of the distances (if valid)
+  HostArr<int64_t> ro;      // checkpoint of the edge set while not resident
+  HostArr<int32_t> col, w;
+  HostArr<int32_t> ck_dist, ck_parent;   // and of the distances (if valid)
+  int64_t ck_m = 0;          // edges in the checkpoint
   int64_t bound = 0;        // footprint bound of the checkpointed graph
   int64_t charge = 0;       // bytes counted in `resident` while resident
   bool busy = false;        // a worker holds it (request, load or eviction)
@@ -98,7 +148,7 @@ struct sp_server {
 // holds them (checked exact on the device), else computed from the source.
 sp_status sp_server::load(GEnt *ge) {
   sp_graph *g = nullptr;
-  const int64_t m = ge->ro.empty() ? 0 : ge->ro.back();
+  const int64_t m = ge->ck_m;
   sp_status rc = sp_graph_create(ge->n, m, ge->ro.data(), ge->col.data(), ge->w.data(), 0,
                                  cfg.slack, nullptr, ge->stream, &g);
   if (rc != SP_OK) return rc;
@@ -123,11 +173,11 @@ sp_status sp_server::load(GEnt *ge) {
   ge->g = g;
   ge->charge = std::max<int64_t>(ge->bound, info.device_bytes);
   if (restored) ++restores;
-  std::vector<int64_t>().swap(ge->ro);   // the checkpoint is stale from here on
-  std::vector<int32_t>().swap(ge->col);
-  std::vector<int32_t>().swap(ge->w);
-  std::vector<int32_t>().swap(ge->ck_dist);
-  std::vector<int32_t>().swap(ge->ck_parent);
+  ge->ro.release();   // the checkpoint is stale from here on
+  ge->col.release();
+  ge->w.release();
+  ge->ck_dist.release();
+  ge->ck_parent.release();
   return SP_OK;
 }
 
@@ -137,18 +187,15 @@ sp_status sp_server::evict(GEnt *ge) {
   int64_t m = 0;
   sp_status rc = sp_graph_num_edges(ge->g, &m);
   if (rc != SP_OK) return rc;
-  ge->ro.assign((size_t)ge->n + 1, 0);
-  ge->col.assign((size_t)std::max<int64_t>(m, 1), 0);
-  ge->w.assign((size_t)std::max<int64_t>(m, 1), 0);
+  if (!ge->ro.alloc((size_t)ge->n + 1) || !ge->col.alloc((size_t)m) || !ge->w.alloc((size_t)m))
+    return SP_ENOMEM;
   rc = sp_export_csr(ge->g, 0, ge->ro.data(), ge->col.data(), ge->w.data(), 0);
   if (rc != SP_OK) return rc;
-  ge->col.resize((size_t)m);
-  ge->w.resize((size_t)m);
-  ge->ck_dist.assign((size_t)ge->n, 0);
-  ge->ck_parent.assign((size_t)ge->n, 0);
-  if (sp_get_dist(ge->g, ge->ck_dist.data(), ge->ck_parent.data(), 0) != SP_OK) {
-    std::vector<int32_t>().swap(ge->ck_dist);   // no valid distances: recompute on load
-    std::vector<int32_t>().swap(ge->ck_parent);
+  ge->ck_m = m;
+  if (!ge->ck_dist.alloc((size_t)ge->n) || !ge->ck_parent.alloc((size_t)ge->n) ||
+      sp_get_dist(ge->g, ge->ck_dist.data(), ge->ck_parent.data(), 0) != SP_OK) {
+    ge->ck_dist.release();   // no valid distances: recompute on load
+    ge->ck_parent.release();
   }
   int64_t b = 0;
   ge->bound = sp_footprint_bound(ge->n, m, cfg.slack, cfg.max_batch_updates, &b) == SP_OK
@@ -364,9 +411,12 @@ sp_status sp_server_add_graph(sp_server *s, int32_t n, int64_t m, const int64_t 
   auto ge = std::make_unique<GEnt>();
   ge->n = n;
   ge->source = source;
-  ge->ro.assign(row_off, row_off + n + 1);
-  ge->col.assign(col, col + m);
-  ge->w.assign(w, w + m);
+  if (!ge->ro.alloc((size_t)n + 1) || !ge->col.alloc((size_t)m) || !ge->w.alloc((size_t)m))
+    return SP_ENOMEM;
+  std::copy(row_off, row_off + n + 1, ge->ro.data());
+  std::copy(col, col + m, ge->col.data());
+  std::copy(w, w + m, ge->w.data());
+  ge->ck_m = m;
   // admitted by an upper bound of its footprint, batch buffers included
   sp_status rc = sp_footprint_bound(n, m, s->cfg.slack, s->cfg.max_batch_updates, &ge->bound);
   if (rc != SP_OK) return rc;

@@ -233,6 +233,8 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->mcnt = 0;
   c->bstrips = 0;
   c->mpos = 0;
+  c->sstrips = 0;
+  c->spos = 0;
   c->n_seg = 0;
   c->pool_need[0] = c->pool_used[0];
   c->pool_need[1] = c->pool_used[1];
@@ -292,6 +294,7 @@ __device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) 
 
 struct CountArgs {
   Ctl *ctl;
+  long long strips_cap;  // small rows are listed from the end of strips
   const u64 *keys;
   const u32 *vals;
   Seg *seg;
@@ -310,8 +313,14 @@ struct CountArgs {
   u32 miss_site;         // test hook of the bounded waits (Limits::miss_site)
 };
 
-// The merge works on strips of kStrip old entries of a row, one warp each.
+// The merge works on strips of kStrip old entries of a row, one warp each,
+// and on groups of kGroup small rows (at most kSmallRow old entries and
+// kSmallItems items each), one warp per group: lane j takes entry j of every
+// row of the group.
 constexpr int kStrip = 256;
+constexpr int kGroup = 8;
+constexpr int kSmallRow = 32;
+constexpr int kSmallItems = 16;
 
 constexpr int kCT = 256;              // threads per block of the count pass
 constexpr int kCI = 4;                // items per thread per sub-tile
@@ -494,7 +503,7 @@ __global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
     const u32 si = base + t;
     bool ok = si < nseg;
     Seg sg;
-    u32 nstr = 0;
+    u32 nstr = 0, nsmall = 0;
     if (ok) {
       sg = a.seg[si];
       if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
@@ -532,18 +541,25 @@ __global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
         sg.new_cap = rm.cap;
       }
       a.seg[si] = sg;
-      nstr = rm.deg > kStrip ? (u32)((rm.deg + kStrip - 1) / kStrip) : 1u;
+      if (rm.deg <= kSmallRow && sg.end - sg.first <= (u32)kSmallItems)
+        nsmall = 1;
+      else
+        nstr = rm.deg > kStrip ? (u32)((rm.deg + kStrip - 1) / kStrip) : 1u;
       ++touched;
       slots += (u64)rm.deg + (u64)new_deg;
     }
-    {   // reserve the strips: one atomic per block
-      u32 stot;
+    {   // reserve the strips (from the front) and the small rows (from the
+        // back of the same array): one atomic each per block
+      u32 stot, smtot;
       const u32 se = block_excl_scan_u32(nstr, scratch, &stot);
+      const u32 sme = block_excl_scan_u32(nsmall, scratch, &smtot);
       if (t == 0) scratch[35] = stot ? atomicAdd(&c->bstrips, stot) : 0u;
+      if (t == 32) scratch[36] = smtot ? atomicAdd(&c->sstrips, smtot) : 0u;
       __syncthreads();
-      const u32 sb = scratch[35] + se;
+      const u32 sb = scratch[35] + se, smb = scratch[36] + sme;
       __syncthreads();
       for (u32 k = 0; k < nstr; ++k) a.strips[sb + k] = make_int2((int)si, (int)(k * kStrip));
+      if (nsmall) a.strips[a.strips_cap - 1 - smb] = make_int2((int)si, 0);
     }
   }
   block_add(del_ok, &sums[0], &c->del_applied);
@@ -568,6 +584,7 @@ struct MergeArgs {
   const Seg *seg;
   const u32 *opos;
   const int2 *strips;
+  long long strips_cap;   // small rows are listed from the end of strips
   Store st[2];
   int bits;
   u32 n_items;
@@ -628,7 +645,11 @@ struct StripItems {
   unsigned char fl[kStripItems];   // bit0 applied, bit1 present, bit2 insertion
   Seg seg[kMergeGrab];             // the grabbed strips' segments
   int2 sp[kMergeGrab];             // ... and strip records
+  u64 gpend[kGroup];               // small-row groups: applied updates of each row
+  u32 goff[kGroup + 1];            // ... and where each row's items are staged
 };
+static_assert(kGroup <= kMergeGrab && kGroup * kSmallItems <= kStripItems,
+              "a small-row group's records and items fit the warp's stage");
 
 __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
   __shared__ StripItems sitems[kThreads / 32];
@@ -775,6 +796,108 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
             dst[pos] = make_int2((int)((key >> 1) & cmask), (int)a.vals[i]);
           else bad = true;
         }
+      }
+    }
+  }
+  // Groups of small rows (at most kSmallRow old entries and kSmallItems
+  // items each): a warp merges kGroup of them at once, lane j taking old
+  // entry j of every row, so the dependent loads of eight rows are in flight
+  // together.  The placement is the strips' (prefix counts of the applied
+  // updates before each element).
+  const u32 nsmall = ld_cg_u32(&c->sstrips);
+  const u32 ngroups = (nsmall + kGroup - 1) / kGroup;
+  for (;;) {
+    u32 g0 = 0;
+    if (lane == 0) g0 = atomicAdd(&c->spos, 1u);
+    g0 = __shfl_sync(kFull, g0, 0);
+    if (g0 >= ngroups) break;
+    const u32 s0 = g0 * kGroup;
+    const u32 cnt = min(s0 + (u32)kGroup, nsmall) - s0;
+    __syncwarp();   // every lane is done with the previous group's stage
+    u32 kt = 0;
+    if ((u32)lane < cnt) {
+      const int2 q = __ldcg(a.strips + (a.strips_cap - 1 - (long long)(s0 + lane)));
+      const Seg sg = a.seg[q.x];
+      S.seg[lane] = sg;
+      kt = sg.end - sg.first;
+      S.gpend[lane] = a.item_pref[sg.end] - sg.base_pref;
+      if (sg.old_deg > kSmallRow || kt > (u32)kSmallItems) {   // never expected
+        bad = true;
+        kt = 0;
+      }
+    }
+    bad = __any_sync(kFull, bad);
+    if (bad) break;   // warp-uniform; the flag below makes the call fail
+    // where each row's items go in the stage: exclusive prefix of kt
+    {
+      const u32 inc = (u32)warp_incl_scan_u64(kt);
+      const u32 tot = __shfl_sync(kFull, inc, cnt - 1);
+      if ((u32)lane < cnt) S.goff[lane] = inc - kt;
+      if (lane == 0) S.goff[cnt] = tot;
+    }
+    __syncwarp();
+    const u32 ktot = S.goff[cnt];
+    int2 en[kGroup];
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t) {
+      en[t] = make_int2(0, 0);
+      if ((u32)t < cnt) {
+        const Seg &sg = S.seg[t];
+        if (lane < sg.old_deg) en[t] = a.st[sg.dir].adj[sg.old_start + lane];
+      }
+    }
+    for (u32 q = lane; q < ktot; q += 32) {
+      u32 t = 0;
+      while (t + 1 < cnt && S.goff[t + 1] <= q) ++t;
+      const Seg &sg = S.seg[t];
+      const u32 i = sg.first + (q - S.goff[t]);
+      const u64 key = a.keys[i];
+      S.pre[q] = a.item_pref[i] - sg.base_pref;
+      S.col[q] = (u32)((key >> 1) & cmask);
+      S.w[q] = a.vals[i];
+      S.opos[q] = a.opos[i];
+      S.fl[q] = (unsigned char)((a.flags[i] & 3) | ((key & 1) ? 4 : 0));
+    }
+    if ((u32)lane < cnt) {   // the rows' new places
+      const Seg &sg = S.seg[lane];
+      RowMeta nm;
+      nm.start = sg.dest;
+      nm.deg = sg.new_deg;
+      nm.cap = sg.new_cap;
+      a.st[sg.dir].row[sg.row] = nm;
+      a.st[sg.dir].alt[sg.row] = sg.new_alt;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t) {
+      if ((u32)t < cnt) {
+        const Seg &sg = S.seg[t];
+        if (lane < sg.old_deg) {
+          const u32 cj = (u32)en[t].x;
+          const u32 o0 = S.goff[t], o1 = S.goff[t + 1];
+          u32 lo = o0;
+          while (lo < o1 && S.col[lo] < cj) ++lo;
+          const bool del = lo < o1 && S.col[lo] == cj && (S.fl[lo] & 5) == 1;
+          if (!del) {
+            const u64 pp = lo < o1 ? S.pre[lo] : S.gpend[t];
+            const int pos = lane - (int)(u32)pp + (int)(u32)(pp >> 32);
+            if (pos >= 0 && pos < sg.new_deg) a.st[sg.dir].adj[sg.dest + pos] = en[t];
+            else bad = true;
+          }
+        }
+      }
+    }
+    for (u32 q = lane; q < ktot; q += 32) {
+      if ((S.fl[q] & 5) == 5) {   // applied insertion
+        u32 t = 0;
+        while (t + 1 < cnt && S.goff[t + 1] <= q) ++t;
+        const Seg &sg = S.seg[t];
+        const u64 pp = S.pre[q];
+        const int pos = (int)S.opos[q] + ((S.fl[q] >> 1) & 1) - (int)(u32)pp +
+                        (int)(u32)(pp >> 32);
+        if (pos >= 0 && pos < sg.new_deg)
+          a.st[sg.dir].adj[sg.dest + pos] = make_int2((int)S.col[q], (int)S.w[q]);
+        else bad = true;
       }
     }
   }
@@ -1000,6 +1123,7 @@ void launch_count(sp_graph *g, long long ni, int *launches, int avoid_sms) {
   a.item_pref = b.item_pref;
   a.opos = b.opos;
   a.strips = b.strips;
+  a.strips_cap = b.strips_cap;
   a.tab = (u64 *)b.tmp;   // the batch sort's table is free again
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
@@ -1048,6 +1172,7 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   a.seg = b.seg;
   a.opos = b.opos;
   a.strips = b.strips;
+  a.strips_cap = b.strips_cap;
   a.st[0] = g->fwd;
   a.st[1] = g->rev;
   a.bits = g->bits;
