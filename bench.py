@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20",
-                    help="rmat20 | rmat<scale> | er1k | grid<side>-<pct> (e.g. grid4096-1) "
+                    help="rmat20 | rmat<scale> | er1k | grid<side>-<pct>[u] (e.g. grid4096-1; "
+                         "u: uniform-pair insertions) "
                          "| batched64 | serving")
     ap.add_argument("--batch-pct", type=float, default=None)
     ap.add_argument("--seed", type=int, default=1)
@@ -100,9 +101,13 @@ def make_workload(name: str, seed: int, pct: float | None):
         return W, {"scale": scale, "edge_factor": 16}
     if name.startswith("grid"):
         side, p = name[4:].split("-")
+        # a trailing "u": insertions join uniform vertex pairs (a sensitivity
+        # run: long shortcuts collapse the diameter) instead of 5x5 neighbours
+        kind = "uniform" if p.endswith("u") else "local5"
+        p = p.rstrip("u")
         frac = (pct if pct is not None else float(p)) / 100.0
-        W = wl.grid(int(side), int(side), batch_frac=frac, seed=seed)
-        return W, {"rows": int(side), "cols": int(side)}
+        W = wl.grid(int(side), int(side), batch_frac=frac, seed=seed, insert_kind=kind)
+        return W, {"rows": int(side), "cols": int(side), "insertions": kind}
     raise SystemExit(f"unknown workload {name}")
 
 

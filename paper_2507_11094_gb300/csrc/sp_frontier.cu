@@ -84,8 +84,24 @@ __device__ __forceinline__ u64 ld_acquire_u64(const u64 *p) {
 // Returns whether a timeout has been raised (the same answer in every thread
 // of the block, so that loops leave in step and no __syncthreads is left
 // waiting for threads that have gone).
-__device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Limits &lim) {
+// With `src`, thread 0 also reads the next round's frontier counters once
+// the wait is over and hands them to the block in *out: one read per block
+// instead of one per warp, all of them at the same line.
+struct RoundCounts {
+  u64 q;        // next frontier: entries << 32 | edges
+  u32 ns;       // its small list
+  u32 nf, fm;   // far pile: count and smallest distance (0, ~0 without one)
+};
+struct CountSrc {
+  const u64 *q;
+  const u32 *ns, *nf, *fm;   // nf, fm null without a far pile
+};
+
+__device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Limits &lim,
+                                          const CountSrc *src = nullptr,
+                                          RoundCounts *out = nullptr) {
   __shared__ int s_stop;
+  __shared__ RoundCounts s_rc;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -110,8 +126,15 @@ __device__ __forceinline__ bool grid_sync(u64 *bar, u64 target, Ctl *c, const Li
       }
     }
     s_stop = ld_cg_i32(&c->timeout) != 0;
+    if (src) {
+      s_rc.q = ld_cg_u64(src->q);
+      s_rc.ns = ld_cg_u32(src->ns);
+      s_rc.nf = src->nf ? ld_cg_u32(src->nf) : 0u;
+      s_rc.fm = src->fm ? ld_cg_u32(src->fm) : 0xFFFFFFFFu;
+    }
   }
   __syncthreads();
+  if (src) *out = s_rc;
   return s_stop != 0;
 }
 
@@ -153,19 +176,20 @@ __device__ __forceinline__ bool stage_reserve(Stage *st, u32 cnt, u32 &pos) {
   return false;
 }
 
-// Append up to K vertices per lane to queue q (warp-collective).  A vertex
-// with 1..q.small edges goes to the small list; a larger one reserves deg
-// slots of the queue's edge space, and the chunk-owner table gets its slot
-// for every chunk whose first edge falls in that range.  With block stages
-// the vertices wait there and are published when the block flushes.
-__device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, const u32 *x,
-                                        const bool *want, int kk, u64 &n_enq) {
+// Append up to K vertices per lane to queue q (warp-collective), given
+// their out-degrees (0: not appended).  A vertex with 1..q.small edges goes
+// to the small list; a larger one reserves deg slots of the queue's edge
+// space, and the chunk-owner table gets its slot for every chunk whose first
+// edge falls in that range.  With block stages the vertices wait there and
+// are published when the block flushes.
+__device__ __forceinline__ void enqueue_d(const Queue &q, const u32 *x, const int *dk, int kk,
+                                          u64 &n_enq) {
   const int lane = threadIdx.x & 31;
   int d[K];
   u32 cnt = 0, sum = 0, scount = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    d[k] = (k < kk && want[k]) ? __ldg(&row[x[k]].deg) : 0;
+    d[k] = k < kk ? dk[k] : 0;
     if (d[k] > (int)q.small) {
       ++cnt;
       sum += (u32)d[k];
@@ -229,6 +253,15 @@ __device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, cons
       eb += (u32)d[k];
     }
   }
+}
+
+// The same, reading the out-degree of every wanted vertex.
+__device__ __forceinline__ void enqueue(const Queue &q, const RowMeta *row, const u32 *x,
+                                        const bool *want, int kk, u64 &n_enq) {
+  int d[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d[k] = (k < kk && want[k]) ? __ldg(&row[x[k]].deg) : 0;
+  enqueue_d(q, x, d, kk, n_enq);
 }
 
 // Block scan helper: exclusive prefix of one value per thread; the block
@@ -675,9 +708,22 @@ struct PushOp {
         }
       }
     }
+    // Frontier rounds issue the dedupe exchange of a near candidate and the
+    // read of its out-degree together with its atomicMin, not after it.  A
+    // candidate below the distance read this round that loses its atomicMin
+    // lost to an improvement made this round, whose own candidate is smaller,
+    // so also near and exchanged: whichever exchange comes first enqueues the
+    // vertex, which is then enqueued exactly when it was improved.
+    bool spec[K];
+    u32 ex[K];
+    int dg[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K; ++k) {
+      spec[k] = pool == nullptr && tried[k] && nd[k] < thresh;
       old[k] = tried[k] ? atomicMin((unsigned long long *)(s + ed[k].x), cand[k]) : 0ull;
+      ex[k] = spec[k] ? atomicExch(qflag + ed[k].x, tag) : tag;
+      dg[k] = spec[k] ? __ldg(&row[tx[k]].deg) : 0;
+    }
     bool pw[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -686,8 +732,9 @@ struct PushOp {
         ++n_imp;
         if (nd[k] >= thresh) far[k] = atomicExch(ftag + ed[k].x, phase) != phase;
         else if (pool) pw[k] = true;
-        else want[k] = atomicExch(qflag + ed[k].x, tag) != tag;
       }
+      want[k] = spec[k] && ex[k] != tag;
+      if (!want[k]) dg[k] = 0;
     }
     if (pool) {
       bool rest[K];
@@ -699,7 +746,8 @@ struct PushOp {
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (far[k] && nd[k] < fmin) fmin = nd[k];
-    enqueue(next, row, tx, want, K, n_enq);
+    if (pool) enqueue(next, row, tx, want, K, n_enq);
+    else enqueue_d(next, tx, dg, K, n_enq);
     if (pile) far_append(pile, pcnt, far_min, fst, tx, far, K, fmin);
   }
 };
@@ -841,24 +889,28 @@ struct PullOp {
     bool imp[K], want[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) cur[k] = has[k] ? ld_cg_u64(s + cv[k]) : 0ull;
+    // the exchange and the out-degree read go with the atomicMin, as in the
+    // push rounds: a candidate that loses its atomicMin lost to a smaller one
+    // of this stage, which exchanges too
+    u32 pr[K];
+    int dg[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       has[k] = has[k] && cb[k] < cur[k];
       old[k] = has[k] ? atomicMin((unsigned long long *)(s + cv[k]), cb[k]) : 0ull;
+      pr[k] = has[k] ? atomicExch(qflag + cv[k], tag) : tag;
+      dg[k] = has[k] ? __ldg(&row[cv[k]].deg) : 0;
     }
     u32 mind = kInf;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       imp[k] = has[k] && cb[k] < old[k];
       if (imp[k] && dist_of(cb[k]) < mind) mind = dist_of(cb[k]);
+      want[k] = has[k] && pr[k] != tag;
+      if (!want[k]) dg[k] = 0;
     }
     if (mind < kInf) atomicMin(seed_min, mind);
-    u32 pr[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) pr[k] = imp[k] ? atomicExch(qflag + cv[k], tag) : tag;
-#pragma unroll
-    for (int k = 0; k < K; ++k) want[k] = imp[k] && pr[k] != tag;
-    enqueue(next, row, cv, want, K, n_enq);
+    enqueue_d(next, cv, dg, K, n_enq);
   }
 };
 
@@ -1568,10 +1620,13 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
   // writes it back, after the last barrier)
   const u32 tag0 = ld_cg_u32(&c->epoch);
   const u32 phase0 = ld_cg_u32(&c->phase);
-  target += gridDim.x;
-  bool stop = grid_sync(bar, target, c, a.lim);
-
   const bool nf = kPushOp && a.lim.delta > 0;
+  target += gridDim.x;
+  RoundCounts rc;
+  CountSrc csrc{qcnt_ptr(c, 0), scnt_ptr(c, 0), nf ? fcnt_ptr(c, 0) : nullptr,
+                nf ? fmin_ptr(c, 0) : nullptr};
+  bool stop = grid_sync(bar, target, c, a.lim, &csrc, &rc);
+
   u32 thresh = 0xFFFFFFFFu;
   if (nf) {
     const u32 sm = ld_cg_u32(&c->seed_min);
@@ -1592,9 +1647,9 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
       capped = true;
       break;
     }
-    const u64 q = snap ? snap_q : ld_cg_u64(qcnt_ptr(c, cur));
+    const u64 q = snap ? snap_q : rc.q;
     const u32 ne = (u32)(q >> 32), nedge = (u32)q;
-    const u32 nsmall = snap ? snap_sn : ld_cg_u32(scnt_ptr(c, cur));
+    const u32 nsmall = snap ? snap_sn : rc.ns;
     const bool from_snap = snap;
     snap = false;
     const u32 sgroups = (nsmall + 31) / 32;
@@ -1629,10 +1684,10 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
       continue;
     }
     if (items == 0) {
-      if (nf) n_far = from_snap ? snap_fn : ld_cg_u32(fcnt_ptr(c, f));
+      if (nf) n_far = from_snap ? snap_fn : rc.nf;
       if (n_far == 0) break;                       // fixed point reached
       split = true;
-      const u32 fm = from_snap ? snap_fm : ld_cg_u32(fmin_ptr(c, f));
+      const u32 fm = from_snap ? snap_fm : rc.fm;
       thresh = sat_add(thresh > fm ? thresh : fm, a.lim.delta);
     }
     const u32 nxt = next3(cur);
@@ -1745,7 +1800,9 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
     cur = nxt;
     ++round;
     target += gridDim.x;
-    stop = grid_sync(bar, target, c, a.lim);
+    csrc = CountSrc{qcnt_ptr(c, cur), scnt_ptr(c, cur), nf ? fcnt_ptr(c, f) : nullptr,
+                    nf ? fmin_ptr(c, f) : nullptr};
+    stop = grid_sync(bar, target, c, a.lim, &csrc, &rc);
   }
   if (OP == kOpInval && jump) {
     const JumpState js = jump_phase(a, bar, target, scratch, &sf);
@@ -1892,6 +1949,7 @@ __device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *s
     const long long i = base + lane;
     bool want[K] = {};
     u32 v[K] = {};
+    int dg[K] = {};
     if (i < nfw) {
       const u64 key = a.keys[i];
       const unsigned char fl = a.flags[i];
@@ -1909,17 +1967,20 @@ __device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *s
           } else {
             const u64 cand = pack(nd, u);
             if (cand < sv) {
+              // exchange and out-degree with the atomicMin (a candidate that
+              // loses it lost to a smaller insertion of this stage, which
+              // exchanges too)
               const u64 old = atomicMin((unsigned long long *)(a.s + v[0]), cand);
-              if (cand < old) {
-                atomicMin(&c->seed_min, nd);
-                want[0] = atomicExch(a.qflag + v[0], tag) != tag;
-              }
+              want[0] = atomicExch(a.qflag + v[0], tag) != tag;
+              dg[0] = __ldg(&a.fwd.row[v[0]].deg);
+              if (cand < old) atomicMin(&c->seed_min, nd);
+              if (!want[0]) dg[0] = 0;
             }
           }
         }
       }
     }
-    enqueue(q0, a.fwd.row, v, want, 1, n_enq);
+    enqueue_d(q0, v, dg, 1, n_enq);
   }
   // published by the caller, together with the cut list's
   u64 q = warp_sum(n_enq);

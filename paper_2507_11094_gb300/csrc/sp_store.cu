@@ -10,6 +10,7 @@
 // DynSSSP driver in one pass).  A row that outgrows its capacity moves to a
 // spare pool at the end of the slot array.
 #include <algorithm>
+#include <cstddef>
 
 #include "sp_graph.cuh"
 
@@ -28,35 +29,6 @@ inline unsigned blocks_for(long long work, int per_block, int cap) {
 }
 
 __device__ __forceinline__ void set_status(Ctl *c, int st) { atomicCAS(&c->status, 0, st); }
-
-__device__ __forceinline__ u32 warp_incl_scan_u32(u32 x) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
-
-// Exclusive prefix of one value per thread over the block (smem scratch of
-// 32 words); the block total goes to *total.
-__device__ __forceinline__ u32 block_excl_scan_u32(u32 x, u32 *scratch, u32 *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const u32 incl = warp_incl_scan_u32(x);
-  if (lane == 31) scratch[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    u32 v = lane < nwarps ? scratch[lane] : 0u;
-    v = warp_incl_scan_u32(v);
-    if (lane < nwarps) scratch[lane] = v;
-  }
-  __syncthreads();
-  const u32 r = (warp ? scratch[warp - 1] : 0u) + incl - x;
-  *total = scratch[nwarps - 1];
-  __syncthreads();
-  return r;
-}
 
 // Add per-thread counters into global ones with one atomic per block.
 __device__ __forceinline__ void block_add(u64 v, u64 *sm, u64 *global) {
@@ -282,16 +254,6 @@ __global__ void k_check_batch(const int *__restrict__ ds, const int *__restrict_
 // --------------------------------------------------------------------------
 
 
-// First slot j in [0, deg) of a sorted row with row[j].x >= c.
-__device__ __forceinline__ int row_lower_bound(const int2 *row, int deg, int c) {
-  int lo = 0, hi = deg;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (__ldg(&row[mid].x) < c) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 struct CountArgs {
   Ctl *ctl;
   long long strips_cap;  // small rows are listed from the end of strips
@@ -324,6 +286,10 @@ constexpr int kSmallItems = 16;
 
 constexpr int kCT = 256;              // threads per block of the count pass
 constexpr int kCI = 4;                // items per thread per sub-tile
+constexpr int kCS = 4;                // touched rows per thread and pass (third step)
+static_assert(offsetof(Seg, first) == 0 && offsetof(Seg, end) == 4 && offsetof(Seg, row) == 8 &&
+                  offsetof(Seg, dir) == 12 && alignof(Seg) == 8 && sizeof(Seg) % 8 == 0,
+              "the count pass reads a Seg's first four fields as two 8-byte words");
 constexpr int kCTile = kCT * kCI;
 
 __device__ __forceinline__ u64 warp_incl_scan_u64(u64 x) {
@@ -372,7 +338,7 @@ __device__ __forceinline__ u64 block_excl_scan_u64(u64 x, u64 *ws, u64 *total) {
 //     the spare pool when the row outgrows its capacity), and the row's
 //     strips of kStrip old entries (one strip for a row with fewer), the
 //     merge's units.
-__global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
+__global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
   __shared__ u32 scratch[40];
   __shared__ u64 ws64[kCT / 32];
   __shared__ u64 s_run;
@@ -499,67 +465,105 @@ __global__ void __launch_bounds__(kCT) k_count(CountArgs a) {
 
   const u32 nseg = ld_cg_u32(&c->n_seg);
   u64 touched = 0, relocated = 0, slots = 0;
-  for (u32 base = b * kCT; base < nseg; base += G * kCT) {
-    const u32 si = base + t;
-    bool ok = si < nseg;
-    Seg sg;
-    u32 nstr = 0, nsmall = 0;
-    if (ok) {
-      sg = a.seg[si];
-      if (sg.first >= sg.end || sg.end > a.n_items || sg.row < 0 || sg.row >= a.n ||
-          sg.dir < 0 || sg.dir > 1) {  // never expected: record and skip
-        atomicExch(&c->bad, 1);
-        ok = false;
+  // kCS segments per thread, their loads in flight together: the grid holds
+  // kCT * kCS segments per block and at least one item per segment, so a
+  // batch normally needs one pass
+  for (u32 base = b * kCT * kCS; base < nseg; base += G * kCT * kCS) {
+    u32 f[kCS], e[kCS];
+    int row[kCS], dir[kCS];
+    bool ok[kCS];
+#pragma unroll
+    for (int j = 0; j < kCS; ++j) {
+      const u32 si = base + (u32)j * kCT + t;
+      ok[j] = si < nseg;
+      f[j] = e[j] = 0;
+      row[j] = dir[j] = 0;
+      if (ok[j]) {
+        // first, end, row, dir: two 8-byte loads (a Seg is 8-byte aligned)
+        const int2 *hp = (const int2 *)(a.seg + si);
+        const int2 h0 = __ldcg(hp), h1 = __ldcg(hp + 1);
+        f[j] = (u32)h0.x;
+        e[j] = (u32)h0.y;
+        row[j] = h1.x;
+        dir[j] = h1.y;
+        if (f[j] >= e[j] || e[j] > a.n_items || row[j] < 0 || row[j] >= a.n || dir[j] < 0 ||
+            dir[j] > 1) {  // never expected: record and skip
+          atomicExch(&c->bad, 1);
+          ok[j] = false;
+        }
       }
     }
-    if (ok) {
-      const Store &st = a.st[sg.dir];
-      const RowMeta rm = st.row[sg.row];
-      const u64 pf = __ldcg(a.item_pref + sg.first);
-      const u64 p = __ldcg(a.item_pref + sg.end) - pf;
-      const int new_deg = rm.deg - (int)(u32)p + (int)(u32)(p >> 32);
-      sg.old_start = rm.start;
-      sg.old_deg = rm.deg;
+    RowMeta rm[kCS];
+    u64 pf[kCS], pe[kCS], key[kCS];
+#pragma unroll
+    for (int j = 0; j < kCS; ++j) {
+      rm[j].start = 0;
+      rm[j].deg = rm[j].cap = 0;
+      pf[j] = pe[j] = key[j] = 0;
+      if (ok[j]) {
+        rm[j] = a.st[dir[j]].row[row[j]];
+        pf[j] = __ldcg(a.item_pref + f[j]);
+        pe[j] = __ldcg(a.item_pref + e[j]);
+        key[j] = a.keys[f[j]];
+      }
+    }
+    u32 nstr[kCS], nsmall[kCS];
+    u64 want = 0;   // this thread's strips (low word) and small rows (high word)
+#pragma unroll
+    for (int j = 0; j < kCS; ++j) {
+      nstr[j] = nsmall[j] = 0;
+      if (!ok[j]) continue;
+      const Store &st = a.st[dir[j]];
+      const u64 p = pe[j] - pf[j];
+      const int new_deg = rm[j].deg - (int)(u32)p + (int)(u32)(p >> 32);
+      Seg &sg = a.seg[base + (u32)j * kCT + t];
+      sg.old_start = rm[j].start;
+      sg.old_deg = rm[j].deg;
       sg.new_deg = new_deg;
       sg.pad = 0;
-      sg.prefix = a.keys[sg.first] & ~((2ull << a.bits) - 1);
-      sg.base_pref = pf;
-      if (new_deg > rm.cap) {
+      sg.prefix = key[j] & ~((2ull << a.bits) - 1);
+      sg.base_pref = pf[j];
+      if (new_deg > rm[j].cap) {
         long long nc = row_capacity(new_deg, a.slack);
-        const long long dbl = round_up4(2LL * rm.cap);
+        const long long dbl = round_up4(2LL * rm[j].cap);
         if (dbl > nc) nc = dbl;
-        const u64 off = atomicAdd(&c->pool_need[sg.dir], (u64)(2 * nc));
+        const u64 off = atomicAdd(&c->pool_need[dir[j]], (u64)(2 * nc));
         if ((long long)(off + 2 * nc) > st.slots - st.main_slots)
-          atomicOr(&c->need_grow, sg.dir ? kGrowPoolRev : kGrowPoolFwd);
+          atomicOr(&c->need_grow, dir[j] ? kGrowPoolRev : kGrowPoolFwd);
         sg.dest = st.main_slots + (long long)off;
-        sg.new_alt = sg.dest + nc;
+        sg.new_alt = st.main_slots + (long long)off + nc;
         sg.new_cap = (int)nc;
         ++relocated;
       } else {
-        sg.dest = st.alt[sg.row];
-        sg.new_alt = rm.start;
-        sg.new_cap = rm.cap;
+        sg.dest = st.alt[row[j]];
+        sg.new_alt = rm[j].start;
+        sg.new_cap = rm[j].cap;
       }
-      a.seg[si] = sg;
-      if (rm.deg <= kSmallRow && sg.end - sg.first <= (u32)kSmallItems)
-        nsmall = 1;
+      if (rm[j].deg <= kSmallRow && e[j] - f[j] <= (u32)kSmallItems)
+        nsmall[j] = 1;
       else
-        nstr = rm.deg > kStrip ? (u32)((rm.deg + kStrip - 1) / kStrip) : 1u;
+        nstr[j] = rm[j].deg > kStrip ? (u32)((rm[j].deg + kStrip - 1) / kStrip) : 1u;
+      want += (u64)nstr[j] | ((u64)nsmall[j] << 32);
       ++touched;
-      slots += (u64)rm.deg + (u64)new_deg;
+      slots += (u64)rm[j].deg + (u64)new_deg;
     }
     {   // reserve the strips (from the front) and the small rows (from the
-        // back of the same array): one atomic each per block
-      u32 stot, smtot;
-      const u32 se = block_excl_scan_u32(nstr, scratch, &stot);
-      const u32 sme = block_excl_scan_u32(nsmall, scratch, &smtot);
+        // back of the same array): one scan and one atomic each per block
+      u64 tot;
+      const u64 ex = block_excl_scan_u64(want, ws64, &tot);
+      const u32 stot = (u32)tot, smtot = (u32)(tot >> 32);
       if (t == 0) scratch[35] = stot ? atomicAdd(&c->bstrips, stot) : 0u;
       if (t == 32) scratch[36] = smtot ? atomicAdd(&c->sstrips, smtot) : 0u;
       __syncthreads();
-      const u32 sb = scratch[35] + se, smb = scratch[36] + sme;
+      u32 sb = scratch[35] + (u32)ex, smb = scratch[36] + (u32)(ex >> 32);
       __syncthreads();
-      for (u32 k = 0; k < nstr; ++k) a.strips[sb + k] = make_int2((int)si, (int)(k * kStrip));
-      if (nsmall) a.strips[a.strips_cap - 1 - smb] = make_int2((int)si, 0);
+#pragma unroll
+      for (int j = 0; j < kCS; ++j) {
+        const int si = (int)(base + (u32)j * kCT + t);
+        for (u32 k = 0; k < nstr[j]; ++k) a.strips[sb + k] = make_int2(si, (int)(k * kStrip));
+        sb += nstr[j];
+        if (nsmall[j]) a.strips[a.strips_cap - 1 - smb++] = make_int2(si, 0);
+      }
     }
   }
   block_add(del_ok, &sums[0], &c->del_applied);
@@ -595,26 +599,6 @@ __device__ __forceinline__ bool merge_enabled(Ctl *c) {
          ld_cg_i32(&c->bad) == 0;
 }
 
-// First index p in [lo, hi) with a[p] >= x (hi if none) in a non-decreasing
-// array.  The whole warp searches together: each step probes 32 evenly
-// spaced entries at once, so a range of R entries takes ceil(log32 R)
-// dependent loads instead of log2 R.  Warp-uniform arguments and result.
-__device__ __forceinline__ u32 warp_lower_bound(const u32 *__restrict__ a, u32 lo, u32 hi,
-                                                u32 x) {
-  const u32 lane = threadIdx.x & 31;
-  while (hi > lo) {
-    const u32 step = (hi - lo + 31) / 32;
-    const u32 q = lo + (lane + 1) * step - 1;
-    const bool less = q < hi && __ldg(a + q) < x;
-    const u32 t = __popc(__ballot_sync(kFull, less));
-    const u32 qt = lo + (t + 1) * step - 1;   // lane t's probe, if it had one
-    const u32 nhi = (t < 32 && qt < hi) ? qt : hi;
-    lo += t * step;
-    hi = nhi;
-  }
-  return lo;
-}
-
 // The merged row holds the kept old entries and the applied insertions in
 // col order, so every element knows its output slot from prefix counts:
 //   old entry j (col c):   j - #applied deletions with col < c
@@ -629,12 +613,12 @@ __device__ __forceinline__ u32 warp_lower_bound(const u32 *__restrict__ a, u32 l
 // One warp per strip of kStrip old entries.  The strip owns the items with
 // opos in [j0, jl) (the last strip also those past the end), so every item
 // of the row belongs to exactly one strip, and every item of an earlier
-// strip has a smaller col than every old entry of this one.  The warp loads
-// its old entries (eight coalesced 256-byte loads), finds its item range
-// with two warp-wide searches (none for a row of one strip), stages the
-// items in shared memory, and places both from there: the dependent global
-// loads per strip are the strip record, the row's segment, the searches and
-// one round of item loads.
+// strip has a smaller col than every old entry of this one.  A warp takes
+// kMergeGrab strips at a time and finds all their item ranges at once (one
+// lane per range end, binary searches in lockstep; none for a row of one
+// strip).  Per strip it loads its old entries (eight coalesced 256-byte
+// loads), stages its items in shared memory, and places both from there:
+// the dependent global loads per strip are one round of item loads.
 constexpr int kStripItems = 128;   // items staged per warp
 constexpr int kMergeGrab = 8;      // strips a warp takes at a time
 struct StripItems {
@@ -645,6 +629,8 @@ struct StripItems {
   unsigned char fl[kStripItems];   // bit0 applied, bit1 present, bit2 insertion
   Seg seg[kMergeGrab];             // the grabbed strips' segments
   int2 sp[kMergeGrab];             // ... and strip records
+  u32 ilo[kMergeGrab], ihi[kMergeGrab];   // ... their item ranges
+  u64 pend[kMergeGrab];            // ... and applied updates before their range's end
   u64 gpend[kGroup];               // small-row groups: applied updates of each row
   u32 goff[kGroup + 1];            // ... and where each row's items are staged
 };
@@ -681,6 +667,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
         S.seg[lane] = a.seg[q.x];
       }
       __syncwarp();
+      // the grabbed strips' item ranges: lane l < ng finds the first item of
+      // strip l, lane kMergeGrab + l its end, every binary search in lockstep
+      // with the others (a row of one strip needs none)
+      const u32 ng = gend - grab;
+      if (lane < 2 * kMergeGrab) {
+        const u32 l = (u32)lane & (kMergeGrab - 1);
+        const bool hi_q = lane >= kMergeGrab;
+        u32 r = 0;
+        if (l < ng) {
+          const Seg &sq = S.seg[l];
+          const int jb = S.sp[l].y + (hi_q ? kStrip : 0);
+          u32 lo = sq.first, hi = sq.end;
+          if (jb <= 0) hi = lo;                 // the row's first strip starts at its first item
+          else if (jb >= sq.old_deg) lo = hi;   // its last strip ends at its last
+          while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            if (__ldg(a.opos + mid) < (u32)jb) lo = mid + 1; else hi = mid;
+          }
+          r = lo;
+          if (hi_q) S.ihi[l] = r; else S.ilo[l] = r;
+        }
+        if (hi_q && l < ng) S.pend[l] = a.item_pref[r] - S.seg[l].base_pref;
+      }
+      __syncwarp();
     }
     const u32 sidx = grab++;
     const int2 sp = S.sp[sidx - g0];
@@ -712,10 +722,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge(MergeArgs a) {
       st.row[sg.row] = nm;
       st.alt[sg.row] = sg.new_alt;
     }
-    const u32 ilo = j0 > 0 ? warp_lower_bound(a.opos, sg.first, sg.end, (u32)j0) : sg.first;
-    const u32 ihi = jl < sg.old_deg ? warp_lower_bound(a.opos, ilo, sg.end, (u32)jl) : sg.end;
+    const u32 ilo = S.ilo[sidx - g0], ihi = S.ihi[sidx - g0];
     const u32 k = ihi - ilo;
-    const u64 pend = a.item_pref[ihi] - sg.base_pref;
+    const u64 pend = S.pend[sidx - g0];
     if (k <= (u32)kStripItems) {
       for (u32 q = lane; q < k; q += 32) {
         const u32 i = ilo + q;

@@ -371,8 +371,8 @@ def grid(rows: int = 4096, cols: int = 4096, batch_frac: float = 0.01,
     st = BatchStream(n, row_off, col, w, 1, 1000, insert_kind,
                      grid_shape=(rows, cols))
     b = max(2, int(round(batch_frac * col.size)))
-    return Workload(f"grid{rows}x{cols}", n, row_off, col, w, 0, st, b, seed,
-                    tree_fraction=tree_fraction)
+    name = f"grid{rows}x{cols}" + ("" if insert_kind == "local5" else f"-{insert_kind}")
+    return Workload(name, n, row_off, col, w, 0, st, b, seed, tree_fraction=tree_fraction)
 
 
 # --------------------------------------------------------------------------
