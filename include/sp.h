@@ -174,7 +174,11 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats);
  * Requires a prior successful sp_sssp_init (else SP_ESTATE).  SP_EINVAL (ids
  * out of range, w outside [1, SP_WMAX], negative counts) leaves the graph
  * unchanged.  stats may be NULL; with stats the call also records per-phase
- * CUDA events.
+ * CUDA events.  inputs_on_device = 0: host arrays; page-locked arrays that
+ * are mapped into the device's address space (cudaHostAlloc, pinned tensors)
+ * are read in place by the kernels over the host link, any other host array
+ * is first copied to device staging buffers.  The call is synchronous, so
+ * the arrays may be reused once it returns.
  */
 sp_status sp_apply_batch(sp_graph *g,
                          int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
@@ -188,8 +192,9 @@ sp_status sp_apply_batch(sp_graph *g,
  * the node properties dist and parent that the problem statement of Section
  * 3.2 maintains (propNode<int> dist, propNode<node> parent of the DynSSSP
  * program).  out_on_device: dist/parent are device arrays of the graph's
- * device (else host memory).  The call is synchronous.  SP_ESTATE if no
- * valid distances exist.
+ * device (else host memory; page-locked, mapped host arrays are written in
+ * place by the kernel, others through a device buffer and a copy).  The call
+ * is synchronous.  SP_ESTATE if no valid distances exist.
  */
 sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent,
                       int out_on_device);

@@ -368,6 +368,19 @@ sp_status restore_after(sp_graph *g, bool touched, sp_status rc) {
   return rc;
 }
 
+// The device address of a page-locked host array that is mapped into the
+// device's address space (cudaHostAlloc, torch's pinned memory), or nullptr
+// for any other pointer.  Kernels read and write such arrays in place over
+// the host link (NVLink-C2C on Grace machines), with no staging copy.
+const void *mapped_host(const void *p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Buffers big enough for an asynchronous batch of ni items?
 bool reserved_for(const sp_graph *g, long long ni) {
   const sp::BatchBufs &b = g->bb;
@@ -713,12 +726,35 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   g->last_na = n_add;
   g->last_timed = (int)timed;
   const bool use_graph = g->batch_graphs && g->stream && nb > 0 && repeat;
-  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
+  const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
+  // host arrays in page-locked, mapped memory are read in place by the
+  // kernels; any other host array is copied to the staging buffers first
+  bool in_place = false;
+  if (!inputs_on_device) {
+    const void *m[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    in_place = true;
+    if (n_del) {
+      m[0] = mapped_host(del_src);
+      m[1] = mapped_host(del_dst);
+      in_place = m[0] && m[1];
+    }
+    if (n_add && in_place) {
+      m[2] = mapped_host(add_src);
+      m[3] = mapped_host(add_dst);
+      m[4] = mapped_host(add_w);
+      in_place = m[2] && m[3] && m[4];
+    }
+    if (in_place) {
+      ds = (const int *)m[0]; dd = (const int *)m[1];
+      as = (const int *)m[2]; ad = (const int *)m[3]; aw = (const int *)m[4];
+    }
+  }
+  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device || in_place
+                                                 ? 0 : std::max(n_del, n_add));
   if (rc != SP_OK) return rc;
   auto &b = g->bb;
-  const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
   rec(g, timed, 0);
-  if (!inputs_on_device) {
+  if (!inputs_on_device && !in_place) {
     cudaStream_t s = g->stream;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice
                                                  : cudaMemcpyHostToDevice;
@@ -1403,8 +1439,13 @@ sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_de
   if (!g || !dist) return SP_EINVAL;
   if (g->state != 1) return SP_ESTATE;
   int launches = 0;
+  // a page-locked, mapped host destination is written in place
+  int32_t *mdist = out_on_device ? nullptr : (int32_t *)mapped_host(dist);
+  int32_t *mparent = out_on_device || !parent ? nullptr : (int32_t *)mapped_host(parent);
   if (out_on_device) {
     sp::launch_unpack(g, dist, parent, &launches);
+  } else if (mdist && (!parent || mparent)) {
+    sp::launch_unpack(g, mdist, mparent, &launches);
   } else {
     sp::launch_unpack(g, g->out_dist, parent ? g->out_parent : nullptr, &launches);
     cudaMemcpyAsync(dist, g->out_dist, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream);

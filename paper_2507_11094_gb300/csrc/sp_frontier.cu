@@ -434,7 +434,7 @@ __device__ __forceinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *f
 // there.
 
 constexpr u32 kPoolUnknown = 0xFFFFFFFFu;   // entry degree not read yet
-constexpr int kPU = 4;                       // pool edges per lane and step
+constexpr int kPU = 5;                       // pool edges per lane and step (grid vertices with one inserted edge take one step)
 
 // Fetch a line toward L2 without waiting for it: a pool entry's next use is
 // one sub-round later, by then its row is on chip.

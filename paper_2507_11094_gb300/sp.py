@@ -411,9 +411,21 @@ class Graph:
         _check(load().sp_set_loop_blocks(self._h, int(blocks)), "sp_set_loop_blocks")
 
     def get_dist(self, parent: bool = False, out=None):
-        """dist (and parent) as numpy arrays, or into CUDA tensors ``out``
-        = (dist, parent_or_None)."""
+        """dist (and parent) as numpy arrays, or into ``out`` = (dist,
+        parent_or_None): CUDA tensors, or int32 numpy arrays of n entries
+        (page-locked ones are written in place by the kernel)."""
         lib = load()
+        if out is not None and isinstance(out[0], np.ndarray):
+            d, p = out
+            for x in (d, p):
+                if x is not None and (x.dtype != np.int32 or x.size != self.n or
+                                      not x.flags.c_contiguous or not x.flags.writeable):
+                    raise SpError(SP_EINVAL, "get_dist: out arrays must be writable, "
+                                             "contiguous int32 of n entries")
+            rc = lib.sp_get_dist(self._h, d.ctypes.data_as(ctypes.c_void_p),
+                                 p.ctypes.data_as(ctypes.c_void_p) if p is not None else None, 0)
+            _check(rc, "sp_get_dist")
+            return out
         if out is not None:
             d, p = out
             rc = lib.sp_get_dist(self._h, ctypes.c_void_p(d.data_ptr()),

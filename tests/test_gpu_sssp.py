@@ -607,3 +607,42 @@ def test_repeated_batch_shapes_replay_a_cached_graph(make, slack):
             check_all(g, ref, W.source, store=(k % 2 == 0))
     finally:
         g.close()
+
+
+def test_page_locked_host_batches_and_distances():
+    """Page-locked host arrays are read (batch) and written (distances) in
+    place by the kernels; the results equal the oracle's and those of the
+    staged path for pageable arrays of the same batches."""
+    import torch
+    W = wl.rmat(scale=13, batch_frac=0.01, seed=7)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+
+    def pinned(x):
+        t = torch.empty(x.size, dtype=torch.int32, pin_memory=True)
+        t.numpy()[:] = x
+        return t
+
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g, \
+            sp.Graph(W.n, W.row_off, W.col, W.w) as h:
+        g.sssp_init(W.source)
+        h.sssp_init(W.source)
+        dt = torch.empty(W.n, dtype=torch.int32, pin_memory=True)
+        pt = torch.empty(W.n, dtype=torch.int32, pin_memory=True)
+        for k in range(4):   # the same shape repeats: replayed graphs too
+            b = W.batch(k)
+            keep = [pinned(x) for x in (b.del_src, b.del_dst, b.add_src, b.add_dst, b.add_w)]
+            st = g.apply_batch(*[t.numpy() for t in keep], stats=True)
+            h.apply(b)
+            cnt = ref.apply(b)
+            assert (st.n_del_applied, st.n_del_absent, st.n_add_applied,
+                    st.n_add_present) == cnt
+            dt.fill_(-7)
+            pt.fill_(-7)
+            g.get_dist(out=(dt.numpy(), pt.numpy()))
+            want = ref.dijkstra(W.source)
+            np.testing.assert_array_equal(dt.numpy(), want)
+            ro, col, w = ref.csr()
+            check_sssp(g.n, ro, col, w, W.source, dt.numpy(), pt.numpy())
+            np.testing.assert_array_equal(h.get_dist(), want)
+            for a, c in zip(g.export_csr(), (ro, col, w)):
+                np.testing.assert_array_equal(a, c)
