@@ -128,6 +128,11 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the handle            */
     int32_t state;           /* 0 = no distances, 1 = valid, 2 = SP_ESTATE  */
     int32_t num_sms;
+    int32_t pool_step;       /* edges a lane relaxes per step in the pool
+                                schedule: 5 once at least 1/64 of the
+                                vertices have 5..8 out-edges, else 4 (an
+                                extension: speed only, never a distance) */
+    int32_t reserved;
 } sp_graph_info;
 
 /*
@@ -174,11 +179,11 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats);
  * Requires a prior successful sp_sssp_init (else SP_ESTATE).  SP_EINVAL (ids
  * out of range, w outside [1, SP_WMAX], negative counts) leaves the graph
  * unchanged.  stats may be NULL; with stats the call also records per-phase
- * CUDA events.  inputs_on_device = 0: host arrays; page-locked arrays that
- * are mapped into the device's address space (cudaHostAlloc, pinned tensors)
- * are read in place by the kernels over the host link, any other host array
- * is first copied to device staging buffers.  The call is synchronous, so
- * the arrays may be reused once it returns.
+ * CUDA events.  inputs_on_device = 0: host arrays, moved to device staging
+ * buffers first: page-locked arrays that are mapped into the device's
+ * address space (cudaHostAlloc, pinned tensors) by one kernel that reads
+ * them across the host link, any other host array by the copy engine.  The
+ * call is synchronous, so the arrays may be reused once it returns.
  */
 sp_status sp_apply_batch(sp_graph *g,
                          int64_t n_del, const int32_t *del_src, const int32_t *del_dst,

@@ -129,7 +129,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
 }
 
 void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int regrows,
-                long long ni, bool timed) {
+                long long ni, bool timed, bool fold = false) {
   if (!st) return;
   st->n_del_applied = (int64_t)c.del_applied;
   st->n_del_absent = (int64_t)c.del_absent;
@@ -166,9 +166,14 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
   for (int i = 0; i < SP_NPHASE; ++i) st->ms_phase[i] = 0.f;
   st->ms_total = 0.f;
   if (timed) {
-    for (int i = 0; i < SP_NPHASE; ++i)
-      if (cudaEventElapsedTime(&st->ms_phase[i], g->ev[i], g->ev[i + 1]) != cudaSuccess)
+    // fold: a batch pipeline, whose pull and OnAdd run inside the push launch;
+    // it records no events 5 and 6, and its push phase spans events 4..7
+    for (int i = 0; i < SP_NPHASE; ++i) {
+      if (fold && (i == SP_PH_PULL || i == SP_PH_ADD)) continue;
+      const cudaEvent_t from = fold && i == SP_PH_PUSH ? g->ev[SP_PH_PULL] : g->ev[i];
+      if (cudaEventElapsedTime(&st->ms_phase[i], from, g->ev[i + 1]) != cudaSuccess)
         st->ms_phase[i] = 0.f;
+    }
     // an invalidation beside the store update: its own duration (it overlaps
     // the count and merge phases, so the phases add up to more than the total)
     if (g->last_beside &&
@@ -332,11 +337,13 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
   else if (mode == kInvalAfter && e == cudaSuccess && n_del > 0)
     e = sp::launch_inval(g, ds, dd, n_del, launches);
   rec(g, timed, 4);
-  // the pull and OnAdd run as the first stage of the push loop's launch
-  rec(g, timed, 5);
-  rec(g, timed, 6);
+  // the pull and OnAdd run as the first stage of the push loop's launch: the
+  // push phase spans events 4..7 (fill_stats with `fold`), and events 5 and 6
+  // are not recorded (each timing event is one more node of a captured graph)
   if (e == cudaSuccess) e = sp::launch_push(g, launches, n_del > 0 ? 1 : 0, ni);
   rec(g, timed, 7);
+  // the degree share that picks the pool kernel of the next call
+  if (g->lim.pool_rounds > 0) sp::launch_deg_mid(g, launches);
   sp::launch_finish(g, launches);
   rec(g, timed, 8);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -370,8 +377,8 @@ sp_status restore_after(sp_graph *g, bool touched, sp_status rc) {
 
 // The device address of a page-locked host array that is mapped into the
 // device's address space (cudaHostAlloc, torch's pinned memory), or nullptr
-// for any other pointer.  Kernels read and write such arrays in place over
-// the host link (NVLink-C2C on Grace machines), with no staging copy.
+// for any other pointer.  Kernels read and write such arrays directly across
+// the host link (NVLink-C2C on Grace machines), with no copy-engine transfer.
 const void *mapped_host(const void *p) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -502,7 +509,7 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   g->loop_blocks_push = sp::loop_blocks(0, g->num_sms);
   g->loop_blocks_inval = sp::loop_blocks(1, g->num_sms);
-  g->loop_blocks_pool = sp::loop_blocks(3, g->num_sms);
+  g->loop_blocks_pool = std::min(sp::loop_blocks(3, g->num_sms), sp::loop_blocks(4, g->num_sms));
   g->sort_blocks = sp::batch_sort_blocks(g->num_sms);
   g->count_blocks = sp::count_blocks(g->num_sms);
   if (!coop || g->loop_blocks_push <= 0 || g->loop_blocks_inval <= 0 ||
@@ -595,7 +602,14 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   if (rc == SP_OK) rc = sp::store_build(g, &g->rev, ro_d, col_d, w_d, m, 1, &launches);
   if (rc == SP_OK) rc = sp::ensure_owner_tables(g);
   if (tmp_in) g->al.put(tmp_in, tmp_in_bytes);
+  unsigned long long deg_mid = 0;
+  if (rc == SP_OK) {   // the degree share that picks the pool kernel
+    sp::launch_deg_mid(g, &launches);
+    cudaMemcpyAsync(&deg_mid, &g->ctl->deg_mid, sizeof(deg_mid), cudaMemcpyDeviceToHost,
+                    g->stream);
+  }
   if (rc == SP_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) rc = SP_ECUDA;
+  g->pool_wide = sp::pool_wide_for((long long)deg_mid, g->n);
   if (rc != SP_OK) {
     cudaGetLastError();
     sp_graph_destroy(g);
@@ -727,34 +741,38 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   g->last_timed = (int)timed;
   const bool use_graph = g->batch_graphs && g->stream && nb > 0 && repeat;
   const int *ds = del_src, *dd = del_dst, *as = add_src, *ad = add_dst, *aw = add_w;
-  // host arrays in page-locked, mapped memory are read in place by the
-  // kernels; any other host array is copied to the staging buffers first
-  bool in_place = false;
+  // host arrays in page-locked, mapped memory are gathered into the staging
+  // buffers by one kernel (16-byte loads across the host link); any other
+  // host array is copied there by the copy engine
+  const void *m[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool mapped = false;
   if (!inputs_on_device) {
-    const void *m[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    in_place = true;
+    mapped = true;
     if (n_del) {
       m[0] = mapped_host(del_src);
       m[1] = mapped_host(del_dst);
-      in_place = m[0] && m[1];
+      mapped = m[0] && m[1];
     }
-    if (n_add && in_place) {
+    if (n_add && mapped) {
       m[2] = mapped_host(add_src);
       m[3] = mapped_host(add_dst);
       m[4] = mapped_host(add_w);
-      in_place = m[2] && m[3] && m[4];
-    }
-    if (in_place) {
-      ds = (const int *)m[0]; dd = (const int *)m[1];
-      as = (const int *)m[2]; ad = (const int *)m[3]; aw = (const int *)m[4];
+      mapped = m[2] && m[3] && m[4];
     }
   }
-  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device || in_place
-                                                 ? 0 : std::max(n_del, n_add));
+  sp_status rc = ensure_batch_buffers(g, ni, inputs_on_device ? 0 : std::max(n_del, n_add));
   if (rc != SP_OK) return rc;
   auto &b = g->bb;
   rec(g, timed, 0);
-  if (!inputs_on_device && !in_place) {
+  int staged = 0;
+  if (mapped) {
+    const int *src[5] = {(const int *)m[0], (const int *)m[1], (const int *)m[2],
+                         (const int *)m[3], (const int *)m[4]};
+    int *const dst[5] = {b.in_del_src, b.in_del_dst, b.in_add_src, b.in_add_dst, b.in_add_w};
+    const long long cnt[5] = {n_del, n_del, n_add, n_add, n_add};
+    sp::launch_stage_inputs(g, src, dst, cnt, &staged);
+    ds = b.in_del_src; dd = b.in_del_dst; as = b.in_add_src; ad = b.in_add_dst; aw = b.in_add_w;
+  } else if (!inputs_on_device) {
     cudaStream_t s = g->stream;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice
                                                  : cudaMemcpyHostToDevice;
@@ -868,7 +886,14 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
     g->pr_state = 0;   // ranks no longer hold
     g->tc_state = 0;   // nor does the triangle count
   }
-  fill_stats(g, c, stats, launches, regrows, ni, timed);
+  fill_stats(g, c, stats, launches + staged, regrows, ni, timed, true);
+  if (g->lim.pool_rounds > 0) {   // a changed choice of pool kernel recaptures the graph
+    const bool wide = sp::pool_wide_for((long long)c.deg_mid, g->n);
+    if (wide != g->pool_wide) {
+      g->pool_wide = wide;
+      ++g->gen;
+    }
+  }
   return status_of_repair(g, c);
 }
 
@@ -1570,6 +1595,8 @@ sp_status sp_graph_info_get(const sp_graph *g, sp_graph_info *info) {
   info->device_bytes = g->al.bytes_held;
   info->state = g->state;
   info->num_sms = g->num_sms;
+  info->pool_step = g->pool_wide ? 5 : 4;
+  info->reserved = 0;
   return SP_OK;
 }
 

@@ -32,7 +32,9 @@ namespace sp {
 namespace {
 
 // kOpPool: the push fixedPoint with block-local relaxation (pool schedule)
-constexpr int kOpPush = 0, kOpInval = 1, kOpFlag = 2, kOpPool = 3;
+constexpr int kOpPush = 0, kOpInval = 1, kOpFlag = 2, kOpPool = 3, kOpPoolWide = 4;
+// the two pool kernels differ only in the edges a lane relaxes per step
+__host__ __device__ constexpr bool is_pool(int op) { return op == kOpPool || op == kOpPoolWide; }
 constexpr int K = kEdgesPerLane;
 // block stages of the persistent loops (dynamic shared memory)
 constexpr u32 kStageQ = 4096, kStageQS = 12288, kStageA = 2048, kStageAS = 4096, kStageF = 4096;
@@ -434,7 +436,12 @@ __device__ __forceinline__ void flush_far(Stage *st, u32 *pile, u32 *cnt, u32 *f
 // there.
 
 constexpr u32 kPoolUnknown = 0xFFFFFFFFu;   // entry degree not read yet
-constexpr int kPU = 5;                       // pool edges per lane and step (grid vertices with one inserted edge take one step)
+// Pool edges per lane and step: four (kOpPool) or five (kOpPoolWide).  A warp
+// takes as many steps as its largest entry needs, and each step is one more
+// dependent round trip, so on a grid where batches gave many vertices a fifth
+// edge the wide steps win; where almost every vertex has at most four, the
+// narrow steps issue fewer instructions per sub-round and win.
+constexpr int kPoolWideShare = 64;   // wide when >= 1/64 of the vertices have 5..8 out-edges
 
 // Fetch a line toward L2 without waiting for it: a pool entry's next use is
 // one sub-round later, by then its row is on chip.
@@ -513,6 +520,7 @@ struct PoolCounters {
 // (speculative) read of the target's row in flight together, so that a
 // target it improves enters the other list with its row already known.
 // Improved targets at or above thresh go to the far pile (pile != nullptr).
+template <int kPU>
 __device__ __forceinline__ void pool_drain(const LoopArgs &a, Pool *pl, u32 thresh, u32 tag,
                                            u32 phase, const Queue &qn, u32 *pile, u32 *pcnt,
                                            u32 *pmin, Stage *sf, PoolCounters &pc) {
@@ -1518,12 +1526,12 @@ __device__ __forceinline__ void pull_stage(const LoopArgs &a, Stage *st, Stage *
 __device__ __forceinline__ void add_stage(const LoopArgs &a, Stage *st, Stage *sst, u32 *scratch);
 
 template <int OP>
-__global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads, 1)
+__global__ void __launch_bounds__(is_pool(OP) ? kPoolThreads : kPersistThreads, 1)
     k_loop(LoopArgs a) {
   extern __shared__ __align__(16) u32 dsm[];
   __shared__ Stage sq, sqs, sa, sas, sf;
   __shared__ Pool pool;
-  constexpr bool kPushOp = OP == kOpPush || OP == kOpPool;
+  constexpr bool kPushOp = OP == kOpPush || is_pool(OP);
   __shared__ u32 scratch[40];
   Ctl *c = a.ctl;
   // beside the store update the invalidation starts once the batch is
@@ -1541,7 +1549,7 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
     sa.n = 0; sa.cap = kStageA; sa.vmin = kInf; sa.v = p; sa.d = p + kStageA; p += 2 * kStageA;
     sas.n = 0; sas.cap = kStageAS; sas.vmin = kInf; sas.v = p; sas.d = nullptr; p += kStageAS;
     sf.n = 0; sf.cap = kStageF; sf.vmin = 0xFFFFFFFFu; sf.v = p; sf.d = nullptr;
-    if (OP == kOpPool) {
+    if (is_pool(OP)) {
       pool.e[0] = (uint4 *)(dsm + kLoopSmem / sizeof(u32));
       pool.e[1] = pool.e[0] + kPoolCap;
       pool.n[0] = pool.n[1] = 0u;
@@ -1725,7 +1733,7 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
             dx[0] = dist_of(ld_cg_u64(a.s + x[0]));
             if (dx[0] < kInf) {
               if (dx[0] < thresh) {
-                near[0] = OP == kOpPool || atomicExch(a.qflag + x[0], tag) != tag;
+                near[0] = is_pool(OP) || atomicExch(a.qflag + x[0], tag) != tag;
               } else {
                 keep[0] = true;
                 a.ftag[x[0]] = phase + 1u;
@@ -1734,7 +1742,7 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
             }
           }
           moved += near[0];
-          if (OP == kOpPool) {   // into the pool; what does not fit to the frontier
+          if (is_pool(OP)) {   // into the pool; what does not fit to the frontier
             bool rest[K];
             pool_push<false>(&pool, 0, x, dx, near, 1, nullptr, nullptr, rest, pc.n_in,
                              a.fwd.row, nullptr);
@@ -1746,7 +1754,7 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
       } else {
         PushOp op{a.s, a.qflag, tag, qn, a.fwd.row, thresh,
                   nf ? a.fq[f] : nullptr, fcnt_ptr(c, f), fmin_ptr(c, f), a.ftag,
-                  phase, &sf, OP == kOpPool ? &pool : nullptr};
+                  phase, &sf, is_pool(OP) ? &pool : nullptr};
         for (u32 it = gw; it < items; it += nw) {
           if (it < sgroups) process_small(op, a.qsv[cur], nsmall, it, a.fwd, a.n, c);
           else process_chunk(op, a.qent[cur], a.qown[cur], ne, nedge, it - sgroups, a.fwd, a.n, c);
@@ -1757,11 +1765,11 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
         pc.n_in += op.n_in;
         range_err |= op.range_err;
       }
-      if (OP == kOpPool) {
+      if (is_pool(OP)) {
         // the block relaxes what it improved below thresh before the barrier;
         // its far appends belong to the phase that follows this round's split
         const u32 fp = split ? fk : f;
-        pool_drain(a, &pool, thresh, tag, split ? phase + 1u : phase, qn,
+        pool_drain<OP == kOpPoolWide ? 5 : 4>(a, &pool, thresh, tag, split ? phase + 1u : phase, qn,
                    nf ? a.fq[fp] : nullptr, fcnt_ptr(c, fp), fmin_ptr(c, fp), &sf, pc);
       }
     } else if (OP == kOpFlag) {
@@ -1817,7 +1825,7 @@ __global__ void __launch_bounds__(OP == kOpPool ? kPoolThreads : kPersistThreads
   n_aff = warp_sum(n_aff);
   moved = warp_sum(moved);
   range_err = __any_sync(kFull, range_err | pc.range_err);
-  if (OP == kOpPool) {
+  if (is_pool(OP)) {
     n_edges += warp_sum(pc.n_edges);
     n_imp += warp_sum(pc.n_imp);
     n_enq += warp_sum(pc.n_enq);
@@ -2047,9 +2055,24 @@ __global__ void k_gather_dist(const u64 *__restrict__ s, int n, const int *__res
   }
 }
 
+// Distances (and parents) out of the packed state.  Four vertices per thread
+// with 16-byte stores when the outputs are 16-byte aligned (fewer, larger
+// transactions when they are host memory written across the host link).
 __global__ void k_unpack(const u64 *__restrict__ s, int n, int *dist, int *parent) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-       v += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  const bool vec = ((((unsigned long long)dist) | ((unsigned long long)parent)) & 15) == 0;
+  const long long nv = vec ? n / 4 : 0;
+  for (long long i = tid; i < nv; i += nt) {
+    const ulonglong2 x0 = __ldg((const ulonglong2 *)s + 2 * i);
+    const ulonglong2 x1 = __ldg((const ulonglong2 *)s + 2 * i + 1);
+    ((int4 *)dist)[i] = make_int4((int)dist_of(x0.x), (int)dist_of(x0.y), (int)dist_of(x1.x),
+                                  (int)dist_of(x1.y));
+    if (parent)
+      ((int4 *)parent)[i] = make_int4((int)parent_of(x0.x), (int)parent_of(x0.y),
+                                      (int)parent_of(x1.x), (int)parent_of(x1.y));
+  }
+  for (long long v = 4 * nv + tid; v < n; v += nt) {
     const u64 x = s[v];
     dist[v] = (int)dist_of(x);
     if (parent) parent[v] = (int)parent_of(x);
@@ -2369,15 +2392,16 @@ LoopArgs make_args(sp_graph *g) {
 
 int loop_blocks(int which, int num_sms) {
   int per_sm = 0;
-  const void *fn = which == kOpPush    ? (const void *)k_loop<kOpPush>
-                   : which == kOpInval ? (const void *)k_loop<kOpInval>
-                   : which == kOpPool  ? (const void *)k_loop<kOpPool>
-                                       : (const void *)k_loop<kOpFlag>;
-  const size_t smem = which == kOpPool ? kLoopSmemPool : kLoopSmem;
+  const void *fn = which == kOpPush       ? (const void *)k_loop<kOpPush>
+                   : which == kOpInval    ? (const void *)k_loop<kOpInval>
+                   : which == kOpPool     ? (const void *)k_loop<kOpPool>
+                   : which == kOpPoolWide ? (const void *)k_loop<kOpPoolWide>
+                                          : (const void *)k_loop<kOpFlag>;
+  const size_t smem = is_pool(which) ? kLoopSmemPool : kLoopSmem;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per_sm, fn, which == kOpPool ? kPoolThreads : kPersistThreads, smem) !=
+          &per_sm, fn, is_pool(which) ? kPoolThreads : kPersistThreads, smem) !=
           cudaSuccess ||
       per_sm < 1)
     return 0;
@@ -2402,7 +2426,7 @@ void launch_init(sp_graph *g, int source, int *launches) {
 // takes a quarter of the SMs and leaves the rest to the count and merge.
 static int loop_grid(const sp_graph *g, int op, int concurrent) {
   int blocks = op == kOpPush   ? g->loop_blocks_push
-               : op == kOpPool ? g->loop_blocks_pool
+               : is_pool(op)   ? g->loop_blocks_pool
                                : g->loop_blocks_inval;
   if (g->loop_blocks_user > 0 && g->loop_blocks_user < blocks) blocks = g->loop_blocks_user;
   if (concurrent) blocks = std::max(1, std::min(blocks, g->num_sms / 4));
@@ -2414,8 +2438,8 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
   const int blocks = loop_grid(g, op, a.concurrent);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(op == kOpPool ? kPoolThreads : kPersistThreads);
-  cfg.dynamicSmemBytes = op == kOpPool ? kLoopSmemPool : kLoopSmem;
+  cfg.blockDim = dim3(is_pool(op) ? kPoolThreads : kPersistThreads);
+  cfg.dynamicSmemBytes = is_pool(op) ? kLoopSmemPool : kLoopSmem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident
@@ -2425,6 +2449,7 @@ static cudaError_t launch_loop(sp_graph *g, int op, LoopArgs &a, int *launches,
   ++*launches;
   if (op == kOpPush) return cudaLaunchKernelEx(&cfg, k_loop<kOpPush>, a);
   if (op == kOpPool) return cudaLaunchKernelEx(&cfg, k_loop<kOpPool>, a);
+  if (op == kOpPoolWide) return cudaLaunchKernelEx(&cfg, k_loop<kOpPoolWide>, a);
   if (op == kOpInval) return cudaLaunchKernelEx(&cfg, k_loop<kOpInval>, a);
   return cudaLaunchKernelEx(&cfg, k_loop<kOpFlag>, a);
 }
@@ -2470,8 +2495,29 @@ cudaError_t launch_push(sp_graph *g, int *launches, int pull, long long n_items)
   // a single-block round covers kLocalUnroll edges per thread
   if (a.lim.pool_rounds > 0)
     a.lim.local_edges = std::min<u32>(a.lim.local_edges, (u32)(kLocalUnroll * kPoolThreads));
-  return launch_loop(g, a.lim.pool_rounds > 0 ? kOpPool : kOpPush, a, launches, g->stream);
+  const int op = a.lim.pool_rounds == 0 ? kOpPush : g->pool_wide ? kOpPoolWide : kOpPool;
+  return launch_loop(g, op, a, launches, g->stream);
 }
+
+// Vertices whose out-degree is 5..8 (the share that picks the pool kernel),
+// into ctl->deg_mid (zeroed by the control reset).
+__global__ void k_deg_mid(const RowMeta *__restrict__ row, int n, Ctl *c) {
+  u64 k = 0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int d = row[v].deg;
+    k += d >= 5 && d <= 8;
+  }
+  k = warp_sum(k);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd((unsigned long long *)&c->deg_mid, k);
+}
+
+void launch_deg_mid(sp_graph *g, int *launches) {
+  k_deg_mid<<<(unsigned)std::max(1, g->num_sms * 4), 256, 0, g->stream>>>(g->fwd.row, g->n, g->ctl);
+  ++*launches;
+}
+
+bool pool_wide_for(long long deg_mid, int n) { return deg_mid * kPoolWideShare >= (long long)n; }
 
 void launch_gather(sp_graph *g, const int *vs_d, int k, int *out_d, int *launches) {
   k_gather_dist<<<(unsigned)std::max(1, std::min(g->num_sms * 4, (k + 255) / 256)), 256, 0,

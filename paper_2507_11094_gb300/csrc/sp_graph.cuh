@@ -221,6 +221,7 @@ struct sp_graph {
   int32_t max_rounds_user = 0;
   long long wait_ns_user = 0;
   int loop_blocks_push = 0, loop_blocks_inval = 0, loop_blocks_pool = 0;
+  bool pool_wide = false;   // the pool schedule runs five-edge steps (launch_deg_mid)
   int sort_blocks = 0;          // co-resident blocks of the batch sort
   int count_blocks = 0;         // co-resident blocks of the count pass
   int loop_blocks_user = 0;
@@ -276,6 +277,12 @@ cudaError_t launch_push(sp_graph *g, int *launches, int pull = 0, long long n_it
 // blocks (one per SM) of an invalidation beside the store update
 int inval_beside_blocks(const sp_graph *g);
 void launch_unpack(sp_graph *g, int *dist_d, int *parent_d, int *launches);
+// The pool kernel with five-edge steps once at least 1/64 of the vertices
+// have 5..8 out-edges (counted by launch_deg_mid into ctl->deg_mid).
+void launch_deg_mid(sp_graph *g, int *launches);
+bool pool_wide_for(long long deg_mid, int n);
+void launch_stage_inputs(sp_graph *g, const int *const src[5], int *const dst[5],
+                         const long long cnt[5], int *launches);
 // restore of exported distances: the exactness checks (status SP_EINVAL on a
 // violation), then the packed state
 void launch_state_check(sp_graph *g, const int *dist_d, const int *parent_d, int src,

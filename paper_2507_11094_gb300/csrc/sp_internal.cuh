@@ -148,6 +148,7 @@ struct Ctl {
   u64 pool_in;             // entries appended to the block pools
   u64 pool_ns;             // block 0's time in block-local sub-rounds
   u64 pool_sub0;           // block 0's block-local sub-rounds
+  u64 deg_mid;             // vertices with 5..8 out-edges, when the call counts them
 };
 
 // Launch-time limits and knobs.

@@ -221,6 +221,7 @@ __global__ void k_ctl_reset(Ctl *c, int full) {
   c->local_ns = c->push_ns = 0;
   c->pool_sub = c->pool_in = 0;
   c->pool_ns = c->pool_sub0 = 0;
+  c->deg_mid = 0;
   c->call = c->call + 1;
   if (full == 1) {
     c->epoch = 1;
@@ -1203,6 +1204,47 @@ void launch_check_batch(sp_graph *g, const int *ds, const int *dd, long long nd,
   if (nd + na == 0) return;
   k_check_batch<<<blocks_for(nd + na, kThreads, g->num_sms * 16), kThreads, 0, g->stream>>>(
       ds, dd, nd, as, ad, aw, na, g->n, g->ctl);
+  ++*launches;
+}
+
+// A batch's five arrays from page-locked host memory (device addresses of
+// the mapped arrays) into the device staging buffers: one launch with
+// 16-byte loads across the host link wherever both sides are 16-byte
+// aligned, so that the batch sort then reads device memory.
+struct StageArgs {
+  const int *src[5];
+  int *dst[5];
+  long long cnt[5];
+};
+
+__global__ void k_stage_inputs(StageArgs a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int *src = a.src[q];
+    int *dst = a.dst[q];
+    const long long cnt = a.cnt[q];
+    const bool vec = ((((unsigned long long)src) | ((unsigned long long)dst)) & 15) == 0;
+    const long long nv = vec ? cnt / 4 : 0;
+    for (long long i = tid; i < nv; i += nt)
+      ((int4 *)dst)[i] = __ldg((const int4 *)src + i);
+    for (long long i = 4 * nv + tid; i < cnt; i += nt) dst[i] = __ldg(src + i);
+  }
+}
+
+void launch_stage_inputs(sp_graph *g, const int *const src[5], int *const dst[5],
+                         const long long cnt[5], int *launches) {
+  StageArgs a;
+  long long most = 0;
+  for (int q = 0; q < 5; ++q) {
+    a.src[q] = src[q];
+    a.dst[q] = dst[q];
+    a.cnt[q] = src[q] ? cnt[q] : 0;
+    most = std::max(most, (a.cnt[q] + 3) / 4);
+  }
+  if (most == 0) return;
+  k_stage_inputs<<<blocks_for(most, kThreads, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
   ++*launches;
 }
 

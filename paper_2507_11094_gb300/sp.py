@@ -61,7 +61,8 @@ class GraphInfo(ctypes.Structure):
         ("cap_fwd", ctypes.c_int64), ("cap_rev", ctypes.c_int64),
         ("pool_used_fwd", ctypes.c_int64), ("pool_used_rev", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64), ("state", ctypes.c_int32),
-        ("num_sms", ctypes.c_int32),
+        ("num_sms", ctypes.c_int32), ("pool_step", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

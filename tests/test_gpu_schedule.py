@@ -125,3 +125,68 @@ def test_autotuner_schedule_per_graph_kind():
                 ref.apply(b)
                 d = check_all(g, ref, W.source, store=False)
     assert picked["grid"]["pool_rounds"] > 0, picked
+
+
+def _grid_with_fifth_edges(rows, cols, every, seed=0):
+    """A grid plus, for every `every`-th vertex above the last two rows, one
+    extra out-edge two rows down (never a grid edge, so no duplicate)."""
+    W = wl.grid(rows, cols, seed=seed)
+    n = W.n
+    rng = np.random.default_rng(seed)
+    u = np.repeat(np.arange(n, dtype=np.int64), np.diff(W.row_off))
+    src = np.arange(0, n - 2 * cols, every, dtype=np.int64)
+    eu = np.concatenate([u, src])
+    ev = np.concatenate([W.col.astype(np.int64), src + 2 * cols])
+    ew = np.concatenate([W.w, rng.integers(1, 100, src.size).astype(np.int32)])
+    order = np.lexsort((ev, eu))
+    row_off = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(eu, minlength=n), out=row_off[1:])
+    return n, row_off, ev[order].astype(np.int32), ew[order], W.source
+
+
+@pytest.mark.parametrize("every,step", [(0, 4), (8, 5)])
+def test_pool_step_follows_the_degree_share(every, step):
+    """The pool schedule relaxes four edges per lane and step, or five once
+    at least 1/64 of the vertices have 5..8 out-edges; either way the
+    distances equal the oracle's."""
+    if every:
+        n, ro, col, w, src = _grid_with_fifth_edges(96, 96, every)
+    else:
+        W = wl.grid(96, 96, seed=0)
+        n, ro, col, w, src = W.n, W.row_off, W.col, W.w, W.source
+    ref = oracle.OracleGraph(n, ro, col, w)
+    with sp.Graph(n, ro, col, w) as g:
+        assert g.info().pool_step == step
+        g.set_schedule(8, 64)
+        g.set_delta(20000)
+        g.set_local_rounds(0)
+        g.sssp_init(src)
+        assert g.loop_counters()["pool_subrounds"] > 0
+        check_all(g, ref, src, store=False)
+
+
+def test_pool_step_widens_as_batches_add_fifth_edges():
+    """Batches of nearby insertions give many grid vertices a fifth edge:
+    the pool kernel switches to five-edge steps between batches (a new
+    captured graph), and every batch's distances equal the oracle's."""
+    W = wl.grid(64, 64, batch_frac=0.05, seed=4)
+    steps = []
+
+    def setup(g):
+        g.set_schedule(8, 64)
+        g.set_delta(20000)
+        g.set_local_rounds(0)
+        steps.append(g.info().pool_step)
+
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        setup(g)
+        g.sssp_init(W.source)
+        d = check_all(g, ref, W.source, store=False)
+        for k in range(4):
+            b = W.batch(k, dist=d)
+            g.apply(b)
+            ref.apply(b)
+            d = check_all(g, ref, W.source, store=False)
+            steps.append(g.info().pool_step)
+    assert steps[0] == 4 and steps[-1] == 5, steps

@@ -610,9 +610,9 @@ def test_repeated_batch_shapes_replay_a_cached_graph(make, slack):
 
 
 def test_page_locked_host_batches_and_distances():
-    """Page-locked host arrays are read (batch) and written (distances) in
-    place by the kernels; the results equal the oracle's and those of the
-    staged path for pageable arrays of the same batches."""
+    """Page-locked host arrays are gathered by a kernel (batch) and written
+    in place by the kernel (distances); the results equal the oracle's and
+    those of the copy-engine path for pageable arrays of the same batches."""
     import torch
     W = wl.rmat(scale=13, batch_frac=0.01, seed=7)
     ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
