@@ -419,11 +419,9 @@ def run_gb300(args):
         flush.fill_(k)
         torch.cuda.synchronize()
         ev0.record(stream)
-        g.apply_batch(*arrs)
-        lib = sp.load()
-        import ctypes
-        rc = lib.sp_get_dist(g._h, dist_host.ctypes.data_as(ctypes.c_void_p), None, 0)
-        assert rc == 0
+        # one call: the batch from page-locked host arrays, all distances
+        # after it into a page-locked host array
+        g.apply_batch_get(*arrs, dist_host)
         ev1.record(stream)
         ev1.synchronize()
         if k >= 1:

@@ -192,6 +192,25 @@ sp_status sp_apply_batch(sp_graph *g,
                          int inputs_on_device, sp_batch_stats *stats);
 
 /*
+ * sp_apply_batch followed by sp_get_dist in one call: after the repair a
+ * kernel enqueued behind the batch writes the distances (dist[n]) and, if
+ * parent != NULL, the parents (parent[n]), and the call synchronises once.
+ * This is one round of the DynSSSP driver of Section 3.2 as a server runs
+ * it: apply the update batch, then hand out the node properties dist and
+ * parent that the repair maintains.  Inputs as for sp_apply_batch; outputs
+ * as for sp_get_dist (out_on_device: device arrays of the graph's device;
+ * else host arrays, page-locked mapped ones written in place, others through
+ * a device buffer and a copy).  On any status other than SP_OK the contents
+ * of dist and parent are unspecified.
+ */
+sp_status sp_apply_batch_get(sp_graph *g,
+                             int64_t n_del, const int32_t *del_src, const int32_t *del_dst,
+                             int64_t n_add, const int32_t *add_src, const int32_t *add_dst,
+                             const int32_t *add_w, int inputs_on_device,
+                             int32_t *dist, int32_t *parent, int out_on_device,
+                             sp_batch_stats *stats);
+
+/*
  * Copy distances (dist[n]; SP_INF = unreachable) and, if parent != NULL,
  * parents (parent[n]; -1 for the source and unreachable vertices) out:
  * the node properties dist and parent that the problem statement of Section

@@ -63,16 +63,17 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     const long long c = std::max(want, b.cap_items * 2);
     const size_t tmp_bytes = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
                                        sp::batch_sort_tmp_bytes(g->sort_blocks)}) + 1024;
-    void *p[9];
-    const size_t sz[9] = {(size_t)c * 8, (size_t)c * 8, (size_t)c * 4, (size_t)c * 4, (size_t)c,
-                          (size_t)c * 8, (size_t)c * 4, (size_t)c * sizeof(sp::Seg), tmp_bytes};
+    void *p[10];
+    const size_t sz[10] = {(size_t)c * 8, (size_t)c * 8, (size_t)c * 4, (size_t)c * 4,
+                           (size_t)c,     (size_t)c * 8, (size_t)c * 4,
+                           (size_t)c * sizeof(sp::Seg), tmp_bytes, (size_t)c * 8};
     bool ok = true;
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < 10; ++i) {
       p[i] = ok ? al.get(sz[i]) : nullptr;
       ok = ok && p[i];
     }
     if (!ok) {
-      for (int i = 0; i < 9; ++i) al.put(p[i], sz[i]);
+      for (int i = 0; i < 10; ++i) al.put(p[i], sz[i]);
       return SP_ENOMEM;
     }
     const long long old = b.cap_items;
@@ -82,6 +83,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     al.put(b.opos, old * 4);
     al.put(b.seg, old * sizeof(sp::Seg));
     al.put(b.tmp, b.tmp_bytes);
+    al.put(b.srch, old * 8);
     b.keys = (u64 *)p[0]; b.keys_alt = (u64 *)p[1];
     b.vals = (u32 *)p[2]; b.vals_alt = (u32 *)p[3];
     b.flags = (unsigned char *)p[4];
@@ -90,6 +92,7 @@ sp_status ensure_batch_buffers(sp_graph *g, long long ni, long long nb_host) {
     b.seg = (sp::Seg *)p[7];
     b.tmp = p[8];
     b.tmp_bytes = tmp_bytes;
+    b.srch = (u64 *)p[9];
     b.cap_items = c;
     ++g->gen;
   }
@@ -148,8 +151,13 @@ void fill_stats(sp_graph *g, const Ctl &c, sp_batch_stats *st, int launches, int
   // Algorithmic bytes: what each phase must move, counted from what it did.
   const int passes = (2 * g->bits + 2 + 7) / 8;
   const long long nb = ni / 2;
-  st->alg_bytes[SP_PH_SORT] = ni ? (int64_t)(nb * 20 + ni * 12 + (long long)passes * ni * 24) : 0;
-  st->alg_bytes[SP_PH_COUNT] = (int64_t)(ni * 21 + (long long)c.rows_touched * 16);
+  // the sort phase also holds the old-row searches that run beside the sort
+  // (inputs 10 per item on average, the row's meta 16, the result 8)
+  st->alg_bytes[SP_PH_SORT] =
+      ni ? (int64_t)(nb * 20 + ni * 12 + (long long)passes * ni * 24 + ni * 34) : 0;
+  // key 8, number 4 and search result 8 read; opos 4, flags 1, weight 4 and
+  // prefix 8 written per item; 16 per touched row
+  st->alg_bytes[SP_PH_COUNT] = (int64_t)(ni * 37 + (long long)c.rows_touched * 16);
   st->alg_bytes[SP_PH_MERGE] = (int64_t)(c.merge_slots * 8 + c.rows_touched * 32 + ni * 21);
   st->alg_bytes[SP_PH_INVAL] =
       (int64_t)(c.affected * (16 + 8 + 8 + 4) + c.inval_edges * 16);
@@ -202,7 +210,7 @@ void drop_batch_graphs(sp_graph *g) {
   if (g->bg_graph) cudaGraphDestroy(g->bg_graph);
   g->bg_exec = nullptr;
   g->bg_graph = nullptr;
-  g->bg_sort = g->bg_inval = nullptr;
+  g->bg_sort = g->bg_inval = g->bg_search = nullptr;
   g->bg_ready = false;
 }
 
@@ -212,10 +220,10 @@ void drop_batch_graphs(sp_graph *g) {
 bool inval_beside(const sp_graph *g) { return g->side && g->lim.jump_round == 0; }
 
 // The kernel nodes of the captured batch graph that read the batch inputs:
-// the batch sort (every input array) and the invalidation loop (the
-// deletions).  Every other kernel reads the sorted items.
+// the batch sort and the old-row searches (every input array) and the
+// invalidation loop (the deletions).  Every other kernel reads the sorted items.
 bool find_input_nodes(sp_graph *g) {
-  g->bg_sort = g->bg_inval = nullptr;
+  g->bg_sort = g->bg_inval = g->bg_search = nullptr;
   size_t nn = 0;
   if (cudaGraphGetNodes(g->bg_graph, nullptr, &nn) != cudaSuccess) return false;
   std::vector<cudaGraphNode_t> nodes(nn);
@@ -227,13 +235,16 @@ bool find_input_nodes(sp_graph *g) {
     if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess) return false;
     if (p.func == sp::batch_sort_fn()) g->bg_sort = nd;
     else if (p.func == sp::inval_fn()) g->bg_inval = nd;
+    else if (p.func == sp::search_fn()) g->bg_search = nd;
   }
-  return g->bg_sort != nullptr;
+  return g->bg_sort != nullptr && g->bg_search != nullptr;
 }
 
 cudaError_t retarget_input_nodes(sp_graph *g, const int *ds, const int *dd, long long nd,
                                  const int *as, const int *ad, const int *aw, long long na) {
   cudaError_t e = sp::retarget_batch_sort(g, g->bg_exec, g->bg_sort, ds, dd, nd, as, ad, aw, na);
+  if (e == cudaSuccess)
+    e = sp::retarget_search(g, g->bg_exec, g->bg_search, ds, dd, nd, as, ad, aw, na);
   if (e == cudaSuccess && g->bg_inval)
     e = sp::retarget_inval(g, g->bg_exec, g->bg_inval, ds, dd, nd, inval_beside(g) ? 1 : 0);
   return e;
@@ -306,8 +317,21 @@ cudaError_t enqueue_batch(sp_graph *g, const int *ds, const int *dd, long long n
                           bool timed, int *launches, int mode = kInvalAfter) {
   const long long ni = 2 * (n_del + n_add);
   sp::launch_ctl_reset(g, mode == kInvalKept ? 2 : 0, launches);
-  cudaError_t e = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, launches);
+  // the items' searches in their old rows run beside the batch sort (on the
+  // SMs the sort leaves free; they read only the inputs and the old stores)
+  cudaError_t e = cudaSuccess;
+  if (g->side) {
+    cudaEventRecord(g->fork0_ev, g->stream);
+    cudaStreamWaitEvent(g->side, g->fork0_ev, 0);
+    e = sp::launch_search(g, ds, dd, n_del, as, ad, aw, n_add, launches, g->side);
+    cudaEventRecord(g->search_ev, g->side);
+  } else {
+    e = sp::launch_search(g, ds, dd, n_del, as, ad, aw, n_add, launches, g->stream);
+  }
+  const cudaError_t es = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, launches);
+  if (e == cudaSuccess) e = es;
   rec(g, timed, 1);
+  if (g->side) cudaStreamWaitEvent(g->stream, g->search_ev, 0);
   const bool beside = mode == kInvalBeside && n_del > 0;
   g->last_beside = beside && timed;
   // fork: the invalidation runs beside the count pass and the merge once the
@@ -435,6 +459,7 @@ sp_status sp_graph_destroy(sp_graph *g) {
   al.put(b.seg, c * sizeof(sp::Seg));
   al.put(b.strips, (size_t)b.strips_cap * 8);
   al.put(b.tmp, b.tmp_bytes);
+  al.put(b.srch, c * 8);
   c = b.cap_in;
   al.put(b.in_del_src, c * 4); al.put(b.in_del_dst, c * 4);
   al.put(b.in_add_src, c * 4); al.put(b.in_add_dst, c * 4); al.put(b.in_add_w, c * 4);
@@ -472,6 +497,8 @@ sp_status sp_graph_destroy(sp_graph *g) {
     if (e) cudaEventDestroy(e);
   if (g->fork_ev) cudaEventDestroy(g->fork_ev);
   if (g->join_ev) cudaEventDestroy(g->join_ev);
+  if (g->fork0_ev) cudaEventDestroy(g->fork0_ev);
+  if (g->search_ev) cudaEventDestroy(g->search_ev);
   if (g->side) cudaStreamDestroy(g->side);
   cudaStreamSynchronize(g->stream);
   delete g;
@@ -532,7 +559,9 @@ sp_status sp_graph_create(int32_t n, int64_t m, const int64_t *row_off, const in
   if (g->stream &&
       (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
        cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-       cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming) != cudaSuccess)) {
+       cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->fork0_ev, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->search_ev, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
     sp_graph_destroy(g);
     return SP_ECUDA;
@@ -719,10 +748,89 @@ sp_status sp_sssp_init(sp_graph *g, int32_t source, sp_batch_stats *stats) {
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Where a batch call writes the distances (and parents) after the repair:
+// device addresses for the unpack kernel, or the graph's unpack buffers and
+// a copy to pageable host arrays behind it.  want = false: no read-out.
+struct DistOut {
+  bool want = false;
+  int32_t *dist_d = nullptr, *parent_d = nullptr;   // unpack targets
+  int32_t *dist_h = nullptr, *parent_h = nullptr;   // pageable host copies (or null)
+};
+
+sp_status resolve_out(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_device,
+                      DistOut *o) {
+  o->want = true;
+  if (out_on_device) {
+    o->dist_d = dist;
+    o->parent_d = parent;
+    return SP_OK;
+  }
+  int32_t *md = (int32_t *)mapped_host(dist);
+  int32_t *mp = parent ? (int32_t *)mapped_host(parent) : nullptr;
+  if (md && (!parent || mp)) {   // page-locked and mapped: written in place
+    o->dist_d = md;
+    o->parent_d = mp;
+    return SP_OK;
+  }
+  o->dist_d = g->out_dist;
+  o->parent_d = parent ? g->out_parent : nullptr;
+  o->dist_h = dist;
+  o->parent_h = parent;
+  return SP_OK;
+}
+
+void enqueue_out(sp_graph *g, const DistOut &o, int *launches) {
+  if (!o.want) return;
+  sp::launch_unpack(g, o.dist_d, o.parent_d, launches);
+  if (o.dist_h)
+    cudaMemcpyAsync(o.dist_h, o.dist_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream);
+  if (o.parent_h)
+    cudaMemcpyAsync(o.parent_h, o.parent_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost,
+                    g->stream);
+}
+
+sp_status apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                      const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                      const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
+                      sp_batch_stats *stats, const DistOut &out);
+
+}  // namespace
+
+extern "C" {
+
 sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
                          const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
                          const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
                          sp_batch_stats *stats) {
+  return apply_batch(g, n_del, del_src, del_dst, n_add, add_src, add_dst, add_w,
+                     inputs_on_device, stats, DistOut());
+}
+
+sp_status sp_apply_batch_get(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                             const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                             const int32_t *add_dst, const int32_t *add_w,
+                             int inputs_on_device, int32_t *dist, int32_t *parent,
+                             int out_on_device, sp_batch_stats *stats) {
+  if (!g || !dist) return SP_EINVAL;
+  DistOut o;
+  sp_status rc = resolve_out(g, dist, parent, out_on_device, &o);
+  if (rc != SP_OK) return rc;
+  return apply_batch(g, n_del, del_src, del_dst, n_add, add_src, add_dst, add_w,
+                     inputs_on_device, stats, o);
+}
+
+}  // extern "C"
+
+namespace {
+
+sp_status apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
+                      const int32_t *del_dst, int64_t n_add, const int32_t *add_src,
+                      const int32_t *add_dst, const int32_t *add_w, int inputs_on_device,
+                      sp_batch_stats *stats, const DistOut &out) {
   if (!g) return SP_EINVAL;
   if (n_del < 0 || n_add < 0) return SP_EINVAL;
   if ((n_del > 0 && (!del_src || !del_dst)) || (n_add > 0 && (!add_src || !add_dst || !add_w)))
@@ -847,6 +955,8 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
       g->state = 2;
       return SP_ECUDA;
     }
+    // the read-out follows the batch on the stream (a rerun repeats it)
+    enqueue_out(g, out, &launches);
     rc = read_ctl(g, true);   // the batch ends with k_finish, replayed or not
     if (rc != SP_OK) {
       g->state = 2;
@@ -896,6 +1006,10 @@ sp_status sp_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   }
   return status_of_repair(g, c);
 }
+
+}  // namespace
+
+extern "C" {
 
 sp_status sp_sssp_init_multi(sp_graph *g, const int32_t *sources, int32_t k,
                              int sources_on_device, sp_batch_stats *stats) {
@@ -1062,6 +1176,8 @@ sp_status pr_phase(sp_graph *g, const int *ds, const int *dd, long long nd, cons
     sp::launch_ctl_reset(g, 0, launches);
     cudaError_t e = cudaSuccess;
     if (n_flag > 0) e = sp::launch_flag(g, flag_dst, n_flag, launches);
+    const cudaError_t eq = sp::launch_search(g, ds, dd, nd, as, ad, aw, na, launches, g->stream);
+    if (e == cudaSuccess) e = eq;
     const cudaError_t es = sp::launch_batch_sort(g, ds, dd, nd, as, ad, aw, na, launches);
     if (e == cudaSuccess) e = es;
     sp::launch_count(g, ni, launches);
@@ -1329,7 +1445,10 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
   int launches = 0, regrows = 0;
   for (int attempt = 0;; ++attempt) {
     sp::launch_ctl_reset(g, 0, &launches);
-    const cudaError_t es = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
+    const cudaError_t eq =
+        sp::launch_search(g, ds, dd, n_del, as, ad, aw, n_add, &launches, g->stream);
+    cudaError_t es = sp::launch_batch_sort(g, ds, dd, n_del, as, ad, aw, n_add, &launches);
+    if (es == cudaSuccess) es = eq;
     rec(g, true, 1);
     sp::launch_count(g, ni, &launches);
     sp::launch_tc_batch_sym(g, nb, &launches);     // before anything changes
@@ -1539,7 +1658,7 @@ sp_status sp_footprint_bound(int32_t n, int64_t m, float slack, int64_t max_upda
   const int sblocks = sp::batch_sort_blocks(sms);
   const size_t tmp = std::max({sp::sort_tmp_bytes(c), sp::scan_tmp_bytes(c),
                                sp::batch_sort_tmp_bytes(sblocks)}) + 1024;
-  b += (double)c * (8 + 8 + 4 + 4 + 1 + 8 + 4 + sizeof(sp::Seg)) + (double)tmp;
+  b += (double)c * (8 + 8 + 4 + 4 + 1 + 8 + 4 + sizeof(sp::Seg) + 8) + (double)tmp;
   b += 8.0 * (2.0 * M / 256.0 + 2.0 * (double)max_updates + 64.0);   // merge strips
   b += 20.0 * (double)max_updates;                       // staged host inputs
   *bytes = (int64_t)std::ceil(b) + 64 * 256;             // allocation slack

@@ -2381,7 +2381,7 @@ LoopArgs make_args(sp_graph *g) {
   a.concurrent = 0;
   a.seed_pull = 0;
   a.keys = g->bb.keys;
-  a.vals = g->bb.vals;
+  a.vals = g->bb.vals_alt;   // the batch's weights in sorted order (the count pass's)
   a.flags = g->bb.flags;
   a.n_items = 0;
   a.bits = g->bits;

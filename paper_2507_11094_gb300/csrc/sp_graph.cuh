@@ -92,6 +92,9 @@ struct BatchBufs {
   unsigned char *flags = nullptr;   // per item: bit0 = applied, bit1 = edge was present
   u64 *item_pref = nullptr;         // exclusive prefix of the applied updates per item
   u32 *opos = nullptr;              // per item: old entries of its row with a smaller col
+  // per item in the batch's own numbering (the sort carries that number as
+  // its value): weight << 32 | edge present << 31 | position in the old row
+  u64 *srch = nullptr;
   Seg *seg = nullptr;
   int2 *strips = nullptr;           // merge strips: (segment, first old entry)
   long long strips_cap = 0;
@@ -167,6 +170,7 @@ struct sp_graph {
   // side stream of the invalidation, which runs beside the store update
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaEvent_t fork0_ev = nullptr, search_ev = nullptr;   // the search beside the sort
   cudaEvent_t ev_inval[2] = {nullptr, nullptr};
   bool last_beside = false;     // the last timed call ran the invalidation beside
   // PageRank state (allocated by sp_pr_init): ranks in two buffers that
@@ -193,7 +197,8 @@ struct sp_graph {
   // one graph per batch shape; the phase timing events are nodes inside it
   cudaGraph_t bg_graph = nullptr;
   cudaGraphExec_t bg_exec = nullptr;
-  cudaGraphNode_t bg_sort = nullptr, bg_inval = nullptr;   // nodes that read the inputs
+  cudaGraphNode_t bg_sort = nullptr, bg_inval = nullptr,   // nodes that read the inputs
+                  bg_search = nullptr;
   bool bg_ready = false;
   int capturing = -1;                    // >= 0 while the pipeline is captured
   unsigned long long bg_gen = 0;
@@ -256,6 +261,16 @@ cudaError_t launch_batch_sort(sp_graph *g, const int *ds, const int *dd, long lo
 // the captured batch-sort / invalidation node of an instantiated graph,
 // pointed at another batch of the same shape
 const void *batch_sort_fn();
+// The old-row searches of a batch's items (their positions, whether the
+// edge is there, and their weights into bb.srch), for the count pass; they
+// read only the old stores, so they may run beside the batch sort.
+cudaError_t launch_search(sp_graph *g, const int *ds, const int *dd, long long nd,
+                          const int *as, const int *ad, const int *aw, long long na,
+                          int *launches, cudaStream_t stream);
+const void *search_fn();
+cudaError_t retarget_search(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node,
+                            const int *ds, const int *dd, long long nd, const int *as,
+                            const int *ad, const int *aw, long long na);
 cudaError_t retarget_batch_sort(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node,
                                 const int *ds, const int *dd, long long nd, const int *as,
                                 const int *ad, const int *aw, long long na);

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kBT) k_batch_sort(BatchSortArgs a) {
         }
         rk[k] = rev ? (1ull << (2 * bits + 1)) | ((u64)v[k] << (bits + 1)) | ((u64)u[k] << 1) | kind
                     : ((u64)u[k] << (bits + 1)) | ((u64)v[k] << 1) | kind;
-        rv[k] = (u32)w[k];
+        rv[k] = i;   // the item's own number: its search result and weight (k_search)
       }
     }
 #pragma unroll

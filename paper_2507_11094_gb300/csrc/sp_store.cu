@@ -259,7 +259,9 @@ struct CountArgs {
   Ctl *ctl;
   long long strips_cap;  // small rows are listed from the end of strips
   const u64 *keys;
-  const u32 *vals;
+  const u32 *vals;       // each sorted item's number in the batch's own order
+  const u64 *srch;       // by that number: weight << 32 | present << 31 | position
+  u32 *wts;              // out: the weights in sorted order (merge, OnAdd)
   Seg *seg;
   unsigned char *flags;
   u64 *item_pref;      // exclusive prefix of the applied (ins << 32 | dels), n_items + 1
@@ -330,8 +332,9 @@ __device__ __forceinline__ u64 block_excl_scan_u64(u64 x, u64 *ws, u64 *total) {
 //     applies if the edge is absent after the deletions.  Every item also
 //     records where its col falls in the old row (opos: the old entries with
 //     a smaller col) and whether the edge was there (flags bit 1), which is
-//     all the merge needs to place it.  Each thread advances the binary
-//     searches of kCI items in lockstep, so their loads overlap.
+//     all the merge needs to place it, and its weight in sorted order.  The
+//     searches that find those ran beside the batch sort (k_search); an item
+//     reads its result through the number the sort carried as its value.
 //  2. The exclusive prefix of the applied (ins << 32 | dels) over all items
 //     (block scans, then the block bases after a grid barrier).
 //  3. One thread per touched row (after a second barrier): new size,
@@ -349,7 +352,6 @@ __global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
   const u32 G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const u32 ni = a.n_items;
   const u32 cb = min(b * a.chunk, ni), ce = min(cb + a.chunk, ni);
-  const u64 cmask = (1ull << a.bits) - 1;
   u64 *bar = &c->bar_count;
   u64 del_ok = 0, del_abs = 0, add_ok = 0, add_pres = 0;
   if (t == 0) s_run = 0;
@@ -357,9 +359,9 @@ __global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
   __syncthreads();
 
   for (u32 tb = cb; tb < ce; tb += kCTile) {
-    u64 key[kCI], pk[kCI], nk[kCI];
-    int col[kCI], lo[kCI], hi[kCI], deg[kCI], dir[kCI];
-    const int2 *old[kCI];
+    u64 key[kCI], pk[kCI], nk[kCI], sr[kCI];
+    int dir[kCI];
+    u32 orig[kCI];
     bool val[kCI];
 #pragma unroll
     for (int k = 0; k < kCI; ++k) {
@@ -368,47 +370,24 @@ __global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
       key[k] = val[k] ? a.keys[i] : 0ull;
       pk[k] = val[k] && i > 0 ? a.keys[i - 1] : ~0ull;
       nk[k] = val[k] && i + 1 < ni ? a.keys[i + 1] : ~0ull;
+      orig[k] = val[k] ? a.vals[i] : 0u;
     }
+    // the item's search in its old row ran beside the batch sort (k_search)
 #pragma unroll
     for (int k = 0; k < kCI; ++k) {
       dir[k] = (int)(key[k] >> (2 * a.bits + 1));
-      const int row = (int)((key[k] >> (a.bits + 1)) & cmask);
-      col[k] = (int)((key[k] >> 1) & cmask);
-      const Store &st = a.st[dir[k] & 1];
-      RowMeta rm;
-      rm.start = 0;
-      rm.deg = 0;
-      if (val[k]) rm = st.row[row];
-      old[k] = st.adj + rm.start;
-      lo[k] = 0;
-      hi[k] = deg[k] = rm.deg;
-    }
-    for (;;) {   // binary searches in lockstep: every load of a step in flight together
-      bool act = false;
-      int mid[kCI], x[kCI];
-#pragma unroll
-      for (int k = 0; k < kCI; ++k) {
-        act |= lo[k] < hi[k];
-        mid[k] = (lo[k] + hi[k]) >> 1;
-        x[k] = lo[k] < hi[k] ? __ldg(&old[k][mid[k]].x) : 0;
-      }
-      if (!act) break;
-#pragma unroll
-      for (int k = 0; k < kCI; ++k)
-        if (lo[k] < hi[k]) {
-          if (x[k] < col[k]) lo[k] = mid[k] + 1; else hi[k] = mid[k];
-        }
+      sr[k] = val[k] && orig[k] < ni ? __ldcg(a.srch + orig[k]) : 0ull;
     }
     u64 iv[kCI];
 #pragma unroll
     for (int k = 0; k < kCI; ++k) {
-      const int cl = lo[k] < deg[k] ? __ldg(&old[k][lo[k]].x) : -1;
       iv[k] = 0;
       if (!val[k]) continue;
       const u32 i = tb + k * kCT + t;
-      const bool present = cl == col[k];
+      const bool present = (sr[k] >> 31) & 1;
       const unsigned char pbit = present ? 2 : 0;
-      a.opos[i] = (u32)lo[k];
+      a.opos[i] = (u32)sr[k] & 0x7FFFFFFFu;
+      a.wts[i] = (u32)(sr[k] >> 32);
       if ((key[k] & 1) == 0) {
         const bool applied = present && pk[k] != key[k];
         a.flags[i] = (applied ? 1 : 0) | pbit;
@@ -421,9 +400,9 @@ __global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
         if (pk[k] == key[k] || nk[k] == key[k]) {
           while (first > 0 && a.keys[first - 1] == key[k]) --first;
           while (last + 1 < ni && a.keys[last + 1] == key[k]) ++last;
-          u32 bi = first, bw = a.vals[first];
+          u32 bi = first, bw = (u32)(__ldcg(a.srch + a.vals[first]) >> 32);
           for (u32 q = first + 1; q <= last; ++q) {
-            const u32 w2 = a.vals[q];
+            const u32 w2 = (u32)(__ldcg(a.srch + a.vals[q]) >> 32);
             if (w2 < bw) { bw = w2; bi = q; }
           }
           best = bi == i;
@@ -574,6 +553,110 @@ __global__ void __launch_bounds__(kCT, 3) k_count(CountArgs a) {
   block_add(touched, &sums[4], &c->rows_touched);
   block_add(relocated, &sums[5], &c->rows_relocated);
   block_add(slots, &sums[6], &c->merge_slots);
+}
+
+// --------------------------------------------------------------------------
+// batch: the old-row searches, beside the batch sort
+// --------------------------------------------------------------------------
+
+struct SearchArgs {
+  const int *ds, *dd, *as, *ad, *aw;
+  long long nd, na;
+  Store st[2];
+  u64 *srch;
+  int n;
+  u32 n_items;
+};
+
+// Item i of the batch in the batch sort's own numbering (update j < nd is
+// deletion j, then the insertions; item j is its forward item, nb + j its
+// reverse one): the binary search of its col in its old row, as the count
+// pass needs it (position = old entries with a smaller col, and whether the
+// edge is there), and its weight, into srch[i].  The stores do not change
+// before the merge, so this runs beside the sort; ids out of range (the sort
+// rejects the batch) get 0.  Each thread advances kCI searches in lockstep.
+__global__ void __launch_bounds__(kCT) k_search(SearchArgs a) {
+  const long long nb = a.nd + a.na;
+  const u32 ni = a.n_items;
+  for (u32 tb = blockIdx.x * (u32)kCTile; tb < ni; tb += gridDim.x * (u32)kCTile) {
+    int col[kCI], lo[kCI], hi[kCI], deg[kCI];
+    u32 w[kCI];
+    const int2 *old[kCI];
+    bool val[kCI];
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {   // every input load first
+      const u32 i = tb + (u32)(k * kCT) + threadIdx.x;
+      val[k] = i < ni;
+      int u = 0, v = 0;
+      w[k] = 0;
+      const bool rev = (long long)i >= nb;
+      const long long j = rev ? (long long)i - nb : (long long)i;
+      if (val[k]) {
+        if (j < a.nd) {
+          u = __ldg(a.ds + j);
+          v = __ldg(a.dd + j);
+        } else {
+          u = __ldg(a.as + (j - a.nd));
+          v = __ldg(a.ad + (j - a.nd));
+          w[k] = (u32)__ldg(a.aw + (j - a.nd));
+        }
+      }
+      const bool ok = val[k] && u >= 0 && u < a.n && v >= 0 && v < a.n;
+      const int row = rev ? v : u;
+      col[k] = rev ? u : v;
+      RowMeta rm;
+      rm.start = 0;
+      rm.deg = 0;
+      if (ok) rm = a.st[rev ? 1 : 0].row[row];
+      old[k] = a.st[rev ? 1 : 0].adj + rm.start;
+      lo[k] = 0;
+      hi[k] = deg[k] = rm.deg;
+    }
+    for (;;) {   // binary searches in lockstep: every load of a step in flight together
+      bool act = false;
+      int mid[kCI], x[kCI];
+#pragma unroll
+      for (int k = 0; k < kCI; ++k) {
+        act |= lo[k] < hi[k];
+        mid[k] = (lo[k] + hi[k]) >> 1;
+        x[k] = lo[k] < hi[k] ? __ldg(&old[k][mid[k]].x) : 0;
+      }
+      if (!act) break;
+#pragma unroll
+      for (int k = 0; k < kCI; ++k)
+        if (lo[k] < hi[k]) {
+          if (x[k] < col[k]) lo[k] = mid[k] + 1; else hi[k] = mid[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCI; ++k) {
+      const int cl = lo[k] < deg[k] ? __ldg(&old[k][lo[k]].x) : -1;
+      if (val[k]) {
+        const u32 i = tb + (u32)(k * kCT) + threadIdx.x;
+        a.srch[i] = ((u64)w[k] << 32) | (cl == col[k] ? 0x80000000ull : 0ull) | (u32)lo[k];
+      }
+    }
+  }
+}
+
+SearchArgs search_args(sp_graph *g, const int *ds, const int *dd, long long nd, const int *as,
+                       const int *ad, const int *aw, long long na) {
+  SearchArgs a;
+  a.ds = ds; a.dd = dd; a.as = as; a.ad = ad; a.aw = aw;
+  a.nd = nd; a.na = na;
+  a.st[0] = g->fwd;
+  a.st[1] = g->rev;
+  a.srch = g->bb.srch;
+  a.n = g->n;
+  a.n_items = (u32)(2 * (nd + na));
+  return a;
+}
+
+// One block of 256 threads per SM at most: beside it an SM still holds a
+// block of the batch sort (512 threads, 90-116 KB of shared memory, about
+// 45k registers), so the search never delays the sort's cooperative grid.
+unsigned search_grid(const sp_graph *g, long long ni) {
+  return blocks_for(ni, kCTile, std::max(1, g->num_sms));
 }
 
 // --------------------------------------------------------------------------
@@ -1128,6 +1211,8 @@ void launch_count(sp_graph *g, long long ni, int *launches, int avoid_sms) {
   a.ctl = g->ctl;
   a.keys = b.keys;
   a.vals = b.vals;
+  a.srch = b.srch;
+  a.wts = b.vals_alt;   // free once the sort has ended (its output is keys / vals)
   a.seg = b.seg;
   a.flags = b.flags;
   a.item_pref = b.item_pref;
@@ -1176,7 +1261,7 @@ void launch_merge(sp_graph *g, long long ni, int *launches) {
   MergeArgs a;
   a.ctl = g->ctl;
   a.keys = b.keys;
-  a.vals = b.vals;
+  a.vals = b.vals_alt;   // the weights in sorted order (written by the count pass)
   a.flags = b.flags;
   a.item_pref = b.item_pref;
   a.seg = b.seg;
@@ -1220,17 +1305,28 @@ struct StageArgs {
 __global__ void k_stage_inputs(StageArgs a) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
+  long long nv[5], most = 0;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const int *src = a.src[q];
-    int *dst = a.dst[q];
-    const long long cnt = a.cnt[q];
-    const bool vec = ((((unsigned long long)src) | ((unsigned long long)dst)) & 15) == 0;
-    const long long nv = vec ? cnt / 4 : 0;
-    for (long long i = tid; i < nv; i += nt)
-      ((int4 *)dst)[i] = __ldg((const int4 *)src + i);
-    for (long long i = 4 * nv + tid; i < cnt; i += nt) dst[i] = __ldg(src + i);
+    const bool vec =
+        ((((unsigned long long)a.src[q]) | ((unsigned long long)a.dst[q])) & 15) == 0;
+    nv[q] = vec ? a.cnt[q] / 4 : 0;
+    most = nv[q] > most ? nv[q] : most;
   }
+  // a thread's loads of all five arrays are in flight together (one
+  // round trip across the link), then its stores
+  for (long long i = tid; i < most; i += nt) {
+    int4 v[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (i < nv[q]) v[q] = __ldg((const int4 *)a.src[q] + i);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (i < nv[q]) ((int4 *)a.dst[q])[i] = v[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q)   // tails, and arrays that are not 16-byte aligned
+    for (long long i = 4 * nv[q] + tid; i < a.cnt[q]; i += nt) a.dst[q][i] = __ldg(a.src[q] + i);
 }
 
 void launch_stage_inputs(sp_graph *g, const int *const src[5], int *const dst[5],
@@ -1246,6 +1342,32 @@ void launch_stage_inputs(sp_graph *g, const int *const src[5], int *const dst[5]
   if (most == 0) return;
   k_stage_inputs<<<blocks_for(most, kThreads, g->num_sms * 8), kThreads, 0, g->stream>>>(a);
   ++*launches;
+}
+
+cudaError_t launch_search(sp_graph *g, const int *ds, const int *dd, long long nd,
+                          const int *as, const int *ad, const int *aw, long long na,
+                          int *launches, cudaStream_t stream) {
+  const long long ni = 2 * (nd + na);
+  if (ni == 0) return cudaSuccess;
+  k_search<<<search_grid(g, ni), kCT, 0, stream>>>(search_args(g, ds, dd, nd, as, ad, aw, na));
+  ++*launches;
+  return cudaGetLastError();
+}
+
+const void *search_fn() { return (const void *)k_search; }
+
+cudaError_t retarget_search(sp_graph *g, cudaGraphExec_t ex, cudaGraphNode_t node,
+                            const int *ds, const int *dd, long long nd, const int *as,
+                            const int *ad, const int *aw, long long na) {
+  SearchArgs a = search_args(g, ds, dd, nd, as, ad, aw, na);
+  void *args[1] = {&a};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)k_search;
+  p.gridDim = dim3(search_grid(g, 2 * (nd + na)));
+  p.blockDim = dim3(kCT);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  return cudaGraphExecKernelNodeSetParams(ex, node, &p);
 }
 
 void launch_finish(sp_graph *g, int *launches) {

@@ -115,6 +115,8 @@ SIGNATURES = {
     "sp_graph_destroy": (ctypes.c_int, [_P]),
     "sp_sssp_init": (ctypes.c_int, [_P, _I32, _P]),
     "sp_apply_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int, _P]),
+    "sp_apply_batch_get": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, ctypes.c_int,
+                                          _P, _P, ctypes.c_int, _P]),
     "sp_get_dist": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "sp_graph_num_edges": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sp_export_csr": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]),
@@ -371,6 +373,44 @@ class Graph:
             _check(rc, "sp_apply_batch", self._h)
             return st
         return rc, st
+
+    def apply_batch_get(self, del_src, del_dst, add_src, add_dst, add_w, dist, parent=None,
+                        stats: bool = False):
+        """apply_batch, then the distances (and parents) after it into
+        ``dist`` / ``parent``, in one call with one synchronisation: CUDA
+        tensors or int32 numpy arrays of n entries (page-locked host arrays
+        are written in place).  Returns BatchStats (or None)."""
+        arr = _Arrays([del_src, del_dst, add_src, add_dst, add_w], [np.int32] * 5)
+        size = (lambda a: int(a.numel())) if arr.on_device else (lambda a: int(a.size))
+        nd, na = size(arr.keep[0]), size(arr.keep[2])
+        if size(arr.keep[1]) != nd or size(arr.keep[3]) != na or size(arr.keep[4]) != na:
+            raise SpError(SP_EINVAL, "batch array sizes")
+        out_dev = _is_cuda_tensor(dist)
+        ptrs = []
+        for x in (dist, parent):
+            if x is None:
+                ptrs.append(None)
+                continue
+            if out_dev:
+                t = _torch()
+                if (not _is_cuda_tensor(x) or x.dtype != t.int32 or x.numel() != self.n or
+                        not x.is_contiguous() or x.device.index != self.device):
+                    raise SpError(SP_EINVAL, "apply_batch_get: outputs must be contiguous "
+                                             "int32 CUDA tensors of n entries on the graph's "
+                                             "device")
+                ptrs.append(ctypes.c_void_p(x.data_ptr()))
+            else:
+                if (not isinstance(x, np.ndarray) or x.dtype != np.int32 or x.size != self.n or
+                        not x.flags.c_contiguous or not x.flags.writeable):
+                    raise SpError(SP_EINVAL, "apply_batch_get: outputs must be writable, "
+                                             "contiguous int32 arrays of n entries")
+                ptrs.append(x.ctypes.data_as(ctypes.c_void_p))
+        st = BatchStats() if stats else None
+        rc = load().sp_apply_batch_get(self._h, nd, arr.ptrs[0], arr.ptrs[1], na, arr.ptrs[2],
+                                       arr.ptrs[3], arr.ptrs[4], int(arr.on_device), ptrs[0],
+                                       ptrs[1], int(out_dev), ctypes.byref(st) if st else None)
+        _check(rc, "sp_apply_batch_get", self._h)
+        return st
 
     def apply(self, batch, stats: bool = False):
         """Apply a ``workloads.Batch``."""

@@ -646,3 +646,41 @@ def test_page_locked_host_batches_and_distances():
             np.testing.assert_array_equal(h.get_dist(), want)
             for a, c in zip(g.export_csr(), (ro, col, w)):
                 np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("where", ["device", "page-locked", "pageable"])
+def test_apply_batch_get_returns_the_repaired_distances(where):
+    """One call applies a batch and hands out the distances and parents after
+    it (device tensors, page-locked or pageable host arrays); they equal the
+    oracle's, and a later get_dist agrees."""
+    import torch
+    W = wl.rmat(scale=12, batch_frac=0.02, seed=11)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    if where == "device":
+        d_out = torch.empty(W.n, dtype=torch.int32, device="cuda")
+        p_out = torch.empty(W.n, dtype=torch.int32, device="cuda")
+    elif where == "page-locked":
+        d_out = torch.empty(W.n, dtype=torch.int32, pin_memory=True).numpy()
+        p_out = torch.empty(W.n, dtype=torch.int32, pin_memory=True).numpy()
+    else:
+        d_out = np.empty(W.n, np.int32)
+        p_out = np.empty(W.n, np.int32)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        g.sssp_init(W.source)
+        for k in range(4):   # the same shape repeats: replayed graphs too
+            b = W.batch(k)
+            arrs = (b.del_src, b.del_dst, b.add_src, b.add_dst, b.add_w)
+            if where == "device":
+                arrs = [torch.from_numpy(x).cuda() for x in arrs]
+            g.apply_batch_get(*arrs, d_out, p_out if k % 2 else None)
+            ref.apply(b)
+            want = ref.dijkstra(W.source)
+            d = d_out.cpu().numpy() if where == "device" else d_out
+            np.testing.assert_array_equal(d, want)
+            if k % 2:
+                p = p_out.cpu().numpy() if where == "device" else p_out
+                ro, col, w = ref.csr()
+                check_sssp(g.n, ro, col, w, W.source, d, p)
+            np.testing.assert_array_equal(g.get_dist(), want)
+        with pytest.raises(sp.SpError):
+            g.apply_batch_get(*arrs, np.empty(W.n - 1, np.int32))
