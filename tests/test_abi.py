@@ -62,6 +62,8 @@ def test_argument_checks_need_no_device(lib):
     assert lib.sp_graph_destroy(None) == 0
     assert lib.sp_sssp_init(None, 0, None) == -1
     assert lib.sp_apply_batch(None, 0, None, None, 0, None, None, None, 0, None) == -1
+    assert lib.sp_apply_batch_get(None, 0, None, None, 0, None, None, None, 0, None, None, 1,
+                                  None) == -1
     from paper_2507_11094_gb300 import sp
     srv = ctypes.c_void_p()
     assert lib.sp_server_create(None, ctypes.byref(srv)) == -1
