@@ -216,9 +216,10 @@ sp_status sp_apply_batch_get(sp_graph *g,
  * the node properties dist and parent that the problem statement of Section
  * 3.2 maintains (propNode<int> dist, propNode<node> parent of the DynSSSP
  * program).  out_on_device: dist/parent are device arrays of the graph's
- * device (else host memory; page-locked, mapped host arrays are written in
- * place by the kernel, others through a device buffer and a copy).  The call
- * is synchronous.  SP_ESTATE if no valid distances exist.
+ * device, else SP_EINVAL before anything runs (out_on_device = 0: host
+ * memory; page-locked, mapped host arrays are written in place by the
+ * kernel, others through a device buffer and a copy).  The call is
+ * synchronous.  SP_ESTATE if no valid distances exist.
  */
 sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent,
                       int out_on_device);
@@ -261,7 +262,8 @@ sp_status sp_footprint_bound(int32_t n, int64_t m, float slack, int64_t max_upda
  * Export the current edge set as a row-sorted CSR: row_off[n+1], col[m],
  * w[m] with m from sp_graph_num_edges.  `reverse` = 1 exports the reverse
  * (transpose) store instead: row v lists the sources u of edges u -> v with
- * their weights.  Used for checkpoints and for store tests.
+ * their weights.  Used for checkpoints and for store tests.  out_on_device:
+ * device arrays of the graph's device, else SP_EINVAL before anything runs.
  */
 sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off,
                         int32_t *col, int32_t *w, int out_on_device);
@@ -589,12 +591,12 @@ sp_status sp_tc_apply_batch(sp_graph *g, int64_t n_del, const int32_t *del_src,
                             int inputs_on_device, int64_t *count, sp_batch_stats *stats);
 
 /*
- * sp_apply_batch runs its kernels (seven per batch) as a cached CUDA graph
+ * sp_apply_batch runs its kernels (eight per batch) as a cached CUDA graph
  * when a batch has the same shape (deletion and insertion counts, stats or
  * not) as the one before it: one graph launch replaces the kernel launches.
- * Device inputs are read where they are (the two kernels that read them are
- * pointed at this call's arrays before the launch); host inputs are first
- * copied to internal buffers.  The graph is rebuilt when a buffer or a
+ * Device inputs are read where they are (the three kernels that read them
+ * are pointed at this call's arrays before the launch); host inputs are
+ * first moved to internal buffers.  The graph is rebuilt when a buffer or a
  * setting changes.  on = 0 turns it off (every call launches kernels one by
  * one); the default is 1.  Results do not depend on it.  Requires a
  * non-default stream (graphs are never used on the legacy stream).

@@ -412,6 +412,19 @@ const void *mapped_host(const void *p) {
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+// A device array the graph's kernels may write: memory of the graph's device
+// (or managed memory).  Host pointers passed as device outputs are refused
+// before anything is launched.
+bool device_out(const sp_graph *g, const void *p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice && at.device == g->device) ||
+         at.type == cudaMemoryTypeManaged;
+}
+
 // Buffers big enough for an asynchronous batch of ni items?
 bool reserved_for(const sp_graph *g, long long ni) {
   const sp::BatchBufs &b = g->bb;
@@ -765,6 +778,7 @@ sp_status resolve_out(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_de
                       DistOut *o) {
   o->want = true;
   if (out_on_device) {
+    if (!device_out(g, dist) || (parent && !device_out(g, parent))) return SP_EINVAL;
     o->dist_d = dist;
     o->parent_d = parent;
     return SP_OK;
@@ -1583,6 +1597,8 @@ sp_status sp_get_dist(sp_graph *g, int32_t *dist, int32_t *parent, int out_on_de
   if (!g || !dist) return SP_EINVAL;
   if (g->state != 1) return SP_ESTATE;
   int launches = 0;
+  if (out_on_device && (!device_out(g, dist) || (parent && !device_out(g, parent))))
+    return SP_EINVAL;
   // a page-locked, mapped host destination is written in place
   int32_t *mdist = out_on_device ? nullptr : (int32_t *)mapped_host(dist);
   int32_t *mparent = out_on_device || !parent ? nullptr : (int32_t *)mapped_host(parent);
@@ -1676,7 +1692,11 @@ sp_status sp_export_csr(sp_graph *g, int reverse, int64_t *row_off, int32_t *col
   if (!g || !row_off || (g->m > 0 && (!col || !w))) return SP_EINVAL;
   int launches = 0;
   const sp::Store *st = reverse ? &g->rev : &g->fwd;
-  if (out_on_device) return sp::store_export(g, st, (long long *)row_off, col, w, &launches);
+  if (out_on_device) {
+    if (!device_out(g, row_off) || (g->m > 0 && (!device_out(g, col) || !device_out(g, w))))
+      return SP_EINVAL;
+    return sp::store_export(g, st, (long long *)row_off, col, w, &launches);
+  }
   const size_t nn = (size_t)g->n, mm = (size_t)std::max<long long>(g->m, 1);
   size_t bytes = (nn + 1) * 8 + 2 * mm * 4 + 512;
   char *buf = (char *)g->al.get(bytes);

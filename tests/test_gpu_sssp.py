@@ -684,3 +684,29 @@ def test_apply_batch_get_returns_the_repaired_distances(where):
             np.testing.assert_array_equal(g.get_dist(), want)
         with pytest.raises(sp.SpError):
             g.apply_batch_get(*arrs, np.empty(W.n - 1, np.int32))
+
+
+def test_device_outputs_must_be_device_memory():
+    """Outputs declared as device arrays (out_on_device = 1) that are host
+    memory are refused with SP_EINVAL before anything runs; the graph keeps
+    working."""
+    import ctypes
+    W = wl.tiny_er(seed=5)
+    ref = oracle.OracleGraph(W.n, W.row_off, W.col, W.w)
+    lib = sp.load()
+    host = np.empty(max(W.n + 1, W.m), np.int64)
+    hp = host.ctypes.data_as(ctypes.c_void_p)
+    with sp.Graph(W.n, W.row_off, W.col, W.w) as g:
+        g.sssp_init(W.source)
+        assert lib.sp_get_dist(g._h, hp, None, 1) == sp.SP_EINVAL
+        assert lib.sp_export_csr(g._h, 0, hp, hp, hp, 1) == sp.SP_EINVAL
+        b = W.batch(0)
+        assert lib.sp_apply_batch_get(
+            g._h, b.del_src.size, b.del_src.ctypes.data_as(ctypes.c_void_p),
+            b.del_dst.ctypes.data_as(ctypes.c_void_p), b.add_src.size,
+            b.add_src.ctypes.data_as(ctypes.c_void_p), b.add_dst.ctypes.data_as(ctypes.c_void_p),
+            b.add_w.ctypes.data_as(ctypes.c_void_p), 0, hp, None, 1, None) == sp.SP_EINVAL
+        # nothing changed: the same batch still applies and matches the oracle
+        g.apply(b)
+        ref.apply(b)
+        np.testing.assert_array_equal(g.get_dist(), ref.dijkstra(W.source))
