@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -144,3 +145,23 @@ def test_export_targets_are_checked_before_any_launch():
     for args, msg in cases:
         with pytest.raises(ValueError, match=msg):
             sp._check_export_targets(g, *args)
+
+
+def test_apply_batch_get_outputs_are_checked_before_the_call():
+    """apply_batch_get writes n distances (and parents) through raw pointers:
+    host outputs of the wrong dtype, length or layout, or read-only ones, are
+    refused in the binding before the C call (no GPU needed)."""
+    from paper_2507_11094_gb300 import sp
+    g = sp.Graph.__new__(sp.Graph)
+    g.n, g.device, g._h = 10, 0, None
+    z = np.zeros(3, np.int32)
+    ro = np.zeros(10, np.int32)
+    ro.flags.writeable = False
+    for bad in (np.zeros(9, np.int32), np.zeros(10, np.int64), np.zeros(20, np.int32)[::2],
+                ro, [0] * 10):
+        with pytest.raises(sp.SpError):
+            g.apply_batch_get(z, z, z, z, z, bad)
+    with pytest.raises(sp.SpError):   # a bad parent array with a good dist
+        g.apply_batch_get(z, z, z, z, z, np.zeros(10, np.int32), np.zeros(9, np.int32))
+    with pytest.raises(sp.SpError):   # batch arrays of different lengths
+        g.apply_batch_get(z, z[:2], z, z, z, np.zeros(10, np.int32))
