@@ -19,7 +19,10 @@
  *     library until sp_graph_destroy().
  *   - Host or device pointers: a flag on each call says whether the arrays
  *     are host memory (pageable or pinned) or device memory of the graph's
- *     device.  Device arrays must stay valid until the call returns.
+ *     device.  Device arrays must stay valid until the call returns.  Batch
+ *     arrays and distance outputs in page-locked host memory that is mapped
+ *     into the device's address space are read and written by kernels across
+ *     the host link; other host arrays go through the copy engine.
  *   - Streams: every call is ordered on the CUDA stream given at creation and
  *     returns only after its work on that stream is complete (the status it
  *     returns is the device's).  A handle is not thread-safe; distinct
